@@ -1,0 +1,217 @@
+"""FP64 CPU oracle (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the product path never does.  The
+arithmetic lives in ``ccm_oracle.cpp`` (double precision, plain loops, forward-
+mode dual numbers for exact derivatives); this file only builds it and
+marshals numpy arrays through ctypes.
+
+Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
+  * ``sdf``            -- brute-force polytope distance, LSE bounds, tau -> 0 limit.
+  * ``edge_point``     -- Cyrus-Beck chord midpoint (many iterations, small tau),
+                          inside-edge midpoint, one-step convergence on a face.
+  * ``transition``     -- knot values and C^2 continuity.
+  * ``forward``        -- cube-on-cube closed form and hard limits, rigid-motion
+                          invariance, body-swap symmetry, separation.
+  * ``gradient``/``hvp`` -- central finite differences in FP64, rigid-motion
+                          null directions, Hessian symmetry.
+  * random-hull blended values beyond those invariants: parity unpinned
+    (the paper prints no worked example).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ccm_oracle.cpp")
+_LIB = os.path.join(_HERE, "libccm_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (OpenMP) into ``oracle/libccm_oracle.so``."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", "-o", _LIB, _SRC]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("tau_sdf", C.c_double), ("tau_trace", C.c_double), ("tau_clip", C.c_double),
+                ("tau_blend", C.c_double), ("d_max", C.c_double), ("gate_width", C.c_double),
+                ("trace_iters", C.c_int32), ("flags", C.c_int32)]
+
+
+class _Geom(C.Structure):
+    _fields_ = [("body_piece_off", C.c_void_p), ("piece_v_off", C.c_void_p),
+                ("piece_f_off", C.c_void_p), ("piece_e_off", C.c_void_p),
+                ("verts", C.c_void_p), ("planes", C.c_void_p), ("edges", C.c_void_p)]
+
+
+DEFAULTS = dict(tau_sdf=5e-3, tau_trace=5e-3, tau_clip=5e-3, tau_blend=5e-3,
+                d_max=0.01, gate_width=0.01, trace_iters=3)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P, I64, D, I = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        _lib.ccmo_forward.argtypes = [P, I64, P, P, P, P, P, P, P, I]
+        _lib.ccmo_gradient.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, P, I]
+        _lib.ccmo_hvp.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, P, P, P, I]
+        _lib.ccmo_sdf.argtypes = [P, I, P, D, P]
+        _lib.ccmo_sdf.restype = D
+        _lib.ccmo_edge_point.argtypes = [P, I, P, P, P, P, P]
+        for f in ("ccmo_transition",):
+            getattr(_lib, f).argtypes = [D, D, D]
+            getattr(_lib, f).restype = D
+        _lib.ccmo_softclip.argtypes = [D, D, D, D]
+        _lib.ccmo_softclip.restype = D
+        _lib.ccmo_softplus.argtypes = [D, D]
+        _lib.ccmo_softplus.restype = D
+        _lib.ccmo_sigmoid.argtypes = [D]
+        _lib.ccmo_sigmoid.restype = D
+        _lib.ccmo_pair_contacts.argtypes = [P, I64, I64, P, P, P, P, I64]
+        _lib.ccmo_pair_contacts.restype = I64
+    return _lib
+
+
+def params(**kw) -> Params:
+    d = dict(DEFAULTS)
+    d.update(kw)
+    return Params(float(d["tau_sdf"]), float(d["tau_trace"]), float(d["tau_clip"]),
+                  float(d["tau_blend"]), float(d["d_max"]), float(d["gate_width"]),
+                  int(d["trace_iters"]), 0)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _Packed:
+    """FP64 copies of a Geometry kept alive for the duration of a call."""
+
+    def __init__(self, geom):
+        self.arrs = [np.ascontiguousarray(geom.body_piece_off, np.int64),
+                     np.ascontiguousarray(geom.piece_v_off, np.int64),
+                     np.ascontiguousarray(geom.piece_f_off, np.int64),
+                     np.ascontiguousarray(geom.piece_e_off, np.int64),
+                     np.ascontiguousarray(geom.verts, np.float64),
+                     np.ascontiguousarray(geom.planes, np.float64),
+                     np.ascontiguousarray(geom.edges, np.int32)]
+        self.s = _Geom(*[a.ctypes.data for a in self.arrs])
+
+    def ref(self):
+        return C.byref(self.s)
+
+
+def _scene_args(scene):
+    pa = np.ascontiguousarray(scene.pair_a, np.int64)
+    pb = np.ascontiguousarray(scene.pair_b, np.int64)
+    A = np.ascontiguousarray(scene.pose_a, np.float64)
+    B = np.ascontiguousarray(scene.pose_b, np.float64)
+    goff = scene.group_offsets()
+    return pa, pb, A, B, goff
+
+
+def forward(scene, prm=None, threads=0):
+    """Group outputs y [G, 8] = (d, a, p, n) of every pair (Sec. 4.4)."""
+    prm = prm or params()
+    g = _Packed(scene.geom)
+    pa, pb, A, B, goff = _scene_args(scene)
+    y = np.zeros((int(goff[-1]), 8))
+    lib().ccmo_forward(g.ref(), len(pa), _ptr(pa), _ptr(pb), _ptr(A), _ptr(B),
+                       C.byref(prm), _ptr(goff), _ptr(y), threads)
+    return y
+
+
+def gradient(scene, ybar, prm=None, xi=None, threads=0):
+    """(grad [n,12], y [G,8]) of L = <ybar, y> w.r.t. the twists
+    (w_A, v_A, w_B, v_B), at Exp(xi) T."""
+    prm = prm or params()
+    g = _Packed(scene.geom)
+    pa, pb, A, B, goff = _scene_args(scene)
+    ybar = np.ascontiguousarray(ybar, np.float64)
+    grad = np.zeros((len(pa), 12))
+    y = np.zeros((int(goff[-1]), 8))
+    xi_p = None
+    if xi is not None:
+        xi = np.ascontiguousarray(xi, np.float64)
+        xi_p = _ptr(xi)
+    lib().ccmo_gradient(g.ref(), len(pa), _ptr(pa), _ptr(pb), _ptr(A), _ptr(B), C.byref(prm),
+                        _ptr(goff), _ptr(ybar), xi_p, _ptr(grad), _ptr(y), threads)
+    return grad, y
+
+
+def hvp(scene, ybar, u, prm=None, threads=0):
+    """(grad [n,12], H u [n,12], J u [G,8], y [G,8]) in the twist chart at xi = 0."""
+    prm = prm or params()
+    g = _Packed(scene.geom)
+    pa, pb, A, B, goff = _scene_args(scene)
+    ybar = np.ascontiguousarray(ybar, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    grad = np.zeros((len(pa), 12))
+    hv = np.zeros((len(pa), 12))
+    jv = np.zeros((int(goff[-1]), 8))
+    y = np.zeros((int(goff[-1]), 8))
+    lib().ccmo_hvp(g.ref(), len(pa), _ptr(pa), _ptr(pb), _ptr(A), _ptr(B), C.byref(prm),
+                   _ptr(goff), _ptr(ybar), _ptr(u), _ptr(grad), _ptr(hv), _ptr(jv), _ptr(y),
+                   threads)
+    return grad, hv, jv, y
+
+
+def sdf(planes, x, tau):
+    """(phi, grad phi) of one piece at one point (Sec. 3, smooth intersection)."""
+    planes = np.ascontiguousarray(planes, np.float64).reshape(-1, 4)
+    x = np.ascontiguousarray(x, np.float64).reshape(3)
+    g = np.zeros(3)
+    phi = lib().ccmo_sdf(_ptr(planes), len(planes), _ptr(x), float(tau), _ptr(g))
+    return phi, g
+
+
+def edge_point(planes, vI, vII, prm=None):
+    """(p^e, (alpha_I, alpha_II, clipped_I, clipped_II)) of one edge (Sec. 4.2)."""
+    prm = prm or params()
+    planes = np.ascontiguousarray(planes, np.float64).reshape(-1, 4)
+    a = np.ascontiguousarray(vI, np.float64).reshape(3)
+    b = np.ascontiguousarray(vII, np.float64).reshape(3)
+    pe = np.zeros(3)
+    al = np.zeros(4)
+    lib().ccmo_edge_point(_ptr(planes), len(planes), _ptr(a), _ptr(b), C.byref(prm),
+                          _ptr(pe), _ptr(al))
+    return pe, al
+
+
+def transition(d, d_max=0.01, eps=0.01):
+    return lib().ccmo_transition(float(d), float(d_max), float(eps))
+
+
+def softclip(x, lo, hi, tau):
+    return lib().ccmo_softclip(float(x), float(lo), float(hi), float(tau))
+
+
+def softplus(x, tau):
+    return lib().ccmo_softplus(float(x), float(tau))
+
+
+def sigmoid(x):
+    return lib().ccmo_sigmoid(float(x))
+
+
+def pair_contacts(scene, i=0, prm=None):
+    """Every contact of pair ``i``: rows (group, phi, f, d_c, p_w(3), n_w(3))."""
+    prm = prm or params()
+    g = _Packed(scene.geom)
+    A = np.ascontiguousarray(scene.pose_a[i], np.float64)
+    B = np.ascontiguousarray(scene.pose_b[i], np.float64)
+    bA, bB = int(scene.pair_a[i]), int(scene.pair_b[i])
+    n = lib().ccmo_pair_contacts(g.ref(), bA, bB, _ptr(A), _ptr(B), C.byref(prm), None, 0)
+    rows = np.zeros((n, 10))
+    lib().ccmo_pair_contacts(g.ref(), bA, bB, _ptr(A), _ptr(B), C.byref(prm), _ptr(rows), n)
+    return rows

@@ -1,0 +1,459 @@
+"""Seeded synthetic scenes: convex-decomposed bodies and rigid poses.
+
+This module only *generates inputs*: meshes of convex pieces (vertices, face
+planes, edges), body pairs and rigid poses.  It holds none of the contact
+method's arithmetic (no smooth SDF, sphere trace, mollifier or blend); both the
+CUDA path and the FP64 oracle consume what it returns.
+
+Geometry conventions (Sec. 3, PSQ paragraph): every piece is a convex polytope
+given by its hull vertices, its face planes ``(n, h)`` with ``n`` the unit
+outward normal so that ``n.x + h`` is negative inside, and its edges as pairs of
+piece-local vertex indices.  Poses are ``[n, 12]`` float32 rows: the row-major
+rotation ``R`` (9 values) followed by the translation ``t`` (3 values); a pose
+maps body-frame points to world points, ``x_w = R x + t``.
+
+Workloads (all seeded):
+  * ``cube_pair_scene``   -- unit cubes, one piece each, 64 poses with exact
+                             box-box (15-axis SAT) penetration depth ~ U[0, 0.05].
+  * ``hull_env_scene``    -- environments of two bodies with 8 pieces each; a
+                             piece is the convex hull of 64 points N(c, 0.05^2),
+                             c ~ N(0, 0.1^2) per axis; 70 % of the environments
+                             penetrate by U[0, 0.02], 30 % are separated by a
+                             max-plane gap U[0, 0.02].
+  * ``uneven_scene``      -- pieces per body log-uniform in [1, 64], hull points
+                             per piece log-uniform in [8, 512], same placement.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Geometry", "Scene", "unit_cube_piece", "hull_piece", "random_rotations",
+    "geometry_from_bodies", "cube_pair_scene", "hull_env_scene", "uneven_scene",
+    "log_uniform_int", "box_penetration_depth",
+]
+
+
+# ----------------------------------------------------------------------------
+# containers
+# ----------------------------------------------------------------------------
+@dataclass
+class Geometry:
+    """A set of bodies; each body is a list of convex pieces (flat SoA arrays).
+
+    ``body_piece_off[b] .. body_piece_off[b+1]`` are the pieces of body ``b``;
+    ``piece_v_off``/``piece_f_off``/``piece_e_off`` index ``verts``/``planes``/
+    ``edges`` the same way.  Edge indices are local to their piece.
+    """
+    body_piece_off: np.ndarray  # int64 [nb+1]
+    piece_v_off: np.ndarray     # int64 [np+1]
+    piece_f_off: np.ndarray     # int64 [np+1]
+    piece_e_off: np.ndarray     # int64 [np+1]
+    verts: np.ndarray           # float32 [V, 3]
+    planes: np.ndarray          # float32 [F, 4]  (nx, ny, nz, h)
+    edges: np.ndarray           # int32   [E, 2]  piece-local vertex indices
+
+    @property
+    def n_bodies(self) -> int:
+        return len(self.body_piece_off) - 1
+
+    @property
+    def n_pieces(self) -> int:
+        return len(self.piece_v_off) - 1
+
+    def pieces_of(self, b: int) -> range:
+        return range(int(self.body_piece_off[b]), int(self.body_piece_off[b + 1]))
+
+    def piece(self, p: int):
+        """(verts [V,3], planes [F,4], edges [E,2]) of piece ``p``."""
+        v0, v1 = self.piece_v_off[p], self.piece_v_off[p + 1]
+        f0, f1 = self.piece_f_off[p], self.piece_f_off[p + 1]
+        e0, e1 = self.piece_e_off[p], self.piece_e_off[p + 1]
+        return self.verts[v0:v1], self.planes[f0:f1], self.edges[e0:e1]
+
+    def body_pieces(self, b: int):
+        return [self.piece(p) for p in self.pieces_of(b)]
+
+    def subset(self, bodies) -> "Geometry":
+        """Geometry holding only ``bodies`` (in that order)."""
+        return geometry_from_bodies([self.body_pieces(int(b)) for b in bodies])
+
+
+@dataclass
+class Scene:
+    """Body pairs with poses.  ``pair_a[i], pair_b[i]`` are body indices."""
+    geom: Geometry
+    pair_a: np.ndarray          # int64 [n]
+    pair_b: np.ndarray          # int64 [n]
+    pose_a: np.ndarray          # float32 [n, 12]
+    pose_b: np.ndarray          # float32 [n, 12]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_pairs(self) -> int:
+        return len(self.pair_a)
+
+    def group_offsets(self) -> np.ndarray:
+        """int64 [n+1]: pair i owns groups [off[i], off[i+1]); the first
+        N_A groups are the pieces of body A, then the N_B pieces of body B."""
+        npb = np.diff(self.geom.body_piece_off)
+        cnt = npb[self.pair_a] + npb[self.pair_b]
+        return np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+
+    def piece_pairs(self) -> int:
+        npb = np.diff(self.geom.body_piece_off)
+        return int(np.sum(npb[self.pair_a] * npb[self.pair_b]))
+
+    def take(self, idx) -> "Scene":
+        """Sub-scene of the pairs ``idx`` (geometry is shared, not copied)."""
+        idx = np.asarray(idx, dtype=np.int64)
+        return Scene(self.geom, self.pair_a[idx], self.pair_b[idx],
+                     self.pose_a[idx].copy(), self.pose_b[idx].copy(), dict(self.meta))
+
+
+def geometry_from_bodies(bodies) -> Geometry:
+    """Pack ``bodies`` (list of list of (verts, planes, edges)) into SoA."""
+    bpo = [0]
+    pvo, pfo, peo = [0], [0], [0]
+    V, F, E = [], [], []
+    for pieces in bodies:
+        for (v, f, e) in pieces:
+            V.append(np.asarray(v, np.float32).reshape(-1, 3))
+            F.append(np.asarray(f, np.float32).reshape(-1, 4))
+            E.append(np.asarray(e, np.int32).reshape(-1, 2))
+            pvo.append(pvo[-1] + len(V[-1]))
+            pfo.append(pfo[-1] + len(F[-1]))
+            peo.append(peo[-1] + len(E[-1]))
+        bpo.append(bpo[-1] + len(pieces))
+    return Geometry(
+        np.asarray(bpo, np.int64), np.asarray(pvo, np.int64),
+        np.asarray(pfo, np.int64), np.asarray(peo, np.int64),
+        np.concatenate(V) if V else np.zeros((0, 3), np.float32),
+        np.concatenate(F) if F else np.zeros((0, 4), np.float32),
+        np.concatenate(E) if E else np.zeros((0, 2), np.int32))
+
+
+# ----------------------------------------------------------------------------
+# pieces
+# ----------------------------------------------------------------------------
+def unit_cube_piece(half=0.5, center=(0.0, 0.0, 0.0)):
+    """Axis-aligned cube: 8 vertices, 6 face planes, 12 edges."""
+    c = np.asarray(center, np.float64)
+    verts = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)],
+                     np.float64) * half + c
+    planes = []
+    for ax in range(3):
+        for s in (-1.0, 1.0):
+            n = np.zeros(3)
+            n[ax] = s
+            planes.append([*n, -(half + s * c[ax])])
+    edges = []
+    for i in range(8):
+        for j in range(i + 1, 8):
+            if np.sum(np.abs(verts[i] - verts[j]) > 1e-12) == 1:
+                edges.append([i, j])
+    return verts.astype(np.float32), np.asarray(planes, np.float32), np.asarray(edges, np.int32)
+
+
+def hull_piece(points):
+    """Convex hull of ``points`` [k,3] -> (verts, planes, edges).
+
+    Uses Qhull through scipy (input preparation, not the method).  Facets are
+    triangles; nearly identical facet planes (coplanar triangles) are merged
+    so that each face plane appears once.
+    """
+    from scipy.spatial import ConvexHull
+
+    pts = np.asarray(points, np.float64)
+    hull = ConvexHull(pts)
+    vid = np.asarray(hull.vertices)
+    remap = -np.ones(len(pts), np.int64)
+    remap[vid] = np.arange(len(vid))
+    verts = pts[vid]
+    eqs = hull.equations  # (n, offset): n.x + offset <= 0 inside, n unit outward
+    same = np.abs(eqs[:, None, :] - eqs[None, :, :]).max(-1) < 1e-9
+    first = ~np.tril(same, -1).any(1)          # keep the first of each coplanar set
+    planes = eqs[first]
+    tri = remap[hull.simplices]                                   # [T,3]
+    pairs = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [0, 2]]])
+    owner = np.tile(np.arange(len(tri)), 3)
+    pairs.sort(axis=1)
+    key = pairs[:, 0] * (len(verts) + 1) + pairs[:, 1]
+    if len(planes) != len(eqs):
+        # a segment shared by two coplanar triangles is a face diagonal, not an edge
+        order = np.argsort(key, kind="stable")
+        k, o = key[order], owner[order]
+        dup = (k[1:] == k[:-1]) & (np.abs(eqs[o[1:]] - eqs[o[:-1]]).max(-1) < 1e-9)
+        drop = set(k[1:][dup].tolist())
+        keep = np.array([kk not in drop for kk in key])
+        pairs, key = pairs[keep], key[keep]
+    _, first = np.unique(key, return_index=True)
+    edges = pairs[np.sort(first)]
+    edges = edges[np.lexsort((edges[:, 1], edges[:, 0]))].astype(np.int32)
+    return verts.astype(np.float32), np.asarray(planes, np.float32), edges
+
+
+# ----------------------------------------------------------------------------
+# poses
+# ----------------------------------------------------------------------------
+def random_rotations(rng, n):
+    """Uniform rotations on SO(3) (Shoemake: normalised 4-D Gaussian quaternion)."""
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.empty((n, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def random_unit_vectors(rng, n):
+    u = rng.normal(size=(n, 3))
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def pack_pose(R, t):
+    """[n,3,3], [n,3] -> float32 [n,12]."""
+    R = np.asarray(R, np.float64).reshape(-1, 9)
+    t = np.asarray(t, np.float64).reshape(-1, 3)
+    return np.concatenate([R, t], axis=1).astype(np.float32)
+
+
+def unpack_pose(P):
+    P = np.asarray(P, np.float64)
+    return P[:, :9].reshape(-1, 3, 3), P[:, 9:12]
+
+
+def log_uniform_int(rng, lo, hi, size):
+    """Integers log-uniform in [lo, hi]: floor(exp(U(ln lo, ln(hi + 1))))."""
+    x = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=size))).astype(np.int64)
+    return np.clip(x, lo, hi)
+
+
+def _world_frame(rng, RA, tA, RB, tB):
+    """Apply one common random rigid motion (offset in [-1,1]^3) per pair."""
+    n = len(RA)
+    Rw = random_rotations(rng, n)
+    tw = rng.uniform(-1.0, 1.0, size=(n, 3))
+    RA2 = Rw @ RA
+    RB2 = Rw @ RB
+    tA2 = np.einsum("nij,nj->ni", Rw, tA) + tw
+    tB2 = np.einsum("nij,nj->ni", Rw, tB) + tw
+    return RA2, tA2, RB2, tB2
+
+
+# ----------------------------------------------------------------------------
+# config: unit cube pair
+# ----------------------------------------------------------------------------
+def box_penetration_depth(RA, cA, eA, RB, cB, eB):
+    """Exact penetration depth of two boxes by the separating-axis theorem
+    over the 15 candidate axes (positive = overlap)."""
+    axes = [RA[:, i] for i in range(3)] + [RB[:, j] for j in range(3)]
+    for i in range(3):
+        for j in range(3):
+            c = np.cross(RA[:, i], RB[:, j])
+            nc = np.linalg.norm(c)
+            if nc > 1e-9:
+                axes.append(c / nc)
+    d = cB - cA
+    best = np.inf
+    for L in axes:
+        rA = np.sum(eA * np.abs(RA.T @ L))
+        rB = np.sum(eB * np.abs(RB.T @ L))
+        best = min(best, rA + rB - abs(d @ L))
+    return best
+
+
+def cube_pair_scene(seed=1, n_poses=64, depth_range=(0.0, 0.05), half=0.5):
+    """One pair of unit cubes under ``n_poses`` seeded relative poses.
+
+    Rotation of B uniform on SO(3); B is translated along a uniform random
+    direction until the exact (SAT) penetration depth equals delta ~ U(range),
+    by bisection on the distance (monotone for centred symmetric pairs); a
+    common random rigid motion is then applied to both bodies.
+    """
+    rng = np.random.default_rng(seed)
+    geom = geometry_from_bodies([[unit_cube_piece(half)], [unit_cube_piece(half)]])
+    RA = np.repeat(np.eye(3)[None], n_poses, 0)
+    RB = random_rotations(rng, n_poses)
+    u = random_unit_vectors(rng, n_poses)
+    delta = rng.uniform(*depth_range, size=n_poses)
+    e = np.full(3, half)
+    tA = np.zeros((n_poses, 3))
+    tB = np.zeros((n_poses, 3))
+    for i in range(n_poses):
+        lo, hi = 0.0, 4.0 * half * np.sqrt(3.0)
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            dep = box_penetration_depth(RA[i], np.zeros(3), e, RB[i], mid * u[i], e)
+            if dep > delta[i]:
+                lo = mid
+            else:
+                hi = mid
+        tB[i] = 0.5 * (lo + hi) * u[i]
+    RA, tA, RB, tB = _world_frame(rng, RA, tA, RB, tB)
+    return Scene(geom, np.zeros(n_poses, np.int64), np.ones(n_poses, np.int64),
+                 pack_pose(RA, tA), pack_pose(RB, tB),
+                 {"workload": "cube pair", "depth": delta, "seed": seed})
+
+
+# ----------------------------------------------------------------------------
+# configs: hull environments
+# ----------------------------------------------------------------------------
+def _random_hull_body(rng, n_pieces, n_points, centre_sigma=0.1, point_sigma=0.05):
+    pieces = []
+    for k in range(n_pieces):
+        c = rng.normal(0.0, centre_sigma, size=3)
+        m = int(n_points[k]) if np.ndim(n_points) else int(n_points)
+        pts = rng.normal(0.0, point_sigma, size=(m, 3)) + c
+        pieces.append(hull_piece(pts))
+    return pieces
+
+
+def _pad_body(pieces):
+    """Dense padded arrays of one body for the placement search."""
+    P = len(pieces)
+    Vm = max(len(p[0]) for p in pieces)
+    Fm = max(len(p[1]) for p in pieces)
+    V = np.zeros((P, Vm, 3))
+    F = np.zeros((P, Fm, 4))
+    F[:, :, 3] = -np.inf          # padded plane never binds (value -inf)
+    for i, (v, f, _) in enumerate(pieces):
+        V[i, :len(v)] = v
+        V[i, len(v):] = v[0]      # padded vertex duplicates a real one
+        F[i, :len(f)] = f
+    return V, F
+
+
+def _sup_contact_offset(VF, FS, RF, RS, u_w, target):
+    """Largest s such that some vertex of body F, translated by s*u_w in world,
+    lies at max-plane value <= -target inside some piece of body S.
+
+    For a fixed (piece a, vertex v) the max-plane value along the ray is the
+    convex piecewise-linear function max_k (c_k + s d_k); its sublevel set
+    {<= -target} is an interval whose upper end is min over d_k > 0 of
+    (-target - c_k)/d_k.  Returns -inf if no vertex ever reaches the level.
+    """
+    # vertices of F in S frame at s = 0, and the motion direction in S frame
+    x0 = np.einsum("ij,pvj->pvi", RS.T @ RF, VF)           # [PF, V, 3]
+    du = RS.T @ u_w                                          # [3]
+    n = FS[..., :3]                                          # [PS, F, 3]
+    h = FS[..., 3]
+    c = np.einsum("afk,pvk->apvf", n, x0) + h[:, None, None, :]   # [PS,PF,V,F]
+    d = np.einsum("afk,k->af", n, du)[:, None, None, :] * np.ones_like(c)
+    lvl = -target
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = (lvl - c) / d
+        hi = np.where(d > 0, r, np.inf).min(-1)
+        lo = np.where(d < 0, r, -np.inf).max(-1)
+        ok0 = np.where(d == 0, c <= lvl, True).all(-1)
+    feas = ok0 & (lo <= hi) & np.isfinite(hi)
+    if not feas.any():
+        return -np.inf
+    return hi[feas].max()
+
+
+def _place_pair(rng_dir, bodyA, bodyB, RA, RB, target):
+    """World translation of B (A at the origin) so that the deepest
+    vertex-in-piece max-plane depth equals ``target`` (negative = gap)."""
+    VA, FA = bodyA
+    VB, FB = bodyB
+    u = rng_dir
+    sB = _sup_contact_offset(VB, FA, RB, RA, u, target)     # B's vertices in A
+    sA = _sup_contact_offset(VA, FB, RA, RB, -u, target)    # A's vertices in B
+    s = max(sB, sA)
+    return s * u
+
+
+def _make_env(args):
+    """One environment from its own seed stream (independent of batching)."""
+    seed, e, pieces, npts_spec, sep_frac, depth_range, gap_range = args
+    rng = np.random.default_rng([seed, e])
+    bodies = []
+    for s in range(2):
+        P = int(pieces[s])
+        if npts_spec[0] == "fixed":
+            npts = np.full(P, int(npts_spec[1]))
+        else:
+            npts = log_uniform_int(rng, npts_spec[1], npts_spec[2], size=P)
+        bodies.append(_random_hull_body(rng, P, npts))
+    RA = random_rotations(rng, 1)[0]
+    RB = random_rotations(rng, 1)[0]
+    u = random_unit_vectors(rng, 1)[0]
+    separated = bool(rng.uniform() < sep_frac)
+    target = -rng.uniform(*gap_range) if separated else rng.uniform(*depth_range)
+    tB = _place_pair(u, _pad_body(bodies[0]), _pad_body(bodies[1]), RA, RB, target)
+    RA2, tA2, RB2, tB2 = _world_frame(rng, RA[None], np.zeros((1, 3)), RB[None], tB[None])
+    return bodies, RA2[0], tA2[0], RB2[0], tB2[0], target, separated
+
+
+def _map_envs(jobs, workers):
+    if workers is None:
+        import os
+        workers = min(len(os.sched_getaffinity(0)), 32)
+    if workers <= 1 or len(jobs) < 64:
+        return [_make_env(j) for j in jobs]
+    import multiprocessing as mp
+    # spawn: never fork a process that may already hold a CUDA context
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_make_env, jobs, chunksize=max(1, len(jobs) // (8 * workers)))
+
+
+def hull_env_scene(seed=2, n_envs=4096, pieces_per_body=8, points_per_hull=64,
+                   sep_frac=0.3, depth_range=(0.0, 0.02), gap_range=(0.0, 0.02),
+                   workers=None):
+    """``n_envs`` environments of two bodies with ``pieces_per_body`` pieces.
+
+    Each piece is the hull of ``points_per_hull`` points N(c, 0.05^2), with the
+    piece centre c ~ N(0, 0.1^2) per axis.  Bodies get uniform rotations; B is
+    translated along a uniform direction so that the deepest vertex-in-piece
+    max-plane depth is delta ~ U(depth_range) (70 %) or -g, g ~ U(gap_range)
+    (30 %, separated); a common random rigid motion is applied to both.
+    Every environment draws from its own seed stream ``(seed, env)``, so a
+    scene does not depend on how many worker processes generated it.
+    ``points_per_hull`` is an int or ``("log-uniform", lo, hi)``.
+    """
+    if np.ndim(pieces_per_body) == 0:
+        pieces = np.full((n_envs, 2), int(pieces_per_body), np.int64)
+    else:
+        pieces = np.asarray(pieces_per_body, np.int64).reshape(n_envs, 2)
+    spec = ("fixed", int(points_per_hull)) if np.ndim(points_per_hull) == 0 \
+        else tuple(points_per_hull)
+    jobs = [(seed, e, tuple(pieces[e]), spec, sep_frac, depth_range, gap_range)
+            for e in range(n_envs)]
+    res = _map_envs(jobs, workers)
+    bodies = [b for r in res for b in r[0]]
+    geom = geometry_from_bodies(bodies)
+    RA = np.stack([r[1] for r in res])
+    tA = np.stack([r[2] for r in res])
+    RB = np.stack([r[3] for r in res])
+    tB = np.stack([r[4] for r in res])
+    pa = np.arange(0, 2 * n_envs, 2, dtype=np.int64)
+    return Scene(geom, pa, pa + 1, pack_pose(RA, tA), pack_pose(RB, tB),
+                 {"workload": "hull envs", "seed": seed,
+                  "target_depth": np.array([r[5] for r in res]),
+                  "separated": np.array([r[6] for r in res])})
+
+
+def uneven_scene(seed=4, n_pairs=65536, max_pieces=64, min_points=8, max_points=512,
+                 workers=None):
+    """Uneven batch: pieces per body log-uniform in [1, max_pieces], hull
+    points per piece log-uniform in [min_points, max_points], same hull
+    generation and placement as ``hull_env_scene``."""
+    rng = np.random.default_rng(seed)
+    pieces = log_uniform_int(rng, 1, max_pieces, size=(n_pairs, 2))
+    sc = hull_env_scene(seed=seed, n_envs=n_pairs, pieces_per_body=pieces,
+                        points_per_hull=("log-uniform", min_points, max_points),
+                        workers=workers)
+    sc.meta["workload"] = "uneven"
+    sc.meta["seed"] = seed
+    return sc
