@@ -1,0 +1,178 @@
+/*
+ * ccm.h -- C ABI of the B300-native contact-manifold library.
+ *
+ * One-shot smooth contact manifolds between rigid bodies that are decomposed
+ * into convex pieces (arxiv 2604.17538, Sec. 4).  For every body pair and every
+ * pair of convex pieces the library runs an exact broad-phase cull and the
+ * smooth gate of Sec. 4.3, evaluates vertex-SDF and sphere-traced edge-SDF
+ * contacts (Sec. 4.2) against each piece's smooth polytope SDF (Sec. 3: LSE
+ * over the half-space SDFs of the piece), and blends the contacts of each
+ * convex piece into one contact (Sec. 4.4, N_1 + N_2 contacts per body pair).
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only; nothing throws across the ABI.  On failure
+ *     ccm_last_error() returns a message for the calling thread.
+ *   - Pointers documented as "device" must be device memory of the context's
+ *     GPU; "host" pointers are read before the call returns.
+ *   - Asynchronous entry points enqueue work on the given stream, never
+ *     synchronize and never allocate; an asynchronous CUDA error surfaces as
+ *     CCM_ERR_CUDA from a later call.
+ *   - Poses are float32 rows of 12: row-major R (9) then t (3), mapping body
+ *     frame to world (x_w = R x + t).
+ *   - Group outputs are float32 rows of 8: (d, a, p_x, p_y, p_z, n_x, n_y, n_z)
+ *     = blended signed depth, blend weight, world contact point, world unit
+ *     normal (pointing out of the SDF body).  Pair i owns the groups
+ *     [off[i], off[i+1]): first one per piece of body A (A's vertices and
+ *     edges against B's pieces), then one per piece of body B.  A group with
+ *     no active contact is (d_max, 0, 0, 0, 0, 0, 0, 0).
+ *   - Twist coordinates of a pair (derivatives): (w_A, v_A, w_B, v_B), with
+ *     R_X <- Exp([w_X]x) R_X, t_X <- t_X + v_X.
+ */
+#ifndef CCM_H_
+#define CCM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CCM_API __attribute__((visibility("default")))
+#else
+#define CCM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccm_ctx_s* ccm_ctx;
+typedef struct ccm_batch_s* ccm_batch;
+typedef uint64_t ccm_geom;     /* handle of one resident body */
+typedef uint64_t ccm_ticket;   /* handle of one submitted request */
+typedef void* ccm_stream;      /* a cudaStream_t (0 = legacy default stream) */
+
+typedef enum {
+  CCM_OK = 0,
+  CCM_ERR_INVALID = 1,        /* bad argument, bad geometry or bad handle */
+  CCM_ERR_OOM = 2,            /* device allocation or memory budget exceeded */
+  CCM_ERR_CUDA = 3,           /* CUDA runtime error (message has the detail) */
+  CCM_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out */
+  CCM_ERR_BUSY = 5,           /* request not admitted now; retry later */
+  CCM_ERR_NOT_READY = 6,      /* request still in flight */
+  CCM_ERR_UNKNOWN_TICKET = 7  /* ticket never issued or already retired */
+} ccm_status;
+
+/* Flags of ccm_params.flags */
+#define CCM_FLAG_NO_CULL 1u   /* evaluate every feature (culls are exact; for tests) */
+
+/* Method constants.  The paper fixes none of these values (Sec. 2-4). */
+typedef struct {
+  float tau_sdf;      /* LSE softness of the piece SDF (Sec. 3, Eq. smooth-intersection) */
+  float tau_trace;    /* softness of the sphere-trace gate [[phi > 0]] (Sec. 4.2) */
+  float tau_clip;     /* softness of the edge soft clip (Sec. 2, 4.2) */
+  float tau_blend;    /* softmax temperature of the contact blend (Sec. 4.4) */
+  float d_max;        /* distance threshold of the broad phase (Sec. 4.3) */
+  float gate_width;   /* transition bandwidth epsilon > 0 (Sec. 4.3) */
+  int32_t trace_iters;/* sphere-trace iterations, 0..16 (three in Sec. 4.2) */
+  uint32_t flags;     /* CCM_FLAG_* */
+} ccm_params;
+
+/* Fills *p with the defaults: all softness 5e-3, d_max = 0.01, epsilon = 0.01,
+ * 3 trace iterations, no flags. */
+CCM_API void ccm_default_params(ccm_params* p);
+
+/* Host description of one body: n_pieces convex pieces, each with nv[i]
+ * vertices (xyz), nf[i] face planes (n_x, n_y, n_z, h; n unit outward, so
+ * n.x + h < 0 inside, Sec. 3 half-space SDF) and ne[i] edges (pairs of
+ * piece-local vertex indices).  Arrays are concatenated over the pieces. */
+typedef struct {
+  int32_t n_pieces;
+  const int32_t* nv;
+  const int32_t* nf;
+  const int32_t* ne;
+  const float* verts;      /* [sum nv, 3] */
+  const float* planes;     /* [sum nf, 4] */
+  const int32_t* edges;    /* [sum ne, 2] */
+} ccm_body_desc;
+
+/* Creates a context on CUDA device `device`.  `hbm_budget_bytes` bounds the
+ * device memory the serving loop may admit (0 = no bound).  Errors:
+ * CCM_ERR_INVALID (no such device), CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_create(int device, size_t hbm_budget_bytes, ccm_ctx* out);
+
+/* Releases every device resource of the context (waits for its work). */
+CCM_API void ccm_destroy(ccm_ctx ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+CCM_API const char* ccm_last_error(void);
+
+/* Copies n_bodies bodies into device memory owned by the context and returns
+ * one handle per body in out[n_bodies] (host).  Limits: 1..4096 pieces per
+ * body, 1..1024 vertices, 4..1024 planes and 0..3072 edges per piece; edge
+ * indices must be valid and edges of non-zero length.  Synchronous.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bodies,
+                             ccm_geom* out);
+
+/* Marks bodies as released: later calls reject their handles.  Batches that
+ * were planned before keep working.  Device memory of released bodies is
+ * returned when the context is destroyed.  Errors: CCM_ERR_INVALID. */
+CCM_API ccm_status ccm_free_geometry(ccm_ctx ctx, const ccm_geom* handles, int n);
+
+/* Number of output groups of the n pairs (A[i], B[i]) (host arrays):
+ * sum over pairs of (pieces of A[i] + pieces of B[i]). */
+CCM_API ccm_status ccm_output_size(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
+                           int64_t* groups);
+
+/* Plans a batch of n body pairs (A[i], B[i]) (host arrays): uploads the pair
+ * table and the group offsets and picks the launch shape.  The batch is the
+ * unit that ccm_contacts and ccm_contacts_backward run on; poses change
+ * between calls, pairs do not.  Synchronous; allocates.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_batch_create(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
+                            ccm_batch* out);
+CCM_API void ccm_batch_destroy(ccm_batch batch);
+
+/* Number of pairs and of groups of a batch, and (if off != NULL) the group
+ * offsets off[n+1] copied to host memory. */
+CCM_API ccm_status ccm_batch_info(ccm_batch batch, int64_t* n_pairs, int64_t* n_groups, int64_t* off);
+
+/* Forward pass (Sec. 4.2-4.4).  pose_a, pose_b: device [n,12] float32; y:
+ * device [G,8] float32, fully overwritten.  Asynchronous on `stream`.
+ * Errors: CCM_ERR_INVALID (NULL pointer, bad params), CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
+                        const ccm_params* prm, float* y, ccm_stream stream);
+
+/* Reverse pass.  Given the cotangent ybar (device [G,8]) of the outputs, writes
+ * grad (device [n,12]) = d<ybar, y>/d(twist) at twist = 0.  If dir (device
+ * [n,12]) is given, also writes hvp (device [n,12]) = H dir, the Hessian of
+ * <ybar, y> in the twist chart applied to dir, and, if jvp != NULL, the output
+ * tangents jvp (device [G,8]) = (dy/dtwist) dir.  The per-vertex SDF is
+ * recomputed, not stored.  Asynchronous; allocates nothing.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                 const ccm_params* prm, const float* ybar, const float* dir,
+                                 float* grad, float* hvp, float* jvp, ccm_stream stream);
+
+/* Work counters of the last ccm_contacts_counted call, for the roofline:
+ * counts of piece-pair directions, surviving directions, plane evaluations by
+ * kind and contacts.  Same as ccm_contacts plus device atomics on `counters`
+ * (device, CCM_N_COUNTERS int64, zeroed by the caller). */
+#define CCM_N_COUNTERS 8
+enum {
+  CCM_CNT_DIRS = 0,        /* (SDF piece, feature piece) directions examined */
+  CCM_CNT_DIRS_LIVE = 1,   /* directions that passed the piece-pair gate */
+  CCM_CNT_MAXPASS = 2,     /* plane evaluations of the vertex max pass */
+  CCM_CNT_GATEPASS = 3,    /* plane evaluations of the piece-pair gate */
+  CCM_CNT_EVAL_GRAD = 4,   /* plane evaluations with exp and gradient */
+  CCM_CNT_EVAL_VAL = 5,    /* plane evaluations with exp, value only */
+  CCM_CNT_CONTACTS = 6,    /* contacts with a non-zero weight */
+  CCM_CNT_FEATURES = 7     /* features examined (vertices + edges) */
+};
+CCM_API ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                const ccm_params* prm, float* y, int64_t* counters,
+                                ccm_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCM_H_ */

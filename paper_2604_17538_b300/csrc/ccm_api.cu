@@ -1,0 +1,493 @@
+// Host side of the C ABI declared in include/ccm.h: contexts, resident
+// geometry, batches (pair plans) and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ccm.h"
+#include "ccm_device.cuh"
+#include "ccm_host.h"
+
+namespace ccm {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+ccm_status fail(ccm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+ccm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CCM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CCM_CUDA(call, what)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+template <class T>
+static ccm_status upload(DevBuf& b, const std::vector<T>& h, const char* what) {
+  const size_t bytes = h.size() * sizeof(T);
+  if (bytes > b.bytes) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.ptr, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) return fail(CCM_ERR_OOM, "%s: cudaMalloc(%zu): %s", what, bytes,
+                                      cudaGetErrorString(e));
+    b.bytes = std::max<size_t>(bytes, 256);
+  }
+  if (bytes) CCM_CUDA(cudaMemcpy(b.ptr, h.data(), bytes, cudaMemcpyHostToDevice), what);
+  return CCM_OK;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+DevGeom Context::dev_geom() const {
+  DevGeom g;
+  g.pieces = static_cast<const PieceRec*>(d_pieces.ptr);
+  g.bodies = static_cast<const BodyRec*>(d_bodies.ptr);
+  g.verts = static_cast<const float4*>(d_verts.ptr);
+  g.planes = static_cast<const float4*>(d_planes.ptr);
+  g.edges = static_cast<const uint32_t*>(d_edges.ptr);
+  return g;
+}
+
+ccm_status Context::body_of(ccm_geom h, int32_t* idx) const {
+  if (h == 0 || h > bodies.size()) return fail(CCM_ERR_INVALID, "unknown geometry handle %llu",
+                                               (unsigned long long)h);
+  if (!alive[h - 1]) return fail(CCM_ERR_INVALID, "geometry handle %llu was released",
+                                 (unsigned long long)h);
+  *idx = (int32_t)(h - 1);
+  return CCM_OK;
+}
+
+ccm_status make_kparams(const ccm_params* p, KParams* k) {
+  if (!p) return fail(CCM_ERR_INVALID, "params is NULL");
+  const float taus[4] = {p->tau_sdf, p->tau_trace, p->tau_clip, p->tau_blend};
+  for (float t : taus)
+    if (!(t > 0.f) || !std::isfinite(t)) return fail(CCM_ERR_INVALID, "softness must be > 0");
+  if (!(p->gate_width > 0.f) || !std::isfinite(p->gate_width) || !std::isfinite(p->d_max))
+    return fail(CCM_ERR_INVALID, "gate_width must be > 0 and d_max finite");
+  if (p->trace_iters < 0 || p->trace_iters > 16)
+    return fail(CCM_ERR_INVALID, "trace_iters must be in [0, 16]");
+  k->tau_sdf = p->tau_sdf;
+  k->tau_trace = p->tau_trace;
+  k->tau_clip = p->tau_clip;
+  k->tau_blend = p->tau_blend;
+  k->d_max = p->d_max;
+  k->gate_width = p->gate_width;
+  k->trace_iters = p->trace_iters;
+  k->flags = p->flags;
+  k->c_sdf = (float)(1.4426950408889634 / p->tau_sdf);
+  k->ic_sdf = 1.0f / k->c_sdf;
+  k->c_trace = (float)(1.4426950408889634 / p->tau_trace);
+  k->c_clip = (float)(1.4426950408889634 / p->tau_clip);
+  k->c_blend = (float)(1.4426950408889634 / p->tau_blend);
+  k->inv_gate = (float)(1.0 / p->gate_width);
+  return CCM_OK;
+}
+
+}  // namespace ccm
+
+using namespace ccm;
+
+extern "C" {
+
+const char* ccm_last_error(void) { return g_err.c_str(); }
+
+void ccm_default_params(ccm_params* p) {
+  if (!p) return;
+  p->tau_sdf = p->tau_trace = p->tau_clip = p->tau_blend = 5e-3f;
+  p->d_max = 0.01f;
+  p->gate_width = 0.01f;
+  p->trace_iters = 3;
+  p->flags = 0;
+}
+
+ccm_status ccm_create(int device, size_t hbm_budget_bytes, ccm_ctx* out) {
+  if (!out) return fail(CCM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(CCM_ERR_INVALID, "no CUDA device %d", device);
+  CCM_CUDA(cudaSetDevice(device), "cudaSetDevice");
+  Context* c = new Context();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  cudaDeviceProp prop;
+  CCM_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  c->n_sm = prop.multiProcessorCount;
+  c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  *out = reinterpret_cast<ccm_ctx>(c);
+  return CCM_OK;
+}
+
+void ccm_destroy(ccm_ctx ctx) {
+  if (!ctx) return;
+  Context* c = reinterpret_cast<Context*>(ctx);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  c->shutdown_serving();
+  c->d_pieces.release();
+  c->d_bodies.release();
+  c->d_verts.release();
+  c->d_planes.release();
+  c->d_edges.release();
+  delete c;
+}
+
+ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bodies,
+                             ccm_geom* out) {
+  if (!ctx || !bodies || !out || n_bodies < 0) return fail(CCM_ERR_INVALID, "bad arguments");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+  // validate everything before touching the context
+  for (int b = 0; b < n_bodies; ++b) {
+    const ccm_body_desc& d = bodies[b];
+    if (d.n_pieces < 1 || d.n_pieces > 4096)
+      return fail(CCM_ERR_INVALID, "body %d: n_pieces=%d outside [1, 4096]", b, d.n_pieces);
+    if (!d.nv || !d.nf || !d.ne || !d.verts || !d.planes || (!d.edges))
+      return fail(CCM_ERR_INVALID, "body %d: NULL array", b);
+    int64_t vo = 0, eo = 0, fo = 0;
+    for (int p = 0; p < d.n_pieces; ++p) {
+      const int nv = d.nv[p], nf = d.nf[p], ne = d.ne[p];
+      if (nv < 1 || nv > 1024 || nf < 1 || nf > 1024 || ne < 0 || ne > 3072)
+        return fail(CCM_ERR_INVALID, "body %d piece %d: sizes (%d, %d, %d) out of range", b, p,
+                    nv, nf, ne);
+      for (int64_t i = 0; i < 3 * (int64_t)nv; ++i)
+        if (!std::isfinite(d.verts[3 * vo + i]))
+          return fail(CCM_ERR_INVALID, "body %d piece %d: non-finite vertex", b, p);
+      for (int64_t i = 0; i < 4 * (int64_t)nf; ++i)
+        if (!std::isfinite(d.planes[4 * fo + i]))
+          return fail(CCM_ERR_INVALID, "body %d piece %d: non-finite plane", b, p);
+      for (int j = 0; j < ne; ++j) {
+        const int i0 = d.edges[2 * (eo + j)], i1 = d.edges[2 * (eo + j) + 1];
+        if (i0 < 0 || i1 < 0 || i0 >= nv || i1 >= nv || i0 == i1)
+          return fail(CCM_ERR_INVALID, "body %d piece %d edge %d: bad indices", b, p, j);
+        const float* a = d.verts + 3 * (vo + i0);
+        const float* q = d.verts + 3 * (vo + i1);
+        const double L = std::sqrt((double)(q[0] - a[0]) * (q[0] - a[0]) +
+                                   (double)(q[1] - a[1]) * (q[1] - a[1]) +
+                                   (double)(q[2] - a[2]) * (q[2] - a[2]));
+        if (!(L > 1e-12)) return fail(CCM_ERR_INVALID, "body %d piece %d edge %d: zero length", b, p, j);
+      }
+      vo += nv; fo += nf; eo += ne;
+    }
+  }
+  for (int b = 0; b < n_bodies; ++b) {
+    const ccm_body_desc& d = bodies[b];
+    BodyRec br;
+    br.p0 = (int32_t)c->pieces.size();
+    br.np = d.n_pieces;
+    int64_t vo = 0, eo = 0, fo = 0;
+    for (int p = 0; p < d.n_pieces; ++p) {
+      const int nv = d.nv[p], nf = d.nf[p], ne = d.ne[p];
+      PieceRec pr;
+      pr.v0 = (int32_t)c->verts.size();
+      pr.nv = nv;
+      pr.f0 = (int32_t)c->planes.size();
+      pr.nf = nf;
+      pr.e0 = (int32_t)c->edges.size();
+      pr.ne = ne;
+      pr.body = (int32_t)c->bodies.size();
+      pr.pad = 0;
+      double cx = 0, cy = 0, cz = 0;
+      for (int i = 0; i < nv; ++i) {
+        const float* v = d.verts + 3 * (vo + i);
+        c->verts.push_back(make_float4(v[0], v[1], v[2], 0.f));
+        cx += v[0]; cy += v[1]; cz += v[2];
+      }
+      cx /= nv; cy /= nv; cz /= nv;
+      const float fcx = (float)cx, fcy = (float)cy, fcz = (float)cz;
+      double r = 0;
+      for (int i = 0; i < nv; ++i) {
+        const float* v = d.verts + 3 * (vo + i);
+        const double dx = v[0] - (double)fcx, dy = v[1] - (double)fcy, dz = v[2] - (double)fcz;
+        r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz));
+      }
+      // a slightly inflated radius keeps the float32 gate conservative
+      pr.sphere = make_float4(fcx, fcy, fcz, (float)(r * (1.0 + 1e-5) + 1e-7));
+      for (int k = 0; k < nf; ++k) {
+        const float* q = d.planes + 4 * (fo + k);
+        c->planes.push_back(make_float4(q[0], q[1], q[2], q[3]));
+      }
+      for (int j = 0; j < ne; ++j) {
+        const uint32_t i0 = (uint32_t)d.edges[2 * (eo + j)], i1 = (uint32_t)d.edges[2 * (eo + j) + 1];
+        c->edges.push_back(i0 | (i1 << 16));
+      }
+      c->pieces.push_back(pr);
+      vo += nv; fo += nf; eo += ne;
+    }
+    c->bodies.push_back(br);
+    c->alive.push_back(1);
+    out[b] = (ccm_geom)c->bodies.size();
+  }
+  // resident copy (uploads happen while no batch kernel can be in flight:
+  // loads are synchronous with the device)
+  CCM_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  ccm_status s;
+  if ((s = upload(c->d_pieces, c->pieces, "pieces")) != CCM_OK) return s;
+  if ((s = upload(c->d_bodies, c->bodies, "bodies")) != CCM_OK) return s;
+  if ((s = upload(c->d_verts, c->verts, "verts")) != CCM_OK) return s;
+  if ((s = upload(c->d_planes, c->planes, "planes")) != CCM_OK) return s;
+  if ((s = upload(c->d_edges, c->edges, "edges")) != CCM_OK) return s;
+  return CCM_OK;
+}
+
+ccm_status ccm_free_geometry(ccm_ctx ctx, const ccm_geom* handles, int n) {
+  if (!ctx || (!handles && n > 0)) return fail(CCM_ERR_INVALID, "bad arguments");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (int i = 0; i < n; ++i) {
+    int32_t b;
+    ccm_status s = c->body_of(handles[i], &b);
+    if (s != CCM_OK) return s;
+  }
+  for (int i = 0; i < n; ++i) c->alive[handles[i] - 1] = 0;
+  return CCM_OK;
+}
+
+ccm_status ccm_output_size(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
+                           int64_t* groups) {
+  if (!ctx || n < 0 || (n > 0 && (!A || !B)) || !groups) return fail(CCM_ERR_INVALID, "bad arguments");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  int64_t G = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t a, b;
+    ccm_status s;
+    if ((s = c->body_of(A[i], &a)) != CCM_OK || (s = c->body_of(B[i], &b)) != CCM_OK) return s;
+    G += c->bodies[a].np + c->bodies[b].np;
+  }
+  *groups = G;
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_create(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
+                            ccm_batch* out) {
+  if (!ctx || n < 0 || (n > 0 && (!A || !B)) || !out) return fail(CCM_ERR_INVALID, "bad arguments");
+  if (n > (int64_t)1 << 30) return fail(CCM_ERR_INVALID, "too many pairs");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  *out = nullptr;
+  Batch* bt = new Batch();
+  bt->ctx = c;
+  bt->n = n;
+  ccm_status s = build_batch(c, n, A, B, bt);
+  if (s != CCM_OK) {
+    bt->release();
+    delete bt;
+    return s;
+  }
+  *out = reinterpret_cast<ccm_batch>(bt);
+  return CCM_OK;
+}
+
+void ccm_batch_destroy(ccm_batch batch) {
+  if (!batch) return;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  cudaSetDevice(b->ctx->device);
+  b->release();
+  delete b;
+}
+
+ccm_status ccm_batch_info(ccm_batch batch, int64_t* n_pairs, int64_t* n_groups, int64_t* off) {
+  if (!batch) return fail(CCM_ERR_INVALID, "batch is NULL");
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (n_pairs) *n_pairs = b->n;
+  if (n_groups) *n_groups = b->G;
+  if (off) std::memcpy(off, b->goff.data(), sizeof(int64_t) * (b->n + 1));
+  return CCM_OK;
+}
+
+ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
+                        const ccm_params* prm, float* y, ccm_stream stream) {
+  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                 const ccm_params* prm, const float* ybar, const float* dir,
+                                 float* grad, float* hvp, float* jvp, ccm_stream stream) {
+  return run_backward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, ybar, dir, grad, hvp,
+                      jvp, static_cast<cudaStream_t>(stream));
+}
+
+ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                const ccm_params* prm, float* y, int64_t* counters,
+                                ccm_stream stream) {
+  if (!counters) return fail(CCM_ERR_INVALID, "counters is NULL");
+  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y,
+                     reinterpret_cast<unsigned long long*>(counters),
+                     static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace ccm {
+
+ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom* B, Batch* bt) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+  std::vector<PairRec> pairs(n);
+  bt->goff.assign(n + 1, 0);
+  int64_t G = 0;
+  int vmax = 1, fmax = 1, emax = 1, s_planes = 1, s_pieces = 1, f_verts = 1, f_edges = 1;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t a, b;
+    ccm_status s;
+    if ((s = c->body_of(A[i], &a)) != CCM_OK || (s = c->body_of(B[i], &b)) != CCM_OK) return s;
+    pairs[i].bodyA = a;
+    pairs[i].bodyB = b;
+    pairs[i].goff = G;
+    bt->goff[i] = G;
+    G += c->bodies[a].np + c->bodies[b].np;
+  }
+  bt->goff[n] = G;
+  bt->G = G;
+  // budgets of the per-warp shared-memory slice, from the bodies in the batch
+  std::vector<uint8_t> seen(c->bodies.size(), 0);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int32_t bi : {pairs[i].bodyA, pairs[i].bodyB}) {
+      if (seen[bi]) continue;
+      seen[bi] = 1;
+      const BodyRec& br = c->bodies[bi];
+      int sp = 0, cv = 0, ce = 0;
+      for (int p = 0; p < br.np; ++p) {
+        const PieceRec& pr = c->pieces[br.p0 + p];
+        vmax = std::max(vmax, pr.nv);
+        fmax = std::max(fmax, pr.nf);
+        emax = std::max(emax, pr.ne);
+        sp += pr.nf;
+        if (p < kGroupsPerChunk) { cv += pr.nv; ce += pr.ne; }
+      }
+      s_planes = std::max(s_planes, sp);
+      s_pieces = std::max(s_pieces, br.np);
+      f_verts = std::max(f_verts, cv);
+      f_edges = std::max(f_edges, ce);
+    }
+  }
+  UnitShape us{};
+  us.plane_budget = std::max(fmax, std::min(s_planes, 1024));
+  us.spiece_budget = std::min(s_pieces, 256);
+  us.vert_budget = std::max(vmax, std::min(f_verts, 512));
+  us.edge_budget = std::max(emax, std::min(f_edges, 1536));
+  us.item_v = std::max(vmax, 256);
+  us.item_e = std::max(emax, 512);
+  us.slice_bytes = unit_slice_bytes(us);
+  us.warps = 2;
+  if (us.warps * us.slice_bytes > c->smem_optin) us.warps = 1;
+  if (us.slice_bytes > c->smem_optin)
+    return fail(CCM_ERR_INVALID, "pieces too large: %d bytes of shared memory per warp",
+                us.slice_bytes);
+  bt->us = us;
+  ccm_status s;
+  if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
+  int per_sm = 1;
+  cudaError_t e = configure_forward(us, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "configure_forward");
+  const int64_t units = 2 * n;
+  bt->grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((units + us.warps - 1) / us.warps, (int64_t)c->n_sm * std::max(1, per_sm)));
+  // reverse pass: one warp per block, its own slice layout
+  if (backward_slice_bytes(us, true) > c->smem_optin)
+    return fail(CCM_ERR_INVALID, "pieces too large for the reverse pass");
+  int per_f = 1, per_d = 1;
+  e = configure_backward(us, &per_f, &per_d);
+  if (e != cudaSuccess) return cuda_fail(e, "configure_backward");
+  bt->bwd_grid_f = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_f)));
+  bt->bwd_grid_d = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_d)));
+  std::vector<float> zeros_part((size_t)std::max<int64_t>(1, units) * 24, 0.f);
+  if ((s = upload(bt->d_part, zeros_part, "reverse-pass slots")) != CCM_OK) return s;
+  return CCM_OK;
+}
+
+ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
+                        const float* ybar, const float* dir, float* grad, float* hvp, float* jvp,
+                        cudaStream_t stream) {
+  if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
+  if (b->n == 0) return CCM_OK;
+  if (!pose_a || !pose_b || !ybar || !grad) return fail(CCM_ERR_INVALID, "NULL pointer");
+  if (dir && !hvp) return fail(CCM_ERR_INVALID, "dir given without hvp");
+  KParams kp;
+  ccm_status s = make_kparams(prm, &kp);
+  if (s != CCM_OK) return s;
+  if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
+  CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  BwdLaunch L;
+  L.g = b->ctx->dev_geom();
+  L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.n_pairs = b->n;
+  L.pose_a = pose_a;
+  L.pose_b = pose_b;
+  L.ybar = ybar;
+  L.dir = dir;
+  L.kp = kp;
+  L.us = b->us;
+  L.part = static_cast<float*>(b->d_part.ptr);
+  L.grad = grad;
+  L.hvp = hvp;
+  L.jvp = dir ? jvp : nullptr;
+  L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
+  cudaError_t e = launch_backward(L, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return CCM_OK;
+}
+
+void Batch::release() {
+  d_pairs.release();
+  d_part.release();
+}
+
+ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
+                       float* y, unsigned long long* counters, cudaStream_t stream) {
+  if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
+  if (b->n == 0) return CCM_OK;
+  if (!pose_a || !pose_b || !y) return fail(CCM_ERR_INVALID, "NULL pose or output pointer");
+  KParams kp;
+  ccm_status s = make_kparams(prm, &kp);
+  if (s != CCM_OK) return s;
+  CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  FwdLaunch L;
+  L.g = b->ctx->dev_geom();
+  L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.n_pairs = b->n;
+  L.pose_a = pose_a;
+  L.pose_b = pose_b;
+  L.kp = kp;
+  L.us = b->us;
+  L.y = y;
+  L.counters = counters;
+  L.grid = b->grid;
+  cudaError_t e = launch_forward(L, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return CCM_OK;
+}
+
+}  // namespace ccm

@@ -1,0 +1,909 @@
+// Reverse pass of the contact manifold (Sec. 4.2-4.4 of arxiv 2604.17538):
+// a hand-written adjoint, templated on the scalar type.  With T = float it
+// gives the gradient of L = <ybar, y> with respect to the twists of the two
+// poses; with T = Dual (poses seeded with the tangent of a direction u) the
+// same code yields, forward-over-reverse, H u and the output tangents J u.
+//
+// One warp runs one unit (pair, side) like the forward kernel and re-derives
+// everything it needs -- the per-vertex SDF is recomputed, never stored:
+//   pass 1  recomputes the blends of the unit's groups (online softmax);
+//   then    each group's adjoint coefficients are formed from ybar;
+//   pass 2  recomputes every contact and back-propagates through the blend,
+//           the mollifier (Sec. 4.3), the LSE SDF (its gradient and the
+//           Hessian-vector product (sum_k w_k n_k n_k^T - g g^T) v / tau),
+//           the soft clip, midpoint and sphere-trace steps of an edge
+//           (Sec. 4.2) into the feature points, whose adjoints x_bar are
+//           summed as sum x_bar and sum x cross x_bar in the SDF frame.
+// The unit's 12 twist components are written to a per-unit slot; a second
+// kernel adds the two sides of each pair in a fixed order (deterministic).
+#include "ccm_dual.cuh"
+#include "ccm_unit.cuh"
+#include "ccm_bwd.h"
+
+namespace ccm {
+
+constexpr int kMaxTrace = 16;
+
+// ---------------------------------------------------------------------------
+// scalar-generic smooth operators (Sec. 2) and transition (Sec. 4.3)
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T sigmoid_t(T x, float c) {
+  return rcp_t(1.0f + ex2_t(x * (-c)));
+}
+template <class T> __device__ __forceinline__ T softplus_t(T x, float tau, float c) {
+  return max_t(x, T(0.f)) + tau * log1p_t(ex2_t(abs_t(x) * (-c)));
+}
+template <class T> __device__ __forceinline__ T softclip0_t(T x, T L, float tau, float c) {
+  return softplus_t(x, tau, c) - softplus_t(x - L, tau, c);
+}
+// f_t and its derivative: quintic smoothstep of s = (d_max - d) / eps
+template <class T>
+__device__ __forceinline__ void transition_t(T d, const KParams& kp, T& f, T& fp) {
+  const float sv = (kp.d_max - val(d)) * kp.inv_gate;
+  if (sv <= 0.f) { f = T(0.f); fp = T(0.f); return; }
+  if (sv >= 1.f) { f = T(1.f); fp = T(0.f); return; }
+  const T s = (kp.d_max - d) * kp.inv_gate;
+  const T s2 = s * s;
+  f = s2 * s * fma_t(s, fma_t(s, T(6.f), T(-15.f)), T(10.f));
+  const T om = 1.0f - s;
+  fp = s2 * om * om * (-30.f * kp.inv_gate);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 piece SDF, value + gradient (+ Hessian-vector product) on T
+// ---------------------------------------------------------------------------
+template <class T> struct SdfT {
+  T phi;
+  V3T<T> g, hv;
+};
+
+template <class T, bool kHv>
+__device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float s, V3T<T> v,
+                         const KParams& kp) {
+  SdfT<T> r;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float sc = s * kp.c_sdf;
+    T S(0.f), gx(0.f), gy(0.f), gz(0.f), hx(0.f), hy(0.f), hz(0.f);
+    float mx = -INFINITY;
+#pragma unroll 2
+    for (int k = 0; k < nf; ++k) {
+      const float4 p = pl[k];
+      const T ph = fma_t(p.x, x.x, fma_t(p.y, x.y, fma_t(p.z, x.z, T(p.w))));
+      mx = fmaxf(mx, val(ph));
+      const T e = ex2_t(fma_t(ph, kp.c_sdf, T(-sc)));
+      S += e;
+      gx = fma_t(e, p.x, gx);
+      gy = fma_t(e, p.y, gy);
+      gz = fma_t(e, p.z, gz);
+      if (kHv) {
+        const T en = e * fma_t(p.x, v.x, fma_t(p.y, v.y, p.z * v.z));
+        hx = fma_t(en, p.x, hx);
+        hy = fma_t(en, p.y, hy);
+        hz = fma_t(en, p.z, hz);
+      }
+    }
+    if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
+    const T inv = rcp_t(S);
+    r.phi = fma_t(T(kp.ic_sdf), log2_t(S), T(s));
+    r.g = v3(gx * inv, gy * inv, gz * inv);
+    if (kHv) {
+      const T gv = dot3(r.g, v);
+      const float it = 1.0f / kp.tau_sdf;
+      r.hv = v3((hx * inv - r.g.x * gv) * it, (hy * inv - r.g.y * gv) * it,
+                (hz * inv - r.g.z * gv) * it);
+    }
+    break;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 4.4 blend partials on T (online softmax).  Besides the normaliser U a
+// partial keeps a reference contact r -- the one with the largest logit -- and
+// the weighted differences sum_j u_j (x_j - x_r) of every blended quantity
+// x = (d_c, f, p, grad phi), rather than the plain sums.  The adjoint needs
+// g_c - gbar for g = ybar . (contact values); formed from differences to r it
+// carries no cancellation, and it is exactly 0 for a group whose only active
+// contact is r (there 1/U = 1/f can be huge near the gate edge).
+// ---------------------------------------------------------------------------
+template <class T> struct PartT {
+  T M, U;
+  T rd, rf;          // reference contact: mollified depth, transition weight
+  V3T<T> rp, rn;     // reference point, gradient
+  T Dd, Da;          // sum u (d_c - rd), sum u (f - rf)
+  V3T<T> Dp, Dn;     // sum u (p - rp), sum u (grad phi - rn)
+};
+
+template <class T> __device__ __forceinline__ V3T<T> zero3t() { return v3(T(0.f), T(0.f), T(0.f)); }
+
+template <class T> __device__ __forceinline__ void part_zero(PartT<T>& c) {
+  c.M = T(-INFINITY);
+  c.U = c.rd = c.rf = c.Dd = c.Da = T(0.f);
+  c.rp = c.rn = c.Dp = c.Dn = zero3t<T>();
+}
+
+template <class T>
+__device__ __forceinline__ void part_from_contact(PartT<T>& c, T f, T dc, V3T<T> p, V3T<T> g,
+                                                  float c_blend) {
+  if (val(f) > 0.f) {
+    c.M = dc * (-c_blend);
+    c.U = f;
+    c.rd = dc;
+    c.rf = f;
+    c.rp = p;
+    c.rn = g;
+    c.Dd = c.Da = T(0.f);
+    c.Dp = c.Dn = zero3t<T>();
+  } else {
+    part_zero(c);
+  }
+}
+
+template <class T> __device__ __forceinline__ V3T<T> axpy3(T a, V3T<T> x, V3T<T> y) {
+  return v3(fma_t(a, x.x, y.x), fma_t(a, x.y, y.y), fma_t(a, x.z, y.z));
+}
+template <class T> __device__ __forceinline__ V3T<T> sub3(V3T<T> a, V3T<T> b) {
+  return v3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <class T> __device__ __forceinline__ V3T<T> scale3(T a, V3T<T> x) {
+  return v3(a * x.x, a * x.y, a * x.z);
+}
+
+// a <- a (+) b; the reference of the partial with the larger logit is kept
+// (a's on ties), the other's differences are re-based onto it
+template <class T> __device__ __forceinline__ void part_combine(PartT<T>& a, const PartT<T>& b) {
+  if (val(b.M) == -INFINITY) return;
+  if (val(a.M) == -INFINITY) { a = b; return; }
+  const bool keep_a = val(a.M) >= val(b.M);
+  const PartT<T>& H = keep_a ? a : b;   // keeps its reference
+  const PartT<T>& O = keep_a ? b : a;   // re-based
+  const T rO = ex2_t(O.M - H.M);
+  const T uO = O.U * rO;
+  PartT<T> r;
+  r.M = H.M;
+  r.rd = H.rd; r.rf = H.rf; r.rp = H.rp; r.rn = H.rn;
+  r.U = H.U + uO;
+  r.Dd = fma_t(rO, O.Dd, fma_t(uO, O.rd - H.rd, H.Dd));
+  r.Da = fma_t(rO, O.Da, fma_t(uO, O.rf - H.rf, H.Da));
+  r.Dp = axpy3(rO, O.Dp, axpy3(uO, sub3(O.rp, H.rp), H.Dp));
+  r.Dn = axpy3(rO, O.Dn, axpy3(uO, sub3(O.rn, H.rn), H.Dn));
+  a = r;
+}
+
+__device__ __forceinline__ float shfl_down_t(float v, int o) { return __shfl_down_sync(kFull, v, o); }
+__device__ __forceinline__ Dual shfl_down_t(Dual v, int o) {
+  return Dual(__shfl_down_sync(kFull, v.v, o), __shfl_down_sync(kFull, v.d, o));
+}
+__device__ __forceinline__ float shfl_xor_t(float v, int o) { return __shfl_xor_sync(kFull, v, o); }
+__device__ __forceinline__ Dual shfl_xor_t(Dual v, int o) {
+  return Dual(__shfl_xor_sync(kFull, v.v, o), __shfl_xor_sync(kFull, v.d, o));
+}
+template <class T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_t(v, o);
+  return v;
+}
+
+template <class T> __device__ __forceinline__ V3T<T> shfl_down3(V3T<T> x, int o) {
+  return v3(shfl_down_t(x.x, o), shfl_down_t(x.y, o), shfl_down_t(x.z, o));
+}
+template <class T> __device__ __forceinline__ PartT<T> part_shfl_down(const PartT<T>& c, int o) {
+  PartT<T> r;
+  r.M = shfl_down_t(c.M, o); r.U = shfl_down_t(c.U, o);
+  r.rd = shfl_down_t(c.rd, o); r.rf = shfl_down_t(c.rf, o);
+  r.rp = shfl_down3(c.rp, o); r.rn = shfl_down3(c.rn, o);
+  r.Dd = shfl_down_t(c.Dd, o); r.Da = shfl_down_t(c.Da, o);
+  r.Dp = shfl_down3(c.Dp, o); r.Dn = shfl_down3(c.Dn, o);
+  return r;
+}
+
+// segmented fold of lane contacts sorted by key into the group table
+template <class T>
+__device__ void fold_t(PartT<T> c, int key, PartT<T>* acc, int lane) {
+  const unsigned seg = __match_any_sync(kFull, key);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const PartT<T> b = part_shfl_down(c, o);
+    if (lane + o < 32 && ((seg >> (lane + o)) & 1u)) part_combine(c, b);
+  }
+  if ((__ffs(seg) - 1) == lane && key != 0xffff && val(c.M) != -INFINITY) {
+    PartT<T> g = acc[key];
+    part_combine(g, c);
+    acc[key] = g;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-group adjoint coefficients and the contact adjoint
+// ---------------------------------------------------------------------------
+template <class T> struct Coef {
+  T M, invU;           // log2 max logit, 1/U
+  T gdel;              // gbar - g_r: ybar . (group values - reference contact values)
+  T rd, rf;            // reference contact (see PartT)
+  V3T<T> rp, rn;
+  V3T<T> qb, nb;       // adjoints of the blended point q and of nu = N / U (S frame)
+  float db, ab;        // adjoints of the blended depth and weight (= ybar)
+  int live;
+};
+
+// Contact adjoint: given the contact's SDF value, gradient and H nu_bar at
+// point p, returns x_bar (adjoint of p) -- Sec. 4.3 mollifier and Sec. 4.4
+// blend differentiated by hand; see the derivation in the file header of
+// ccm_bwd.h.
+template <class T>
+__device__ __forceinline__ V3T<T> contact_adjoint(const SdfT<T>& c, V3T<T> p, const Coef<T>& k,
+                                                  const KParams& kp) {
+  T f, fp;
+  transition_t(c.phi, kp, f, fp);
+  if (val(f) <= 0.f) return v3(T(0.f), T(0.f), T(0.f));
+  const T dc = fma_t(f, c.phi - kp.d_max, T(kp.d_max));
+  const T om = ex2_t(dc * (-kp.c_blend) - k.M) * k.invU;   // weight per unit f
+  const T w = f * om;
+  // g_c - gbar = (g_c - g_r) - (gbar - g_r), both from direct differences
+  const T gcr = k.db * (dc - k.rd) + k.ab * (f - k.rf) + dot3(k.qb, sub3(p, k.rp)) +
+                dot3(k.nb, sub3(c.g, k.rn));
+  const T kk = gcr - k.gdel;
+  const T fb = fma_t(w, T(k.ab), kk * om);
+  const T dcb = w * (k.db - kk * (1.0f / kp.tau_blend));
+  const T phib = fma_t(dcb, fma_t(fp, c.phi - kp.d_max, f), fb * fp);
+  return v3(fma_t(w, k.qb.x, fma_t(phib, c.g.x, w * c.hv.x)),
+            fma_t(w, k.qb.y, fma_t(phib, c.g.y, w * c.hv.y)),
+            fma_t(w, k.qb.z, fma_t(phib, c.g.z, w * c.hv.z)));
+}
+
+// ---------------------------------------------------------------------------
+// slice of the backward kernel (per warp)
+// ---------------------------------------------------------------------------
+template <class T> struct BwdSlice {
+  float4* planes;     // [plane_budget]
+  int2* sp;           // [spiece_budget]
+  V3T<T>* xs;         // [vert_budget] F vertices in the S frame
+  uint32_t* edges;    // [edge_budget]
+  int4* fp;           // [32]
+  float4* fs;         // [32]
+  PartT<T>* acc;      // [32]
+  Coef<T>* coef;      // [32]
+  int* dir;           // [32]
+  int* dsub;          // [32]
+  int* pv;            // [33]
+  int* pe;            // [33]
+  float* m;           // [item_v]
+  T* phi;             // [item_v]
+  V3T<T>* grad;       // [item_v]
+  uint16_t* vlist;    // [item_v]
+  uint16_t* elist;    // [item_e]
+  uint8_t* need;      // [item_v]
+};
+
+template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShape& u) {
+  int b = 0;
+  b += 16 * u.plane_budget;
+  b += align16i(8 * u.spiece_budget);
+  b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
+  b += align16i(4 * u.edge_budget);
+  b += 16 * kGroupsPerChunk * 2;
+  b += align16i((int)sizeof(PartT<T>) * kGroupsPerChunk);
+  b += align16i((int)sizeof(Coef<T>) * kGroupsPerChunk);
+  b += align16i(4 * kPending) * 2;
+  b += align16i(4 * (kPending + 1)) * 2;
+  b += align16i(4 * u.item_v);
+  b += align16i((int)sizeof(T) * u.item_v);
+  b += align16i((int)sizeof(V3T<T>) * u.item_v);
+  b += align16i(2 * u.item_v);
+  b += align16i(2 * u.item_e);
+  b += align16i(u.item_v);
+  return b;
+}
+
+template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, const UnitShape& u) {
+  BwdSlice<T> s;
+  s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
+  s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * u.spiece_budget);
+  s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
+  s.edges = reinterpret_cast<uint32_t*>(p);    p += align16i(4 * u.edge_budget);
+  s.fp = reinterpret_cast<int4*>(p);           p += 16 * kGroupsPerChunk;
+  s.fs = reinterpret_cast<float4*>(p);         p += 16 * kGroupsPerChunk;
+  s.acc = reinterpret_cast<PartT<T>*>(p);      p += align16i((int)sizeof(PartT<T>) * kGroupsPerChunk);
+  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i((int)sizeof(Coef<T>) * kGroupsPerChunk);
+  s.dir = reinterpret_cast<int*>(p);           p += align16i(4 * kPending);
+  s.dsub = reinterpret_cast<int*>(p);          p += align16i(4 * kPending);
+  s.pv = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
+  s.pe = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
+  s.m = reinterpret_cast<float*>(p);           p += align16i(4 * u.item_v);
+  s.phi = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * u.item_v);
+  s.grad = reinterpret_cast<V3T<T>*>(p);       p += align16i((int)sizeof(V3T<T>) * u.item_v);
+  s.vlist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_v);
+  s.elist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_e);
+  s.need = reinterpret_cast<uint8_t*>(p);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// edge: trace forward (storing the steps), contact, and optionally adjoint
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T gstep(T phi, float c) {   // sigmoid(phi/tau) phi
+  return sigmoid_t(phi, c) * phi;
+}
+template <class T> __device__ __forceinline__ T gstep_d(T phi, float c) {  // its derivative
+  const T s = sigmoid_t(phi, c);
+  return fma_t(phi * (c * kLn2), s * (1.0f - s), s);
+}
+
+template <class T, bool kAdj>
+__device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> xII, float mI0,
+                       float mII0, T phI0, T phII0, V3T<T> gI0, V3T<T> gII0, const Coef<T>& k,
+                       const KParams& kp, SdfT<T>& c, V3T<T>& pe, V3T<T>& xbI, V3T<T>& xbII) {
+  const V3T<T> d = v3(xII.x - xI.x, xII.y - xI.y, xII.z - xI.z);
+  const T L = sqrt_t(dot3(d, d));
+  const T iL = rcp_t(L);
+  const V3T<T> e = v3(d.x * iL, d.y * iL, d.z * iL);
+  const int K = kp.trace_iters;
+  T a[kMaxTrace + 1], b[kMaxTrace + 1], pa[kMaxTrace], pb[kMaxTrace];
+  V3T<T> ga[kMaxTrace], gb[kMaxTrace];
+  a[0] = T(0.f);
+  b[0] = L;
+  pa[0] = phI0;
+  pb[0] = phII0;
+  ga[0] = gI0;
+  gb[0] = gII0;
+  float ma = mI0, mb = mII0;
+  for (int s = 0; s < K; ++s) {
+    const T sa = gstep(pa[s], kp.c_trace), sb = gstep(pb[s], kp.c_trace);
+    a[s + 1] = a[s] + sa;
+    b[s + 1] = b[s] - sb;
+    if (s + 1 == K) break;
+    const V3T<T> qa = v3(fma_t(a[s + 1], e.x, xI.x), fma_t(a[s + 1], e.y, xI.y),
+                         fma_t(a[s + 1], e.z, xI.z));
+    const V3T<T> qb = v3(fma_t(b[s + 1], e.x, xI.x), fma_t(b[s + 1], e.y, xI.y),
+                         fma_t(b[s + 1], e.z, xI.z));
+    const SdfT<T> ra = sdf_t<T, false>(pl, nf, qa, ma - fabsf(val(sa)), qa, kp);
+    const SdfT<T> rb = sdf_t<T, false>(pl, nf, qb, mb - fabsf(val(sb)), qb, kp);
+    pa[s + 1] = ra.phi; ga[s + 1] = ra.g;
+    pb[s + 1] = rb.phi; gb[s + 1] = rb.g;
+    // exact max-plane values are not tracked here; a looser lower bound only
+    // risks the (exact) repeat pass inside sdf_t
+    ma = val(ra.phi) - kp.tau_sdf * logf((float)nf) - 1e-6f;
+    mb = val(rb.phi) - kp.tau_sdf * logf((float)nf) - 1e-6f;
+  }
+  const T cI = softclip0_t(a[K], L, kp.tau_clip, kp.c_clip);
+  const T cII = softclip0_t(b[K], L, kp.tau_clip, kp.c_clip);
+  const T am = 0.5f * (cI + cII);
+  pe = v3(fma_t(am, e.x, xI.x), fma_t(am, e.y, xI.y), fma_t(am, e.z, xI.z));
+  const float lb = fmaxf(mI0 - val(am), mII0 - (val(L) - val(am)));
+  c = sdf_t<T, kAdj>(pl, nf, pe, lb, k.nb, kp);
+  if (!kAdj) return;
+  // ---- reverse sweep ----
+  const V3T<T> xb = contact_adjoint(c, pe, k, kp);
+  V3T<T> xi = xb;                                   // d pe / d xI = I (with e fixed)
+  V3T<T> eb = v3(am * xb.x, am * xb.y, am * xb.z);  // d pe / d e = am I
+  const T amb = dot3(xb, e);
+  // soft clip: d sc/d alpha = sig(alpha/tc) - sig((alpha - L)/tc), d sc/dL = sig((alpha - L)/tc)
+  const T sIa = sigmoid_t(a[K], kp.c_clip), sIb = sigmoid_t(a[K] - L, kp.c_clip);
+  const T sJa = sigmoid_t(b[K], kp.c_clip), sJb = sigmoid_t(b[K] - L, kp.c_clip);
+  T abar = 0.5f * amb * (sIa - sIb);
+  T bbar = 0.5f * amb * (sJa - sJb);
+  T Lb = 0.5f * amb * (sIb + sJb);
+  for (int s = K - 1; s >= 0; --s) {
+    // chain I: a[s+1] = a[s] + g(phi(xI + a[s] e))
+    const T pbarI = abar * gstep_d(pa[s], kp.c_trace);
+    xi = v3(fma_t(pbarI, ga[s].x, xi.x), fma_t(pbarI, ga[s].y, xi.y), fma_t(pbarI, ga[s].z, xi.z));
+    if (s > 0) {
+      const T t = pbarI * a[s];
+      eb = v3(fma_t(t, ga[s].x, eb.x), fma_t(t, ga[s].y, eb.y), fma_t(t, ga[s].z, eb.z));
+      abar = fma_t(pbarI, dot3(ga[s], e), abar);
+    }
+    // chain II: b[s+1] = b[s] - g(phi(xI + b[s] e)), b[0] = L
+    const T pbarII = -(bbar * gstep_d(pb[s], kp.c_trace));
+    xi = v3(fma_t(pbarII, gb[s].x, xi.x), fma_t(pbarII, gb[s].y, xi.y), fma_t(pbarII, gb[s].z, xi.z));
+    const T t2 = pbarII * b[s];
+    eb = v3(fma_t(t2, gb[s].x, eb.x), fma_t(t2, gb[s].y, eb.y), fma_t(t2, gb[s].z, eb.z));
+    bbar = fma_t(pbarII, dot3(gb[s], e), bbar);
+  }
+  Lb += bbar;   // b[0] = L
+  // e = d / L, L = |d|, d = xII - xI
+  const T ee = dot3(e, eb);
+  const V3T<T> db = v3(fma_t(Lb, e.x, (eb.x - e.x * ee) * iL), fma_t(Lb, e.y, (eb.y - e.y * ee) * iL),
+                       fma_t(Lb, e.z, (eb.z - e.z * ee) * iL));
+  xbII = db;
+  xbI = v3(xi.x - db.x, xi.y - db.y, xi.z - db.z);
+}
+
+// ---------------------------------------------------------------------------
+// one list of live directions: pass 1 (fold) or pass 2 (adjoint)
+// ---------------------------------------------------------------------------
+template <class T> struct Accum {
+  V3T<T> X1, X2;   // sum x_bar, sum x cross x_bar (S frame)
+};
+
+template <class T, int kPass>
+__device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, const KParams& kp,
+                             int lane, Accum<T>& ac) {
+  const int* dsub = sl.dsub;
+  for (int t = lane; t < TV; t += 32) {
+    const int r = find_dir(sl.pv, nd, t);
+    const int code = dsub[r];
+    const int4 f = sl.fp[code >> 16];
+    const int2 s = sl.sp[code & 0xffff];
+    const V3T<T> x = sl.xs[f.x + t - sl.pv[r]];
+    sl.m[t] = max_plane(sl.planes + s.x, s.y, val(x.x), val(x.y), val(x.z));
+    sl.need[t] = 0;
+  }
+  __syncwarp();
+  int n_e = 0;
+  for (int t0 = 0; t0 < TE; t0 += 32) {
+    const int t = t0 + lane;
+    bool live = false;
+    if (t < TE) {
+      const int r = find_dir(sl.pe, nd, t);
+      const int4 f = sl.fp[dsub[r] >> 16];
+      const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+      const int i0 = e & 0xffff, i1 = e >> 16;
+      const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
+      const V3T<T> a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
+      const float dx = val(b.x) - val(a.x), dy = val(b.y) - val(a.y), dz = val(b.z) - val(a.z);
+      const float L = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      live = 0.5f * (sl.m[t0v] + sl.m[t1v] - L) < kp.d_max;
+      if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
+    }
+    const unsigned bal = __ballot_sync(kFull, live);
+    if (live) sl.elist[n_e + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+    n_e += __popc(bal);
+  }
+  __syncwarp();
+  int n_v = 0;
+  for (int t0 = 0; t0 < TV; t0 += 32) {
+    const int t = t0 + lane;
+    const bool live = t < TV && (sl.m[t] < kp.d_max || sl.need[t]);
+    const unsigned bal = __ballot_sync(kFull, live);
+    if (live) sl.vlist[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+    n_v += __popc(bal);
+  }
+  __syncwarp();
+  // vertices
+  for (int k0 = 0; k0 < n_v; k0 += 32) {
+    const int k = k0 + lane;
+    PartT<T> c;
+    part_zero(c);
+    int key = 0xffff;
+    if (k < n_v) {
+      const int t = sl.vlist[k];
+      const int r = find_dir(sl.pv, nd, t);
+      const int code = dsub[r];
+      const int g = code >> 16;
+      const int4 f = sl.fp[g];
+      const int2 s = sl.sp[code & 0xffff];
+      const V3T<T> x = sl.xs[f.x + t - sl.pv[r]];
+      const float m = sl.m[t];
+      key = g;
+      if (kPass == 1) {
+        const SdfT<T> e = sdf_t<T, false>(sl.planes + s.x, s.y, x, m, x, kp);
+        sl.phi[t] = e.phi;
+        if (m < kp.d_max) {
+          T w, wp;
+          transition_t(e.phi, kp, w, wp);
+          const T dc = fma_t(w, e.phi - kp.d_max, T(kp.d_max));
+          part_from_contact(c, w, dc, x, e.g, kp.c_blend);
+        }
+      } else {
+        const Coef<T>& cf = sl.coef[g];
+        const SdfT<T> e = sdf_t<T, true>(sl.planes + s.x, s.y, x, m, cf.nb, kp);
+        sl.phi[t] = e.phi;
+        sl.grad[t] = e.g;
+        if (m < kp.d_max && cf.live) {
+          const V3T<T> xb = contact_adjoint(e, x, cf, kp);
+          ac.X1 = v3(ac.X1.x + xb.x, ac.X1.y + xb.y, ac.X1.z + xb.z);
+          ac.X2 = v3(ac.X2.x + (x.y * xb.z - x.z * xb.y), ac.X2.y + (x.z * xb.x - x.x * xb.z),
+                     ac.X2.z + (x.x * xb.y - x.y * xb.x));
+        }
+      }
+    }
+    if (kPass == 1) fold_t(c, key, sl.acc, lane);
+  }
+  __syncwarp();
+  // edges
+  for (int k0 = 0; k0 < n_e; k0 += 32) {
+    const int k = k0 + lane;
+    PartT<T> c;
+    part_zero(c);
+    int key = 0xffff;
+    if (k < n_e) {
+      const int t = sl.elist[k];
+      const int r = find_dir(sl.pe, nd, t);
+      const int code = dsub[r];
+      const int g = code >> 16;
+      const int4 f = sl.fp[g];
+      const int2 s = sl.sp[code & 0xffff];
+      const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+      const int i0 = e & 0xffff, i1 = e >> 16;
+      const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
+      const V3T<T> a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
+      key = g;
+      SdfT<T> sc;
+      V3T<T> pe, xbI, xbII;
+      const Coef<T>& cf = sl.coef[g];
+      if (kPass == 1) {
+        const V3T<T> z = v3(T(0.f), T(0.f), T(0.f));
+        edge_t<T, false>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
+                         sl.phi[t1v], z, z, cf, kp, sc, pe, xbI, xbII);
+        T w, wp;
+        transition_t(sc.phi, kp, w, wp);
+        const T dc = fma_t(w, sc.phi - kp.d_max, T(kp.d_max));
+        part_from_contact(c, w, dc, pe, sc.g, kp.c_blend);
+      } else if (cf.live) {
+        edge_t<T, true>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
+                        sl.phi[t1v], sl.grad[t0v], sl.grad[t1v], cf, kp, sc, pe, xbI, xbII);
+        ac.X1 = v3(ac.X1.x + xbI.x + xbII.x, ac.X1.y + xbI.y + xbII.y, ac.X1.z + xbI.z + xbII.z);
+        ac.X2 = v3(ac.X2.x + (a.y * xbI.z - a.z * xbI.y) + (b.y * xbII.z - b.z * xbII.y),
+                   ac.X2.y + (a.z * xbI.x - a.x * xbI.z) + (b.z * xbII.x - b.x * xbII.z),
+                   ac.X2.z + (a.x * xbI.y - a.y * xbI.x) + (b.x * xbII.y - b.y * xbII.x));
+      }
+    }
+    if (kPass == 1) fold_t(c, key, sl.acc, lane);
+  }
+  __syncwarp();
+}
+
+template <class T, int kPass>
+__device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& us,
+                                const KParams& kp, int lane, Accum<T>& ac) {
+  int start = 0;
+  while (start < np) {
+    const int r = start + lane;
+    int nvr = 0, ner = 0, code = 0;
+    if (r < np) {
+      code = sl.dir[r];
+      const int4 f = sl.fp[code >> 16];
+      nvr = f.y;
+      ner = f.w;
+    }
+    int iv = nvr, ie = ner;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
+      if (lane >= o) { iv += a; ie += b; }
+    }
+    const bool fits = r < np && iv <= us.item_v && ie <= us.item_e;
+    const int nd = __popc(__ballot_sync(kFull, fits));
+    if (lane < nd) {
+      sl.dsub[lane] = code;
+      sl.pv[lane] = iv - nvr;
+      sl.pe[lane] = ie - ner;
+    }
+    const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
+    __syncwarp();
+    bwd_run_list<T, kPass>(sl, nd, TV, TE, kp, lane, ac);
+    start += nd;
+  }
+}
+
+// all live directions of the staged F chunk against S, chunk by chunk
+template <class T, int kPass>
+__device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec& S, int nfc,
+                          float margin, const UnitShape& us, const KParams& kp, int lane,
+                          Accum<T>& ac) {
+  for (int sc0 = 0; sc0 < S.np;) {
+    int sc1 = sc0, P = 0;
+    while (sc1 < S.np && sc1 - sc0 < us.spiece_budget) {
+      const int nf = g.pieces[S.p0 + sc1].nf;
+      if (P + nf > us.plane_budget) break;
+      P += nf;
+      ++sc1;
+    }
+    const int nsc = sc1 - sc0;
+    if (nsc == 0) break;   // unreachable: budgets hold every piece
+    const int f_first = g.pieces[S.p0 + sc0].f0;
+    __syncwarp();
+    for (int q = lane; q < nsc; q += 32) {
+      const PieceRec p = g.pieces[S.p0 + sc0 + q];
+      sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
+    }
+    for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
+    __syncwarp();
+    int np = 0;
+    const int ndir = nfc * nsc;
+    for (int d0 = 0; d0 < ndir; d0 += 32) {
+      const int d = d0 + lane;
+      bool live = false;
+      int code = 0;
+      if (d < ndir) {
+        const int fcd = d / nsc, scd = d - fcd * nsc;
+        const float4 c = sl.fs[fcd];
+        const int2 s = sl.sp[scd];
+        const float mc = max_plane(sl.planes + s.x, s.y, c.x, c.y, c.z);
+        live = mc - c.w - margin < kp.d_max;
+        code = (fcd << 16) | scd;
+      }
+      const unsigned bal = __ballot_sync(kFull, live);
+      const int nl = __popc(bal);
+      if (np + nl > kPending) {
+        bwd_run_pending<T, kPass>(sl, np, us, kp, lane, ac);
+        np = 0;
+      }
+      if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
+      np += nl;
+      __syncwarp();
+    }
+    if (np > 0) bwd_run_pending<T, kPass>(sl, np, us, kp, lane, ac);
+    sc0 = sc1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// poses on T: the tangent of R is [w]x R and of t is v when differentiating
+// along a twist direction (w, v)
+// ---------------------------------------------------------------------------
+template <class T> struct PoseT {
+  T R[9];
+  T t[3];
+};
+
+__device__ inline void load_pose_t(const float* p, const float* u, PoseT<float>& P) {
+  (void)u;
+  for (int i = 0; i < 9; ++i) P.R[i] = __ldg(p + i);
+  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(p + 9 + i);
+}
+__device__ inline void load_pose_t(const float* p, const float* u, PoseT<Dual>& P) {
+  float R[9];
+  for (int i = 0; i < 9; ++i) R[i] = __ldg(p + i);
+  const float w0 = __ldg(u + 0), w1 = __ldg(u + 1), w2 = __ldg(u + 2);
+  const float W[9] = {0.f, -w2, w1, w2, 0.f, -w0, -w1, w0, 0.f};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      P.R[3 * i + j] = Dual(R[3 * i + j], W[3 * i] * R[j] + W[3 * i + 1] * R[3 + j] +
+                                              W[3 * i + 2] * R[6 + j]);
+  for (int i = 0; i < 3; ++i) P.t[i] = Dual(__ldg(p + 9 + i), __ldg(u + 3 + i));
+}
+
+template <class T> __device__ __forceinline__ V3T<T> rot(const T R[9], V3T<T> x) {
+  return v3(fma_t(R[0], x.x, fma_t(R[1], x.y, R[2] * x.z)),
+            fma_t(R[3], x.x, fma_t(R[4], x.y, R[5] * x.z)),
+            fma_t(R[6], x.x, fma_t(R[7], x.y, R[8] * x.z)));
+}
+template <class T> __device__ __forceinline__ V3T<T> rotT(const T R[9], V3T<T> x) {
+  return v3(fma_t(R[0], x.x, fma_t(R[3], x.y, R[6] * x.z)),
+            fma_t(R[1], x.x, fma_t(R[4], x.y, R[7] * x.z)),
+            fma_t(R[2], x.x, fma_t(R[5], x.y, R[8] * x.z)));
+}
+template <class T> __device__ __forceinline__ V3T<T> cross3(V3T<T> a, V3T<T> b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float tan_of(float) { return 0.f; }
+__device__ __forceinline__ float tan_of(Dual a) { return a.d; }
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(32)
+bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
+                const float* __restrict__ pose_a, const float* __restrict__ pose_b,
+                const float* __restrict__ ybar, const float* __restrict__ dir, KParams kp,
+                UnitShape us, float* __restrict__ part, float* __restrict__ jvp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
+  const int64_t n_units = 2 * n_pairs;
+  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int64_t pi = u >> 1;
+    const int side = (int)(u & 1);
+    const PairRec pr = pairs[pi];
+    const BodyRec bA = g.bodies[pr.bodyA], bB = g.bodies[pr.bodyB];
+    const BodyRec F = side == 0 ? bA : bB, S = side == 0 ? bB : bA;
+    const int64_t row0 = pr.goff + (side == 0 ? 0 : bA.np);
+    const float* pF = (side == 0 ? pose_a : pose_b) + 12 * pi;
+    const float* pS = (side == 0 ? pose_b : pose_a) + 12 * pi;
+    const float* uF = dir ? dir + 12 * pi + (side == 0 ? 0 : 6) : nullptr;
+    const float* uS = dir ? dir + 12 * pi + (side == 0 ? 6 : 0) : nullptr;
+    PoseT<T> PF, PS;
+    load_pose_t(pF, uF, PF);
+    load_pose_t(pS, uS, PS);
+    // relative pose S <- F
+    T Rr[9], tr[3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Rr[3 * i + j] = fma_t(PS.R[i], PF.R[j], fma_t(PS.R[3 + i], PF.R[3 + j], PS.R[6 + i] * PF.R[6 + j]));
+    {
+      const V3T<T> dt = v3(PF.t[0] - PS.t[0], PF.t[1] - PS.t[1], PF.t[2] - PS.t[2]);
+      const V3T<T> q = rotT(PS.R, dt);
+      tr[0] = q.x; tr[1] = q.y; tr[2] = q.z;
+    }
+    const float margin = 1e-6f * (1.0f + fabsf(val(tr[0])) + fabsf(val(tr[1])) + fabsf(val(tr[2])));
+    Accum<T> ac;
+    ac.X1 = v3(T(0.f), T(0.f), T(0.f));
+    ac.X2 = ac.X1;
+    V3T<T> gws = ac.X1, gvs = ac.X1;   // output-transform terms of this lane's groups
+
+    for (int fc0 = 0; fc0 < F.np;) {
+      int fc1 = fc0, V = 0, E = 0;
+      while (fc1 < F.np && fc1 - fc0 < kGroupsPerChunk) {
+        const PieceRec p = g.pieces[F.p0 + fc1];
+        if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
+        V += p.nv;
+        E += p.ne;
+        ++fc1;
+      }
+      const int nfc = fc1 - fc0;
+      if (nfc == 0) break;   // unreachable: budgets hold every piece
+      const PieceRec pfirst = g.pieces[F.p0 + fc0];
+      __syncwarp();
+      if (lane < nfc) {
+        const PieceRec p = g.pieces[F.p0 + fc0 + lane];
+        sl.fp[lane] = make_int4(p.v0 - pfirst.v0, p.nv, p.e0 - pfirst.e0, p.ne);
+        const float4 c = p.sphere;
+        const float cx = val(Rr[0]) * c.x + val(Rr[1]) * c.y + val(Rr[2]) * c.z + val(tr[0]);
+        const float cy = val(Rr[3]) * c.x + val(Rr[4]) * c.y + val(Rr[5]) * c.z + val(tr[1]);
+        const float cz = val(Rr[6]) * c.x + val(Rr[7]) * c.y + val(Rr[8]) * c.z + val(tr[2]);
+        sl.fs[lane] = make_float4(cx, cy, cz, c.w);
+        PartT<T> z;
+        part_zero(z);
+        sl.acc[lane] = z;
+      }
+      for (int i = lane; i < V; i += 32) {
+        const float4 v = g.verts[pfirst.v0 + i];
+        const V3T<T> vv = v3(T(v.x), T(v.y), T(v.z));
+        const V3T<T> x = rot(Rr, vv);
+        sl.xs[i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
+      }
+      for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
+      __syncwarp();
+
+      bwd_sweep<T, 1>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      __syncwarp();
+
+      // group outputs, adjoint coefficients and output-transform terms
+      if (lane < nfc) {
+        const PartT<T> A = sl.acc[lane];
+        const float* yb = ybar + 8 * (row0 + fc0 + lane);
+        Coef<T> cf;
+        cf.db = yb[0];
+        cf.ab = yb[1];
+        cf.live = val(A.U) > 0.f;
+        const V3T<T> pbw = v3(T(yb[2]), T(yb[3]), T(yb[4]));
+        const V3T<T> nbw = v3(T(yb[5]), T(yb[6]), T(yb[7]));
+        if (cf.live) {
+          const T iU = rcp_t(A.U);
+          const T d = fma_t(A.Dd, iU, A.rd), a = fma_t(A.Da, iU, A.rf);
+          const V3T<T> q = axpy3(iU, A.Dp, A.rp);
+          const V3T<T> nu = axpy3(iU, A.Dn, A.rn);
+          const V3T<T> nuw = rot(PS.R, nu);
+          const T nn = sqrt_t(dot3(nuw, nuw));
+          const T inn = val(nn) > 0.f ? rcp_t(nn) : T(0.f);
+          const V3T<T> nw = v3(nuw.x * inn, nuw.y * inn, nuw.z * inn);
+          const V3T<T> qw = rot(PS.R, q);
+          if (jvp) {
+            float* o = jvp + 8 * (row0 + fc0 + lane);
+            o[0] = tan_of(d);
+            o[1] = tan_of(a);
+            o[2] = tan_of(qw.x) + tan_of(PS.t[0]);
+            o[3] = tan_of(qw.y) + tan_of(PS.t[1]);
+            o[4] = tan_of(qw.z) + tan_of(PS.t[2]);
+            o[5] = tan_of(nw.x);
+            o[6] = tan_of(nw.y);
+            o[7] = tan_of(nw.z);
+          }
+          cf.M = A.M;
+          cf.invU = iU;
+          cf.qb = rotT(PS.R, pbw);
+          const V3T<T> nbs = rotT(PS.R, nbw);
+          const V3T<T> ns = rotT(PS.R, nw);
+          const T nsn = dot3(ns, nbs);
+          cf.nb = v3((nbs.x - ns.x * nsn) * inn, (nbs.y - ns.y * nsn) * inn,
+                     (nbs.z - ns.z * nsn) * inn);
+          cf.rd = A.rd; cf.rf = A.rf; cf.rp = A.rp; cf.rn = A.rn;
+          cf.gdel = (cf.db * A.Dd + cf.ab * A.Da + dot3(cf.qb, A.Dp) + dot3(cf.nb, A.Dn)) * iU;
+          // p_w = R_S q + t_S and n_w = R_S nu / |nu| under the twist of S
+          const V3T<T> c1 = cross3(qw, pbw), c2 = cross3(nw, nbw);
+          gws = v3(gws.x + c1.x + c2.x, gws.y + c1.y + c2.y, gws.z + c1.z + c2.z);
+          gvs = v3(gvs.x + pbw.x, gvs.y + pbw.y, gvs.z + pbw.z);
+        } else {
+          cf.M = cf.invU = cf.gdel = cf.rd = cf.rf = T(0.f);
+          cf.qb = cf.nb = cf.rp = cf.rn = zero3t<T>();
+          if (jvp) {
+            float* o = jvp + 8 * (row0 + fc0 + lane);
+            for (int q = 0; q < 8; ++q) o[q] = 0.f;
+          }
+        }
+        sl.coef[lane] = cf;
+      }
+      __syncwarp();
+      bwd_sweep<T, 2>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      fc0 = fc1;
+    }
+
+    // reduce the lanes and form the 12 twist components of this side
+    V3T<T> X1 = ac.X1, X2 = ac.X2;
+    X1 = v3(warp_sum_t(X1.x), warp_sum_t(X1.y), warp_sum_t(X1.z));
+    X2 = v3(warp_sum_t(X2.x), warp_sum_t(X2.y), warp_sum_t(X2.z));
+    gws = v3(warp_sum_t(gws.x), warp_sum_t(gws.y), warp_sum_t(gws.z));
+    gvs = v3(warp_sum_t(gvs.x), warp_sum_t(gvs.y), warp_sum_t(gvs.z));
+    if (lane == 0) {
+      const V3T<T> X1w = rot(PS.R, X1), X2w = rot(PS.R, X2);
+      const V3T<T> dts = v3(PS.t[0] - PF.t[0], PS.t[1] - PF.t[1], PS.t[2] - PF.t[2]);
+      const V3T<T> cx = cross3(dts, X1w);
+      // F: w_F = R_S X2 + (t_S - t_F) x R_S X1, v_F = R_S X1
+      // S: w_S = -R_S X2 + output terms,       v_S = -R_S X1 + output terms
+      T gF[6] = {X2w.x + cx.x, X2w.y + cx.y, X2w.z + cx.z, X1w.x, X1w.y, X1w.z};
+      T gS[6] = {gws.x - X2w.x, gws.y - X2w.y, gws.z - X2w.z,
+                 gvs.x - X1w.x, gvs.y - X1w.y, gvs.z - X1w.z};
+      // slot layout per unit: [grad (w_A, v_A, w_B, v_B) | H u (same layout)]
+      float* o = part + 24 * u;
+      const int offF = side == 0 ? 0 : 6, offS = side == 0 ? 6 : 0;
+      for (int q = 0; q < 6; ++q) {
+        o[offF + q] = val(gF[q]);
+        o[offS + q] = val(gS[q]);
+      }
+      if (uF) {
+        // H u = d/de grad(Exp(e u) T) - 1/2 u_w x grad_w (per body)
+        float hF[6], hS[6], vF[6], vS[6];
+        for (int q = 0; q < 6; ++q) {
+          hF[q] = tan_of(gF[q]); hS[q] = tan_of(gS[q]);
+          vF[q] = val(gF[q]); vS[q] = val(gS[q]);
+        }
+        const float cF[3] = {uF[1] * vF[2] - uF[2] * vF[1], uF[2] * vF[0] - uF[0] * vF[2],
+                             uF[0] * vF[1] - uF[1] * vF[0]};
+        const float cS[3] = {uS[1] * vS[2] - uS[2] * vS[1], uS[2] * vS[0] - uS[0] * vS[2],
+                             uS[0] * vS[1] - uS[1] * vS[0]};
+        for (int q = 0; q < 3; ++q) { hF[q] -= 0.5f * cF[q]; hS[q] -= 0.5f * cS[q]; }
+        for (int q = 0; q < 6; ++q) {
+          o[12 + offF + q] = hF[q];
+          o[12 + offS + q] = hS[q];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// grad / hvp of pair i = the two units' slots, side 0 then side 1
+__global__ void bwd_reduce_kernel(const float* __restrict__ part, int64_t n_pairs,
+                                  float* __restrict__ grad, float* __restrict__ hvp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs * 12) return;
+  const int64_t p = i / 12;
+  const int q = (int)(i - p * 12);
+  grad[i] = part[24 * (2 * p) + q] + part[24 * (2 * p + 1) + q];
+  if (hvp) hvp[i] = part[24 * (2 * p) + 12 + q] + part[24 * (2 * p + 1) + 12 + q];
+}
+
+cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
+  if (L.dir) {
+    const int smem = bwd_slice_bytes<Dual>(L.us);
+    bwd_unit_kernel<Dual><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+                                                        L.pose_b, L.ybar, L.dir, L.kp, L.us,
+                                                        L.part, L.jvp);
+  } else {
+    const int smem = bwd_slice_bytes<float>(L.us);
+    bwd_unit_kernel<float><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+                                                         L.pose_b, L.ybar, nullptr, L.kp, L.us,
+                                                         L.part, nullptr);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = L.n_pairs * 12;
+  bwd_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, stream>>>(L.part, L.n_pairs, L.grad,
+                                                                L.dir ? L.hvp : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d) {
+  const int sf = bwd_slice_bytes<float>(us), sd = bwd_slice_bytes<Dual>(us);
+  cudaError_t e;
+  if (sf > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(bwd_unit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sf)) != cudaSuccess)
+    return e;
+  if (sd > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(bwd_unit_kernel<Dual>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sd)) != cudaSuccess)
+    return e;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_f, bwd_unit_kernel<float>, 32, sf);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_d, bwd_unit_kernel<Dual>, 32, sd);
+  return cudaGetLastError();
+}
+
+int backward_slice_bytes(const UnitShape& us, bool dual) {
+  return dual ? bwd_slice_bytes<Dual>(us) : bwd_slice_bytes<float>(us);
+}
+
+}  // namespace ccm

@@ -1,0 +1,43 @@
+// Launch description of the reverse-pass kernels (ccm_bwd.cu).
+//
+// Adjoint of one contact c of a group with blend weight w_c = f_c om_c,
+// om_c = exp(-d_c / tau_blend) / sum_j f_j exp(-d_j / tau_blend), where the
+// group's outputs are d = sum w d_c, a = sum w f_c, q = sum w p_c and
+// nu = sum w grad phi_c (S frame; the world point is R_S q + t_S and the
+// normal R_S nu / |nu|):
+//   g_c   = dbar d_c + abar f_c + qbar . p_c + nubar . grad phi_c,
+//   gbar  = dbar d + abar a + qbar . q + nubar . nu,
+//   fbar  = w abar + (g_c - gbar) om_c,
+//   dcbar = w (dbar - (g_c - gbar) / tau_blend),
+//   phibar = dcbar (f + f' (phi - d_max)) + fbar f',
+//   xbar  = w qbar + phibar grad phi + w H nubar,
+// with qbar = R_S^T pbar_w and nubar = (nbar_S - n_S (n_S . nbar_S)) / |nu|.
+#pragma once
+#include "../../include/ccm.h"
+#include "ccm_device.cuh"
+#include "ccm_unit.cuh"
+
+namespace ccm {
+
+struct BwdLaunch {
+  DevGeom g;
+  const PairRec* pairs;
+  int64_t n_pairs;
+  const float* pose_a;
+  const float* pose_b;
+  const float* ybar;    // [G, 8]
+  const float* dir;     // [n, 12] or NULL
+  KParams kp;
+  UnitShape us;
+  float* part;          // [2n, 24] per-unit slots (workspace)
+  float* grad;          // [n, 12]
+  float* hvp;           // [n, 12] or NULL
+  float* jvp;           // [G, 8] or NULL
+  int grid;
+};
+
+cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream);
+cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d);
+int backward_slice_bytes(const UnitShape& us, bool dual);
+
+}  // namespace ccm

@@ -1,0 +1,241 @@
+// Device-side data layout and math shared by the contact kernels.
+//
+// Geometry is resident structure-of-arrays: one float4 per vertex (x, y, z, 0),
+// one float4 per face plane (n_x, n_y, n_z, h) -- the half-space SDF
+// phi_k(x) = n_k . x + h_k of Sec. 3 -- and one packed uint32 per edge
+// (i | j << 16, piece-local vertex indices).  Piece and body records index
+// into those arrays.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccm {
+
+struct __align__(16) PieceRec {
+  int32_t v0, nv, f0, nf;   // first vertex / count, first plane / count
+  int32_t e0, ne, body, pad;
+  float4 sphere;            // bounding sphere centre (body frame) and radius
+};
+
+struct BodyRec {
+  int32_t p0, np;           // first piece, piece count
+};
+
+struct PairRec {
+  int32_t bodyA, bodyB;
+  int64_t goff;
+};
+
+struct DevGeom {
+  const PieceRec* __restrict__ pieces;
+  const BodyRec* __restrict__ bodies;
+  const float4* __restrict__ verts;
+  const float4* __restrict__ planes;
+  const uint32_t* __restrict__ edges;
+};
+
+// Method constants with the derived factors the kernels use.
+struct KParams {
+  float tau_sdf, tau_trace, tau_clip, tau_blend, d_max, gate_width;
+  int32_t trace_iters;
+  uint32_t flags;
+  float c_sdf;      // log2(e) / tau_sdf
+  float ic_sdf;     // tau_sdf * ln(2) = 1 / c_sdf
+  float c_trace;    // log2(e) / tau_trace
+  float c_clip;     // log2(e) / tau_clip
+  float c_blend;    // log2(e) / tau_blend
+  float inv_gate;   // 1 / gate_width
+};
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr unsigned kFull = 0xffffffffu;
+
+// 2^x on the SFU (hand-written PTX; flushes denormal results to zero).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2 smooth operators on the device
+// ---------------------------------------------------------------------------
+// sigmoid(x / tau) with c = log2(e) / tau
+__device__ __forceinline__ float sigmoid_c(float x, float c) {
+  return __frcp_rn(1.0f + ex2(-x * c));
+}
+// softplus s+(x) = tau log(1 + e^{x/tau}) = max(x, 0) + tau log1p(e^{-|x|/tau})
+__device__ __forceinline__ float softplus_c(float x, float tau, float c) {
+  return fmaxf(x, 0.0f) + tau * log1pf(ex2(-fabsf(x) * c));
+}
+// softclip(x, 0, L) = s+(x) - s+(x - L)
+__device__ __forceinline__ float softclip0(float x, float L, float tau, float c) {
+  return softplus_c(x, tau, c) - softplus_c(x - L, tau, c);
+}
+// Sec. 4.3 transition: quintic smoothstep of s = (d_max - d) / eps on [0, 1]
+__device__ __forceinline__ float transition(float d, const KParams& kp) {
+  float s = __saturatef((kp.d_max - d) * kp.inv_gate);
+  return s * s * s * fmaf(s, fmaf(s, 6.0f, -15.0f), 10.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 piece SDF: phi = LSE_tau(n_k . x + h_k), evaluated in one pass over
+// the planes with a shift `s` that is a lower bound of the largest plane
+// value (so the largest term is >= 1 and nothing underflows to an empty
+// sum).  The exact largest value is tracked; if the bound was loose enough to
+// risk overflow, the pass is repeated with the exact maximum.
+// ---------------------------------------------------------------------------
+struct SdfGrad {
+  float phi, gx, gy, gz, mx;
+};
+
+__device__ __forceinline__ SdfGrad sdf_grad(const float4* __restrict__ pl, int nf, float x, float y,
+                                            float z, float s, const KParams& kp) {
+  SdfGrad r;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float sc = s * kp.c_sdf;
+    float S = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, mx = -INFINITY;
+#pragma unroll 4
+    for (int k = 0; k < nf; ++k) {
+      const float4 p = pl[k];
+      const float v = fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w)));
+      mx = fmaxf(mx, v);
+      const float e = ex2(fmaf(v, kp.c_sdf, -sc));
+      S += e;
+      gx = fmaf(e, p.x, gx);
+      gy = fmaf(e, p.y, gy);
+      gz = fmaf(e, p.z, gz);
+    }
+    if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
+    const float inv = __frcp_rn(S);
+    r.phi = fmaf(kp.ic_sdf, __log2f(S), s);
+    r.gx = gx * inv;
+    r.gy = gy * inv;
+    r.gz = gz * inv;
+    r.mx = mx;
+    break;
+  }
+  return r;
+}
+
+// value-only SDF at two points at once (the two sphere-trace chains of an edge)
+__device__ __forceinline__ void sdf_val2(const float4* __restrict__ pl, int nf, float x1, float y1,
+                                         float z1, float s1, float x2, float y2, float z2, float s2,
+                                         const KParams& kp, float& phi1, float& mx1, float& phi2,
+                                         float& mx2) {
+  for (int pass = 0; pass < 2; ++pass) {
+    const float sc1 = s1 * kp.c_sdf, sc2 = s2 * kp.c_sdf;
+    float S1 = 0.f, S2 = 0.f, m1 = -INFINITY, m2 = -INFINITY;
+#pragma unroll 4
+    for (int k = 0; k < nf; ++k) {
+      const float4 p = pl[k];
+      const float v1 = fmaf(p.x, x1, fmaf(p.y, y1, fmaf(p.z, z1, p.w)));
+      const float v2 = fmaf(p.x, x2, fmaf(p.y, y2, fmaf(p.z, z2, p.w)));
+      m1 = fmaxf(m1, v1);
+      m2 = fmaxf(m2, v2);
+      S1 += ex2(fmaf(v1, kp.c_sdf, -sc1));
+      S2 += ex2(fmaf(v2, kp.c_sdf, -sc2));
+    }
+    const bool bad1 = (m1 - s1) * kp.c_sdf > 64.0f, bad2 = (m2 - s2) * kp.c_sdf > 64.0f;
+    if (pass == 0 && (bad1 || bad2)) {
+      if (bad1) s1 = m1;
+      if (bad2) s2 = m2;
+      continue;
+    }
+    phi1 = fmaf(kp.ic_sdf, __log2f(S1), s1);
+    phi2 = fmaf(kp.ic_sdf, __log2f(S2), s2);
+    mx1 = m1;
+    mx2 = m2;
+    break;
+  }
+}
+
+// exact largest plane value at x (the hard polytope "depth" max_k phi_k)
+__device__ __forceinline__ float max_plane(const float4* __restrict__ pl, int nf, float x, float y,
+                                           float z) {
+  float mx = -INFINITY;
+#pragma unroll 4
+  for (int k = 0; k < nf; ++k) {
+    const float4 p = pl[k];
+    mx = fmaxf(mx, fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w))));
+  }
+  return mx;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 4.4 blend accumulator of one lane: running maximum logit M (log2
+// units) and the sums U, D, A, P, N of u = f 2^{l - M} times 1, d_c, f, p_c, n_c.
+// ---------------------------------------------------------------------------
+struct BlendAcc {
+  float M, U, D, A, px, py, pz, nx, ny, nz;
+  __device__ __forceinline__ void init() {
+    M = -INFINITY; U = D = A = px = py = pz = nx = ny = nz = 0.f;
+  }
+  __device__ __forceinline__ void add(float f, float dc, float qx, float qy, float qz, float mx_,
+                                      float my_, float mz_, float c_blend) {
+    if (!(f > 0.f)) return;
+    const float l = -dc * c_blend;
+    if (l > M) {
+      const float r = ex2(M - l);   // 0 when M = -inf
+      U *= r; D *= r; A *= r; px *= r; py *= r; pz *= r; nx *= r; ny *= r; nz *= r;
+      M = l;
+    }
+    const float u = f * ex2(l - M);
+    U += u;
+    D = fmaf(u, dc, D);
+    A = fmaf(u, f, A);
+    px = fmaf(u, qx, px); py = fmaf(u, qy, py); pz = fmaf(u, qz, pz);
+    nx = fmaf(u, mx_, nx); ny = fmaf(u, my_, ny); nz = fmaf(u, mz_, nz);
+  }
+  // merge across the warp (fixed butterfly order: deterministic)
+  __device__ __forceinline__ void warp_merge() {
+    const float Mw = warp_max(M);
+    const float r = (Mw == -INFINITY) ? 0.f : ex2(M - Mw);
+    U = warp_sum(U * r); D = warp_sum(D * r); A = warp_sum(A * r);
+    px = warp_sum(px * r); py = warp_sum(py * r); pz = warp_sum(pz * r);
+    nx = warp_sum(nx * r); ny = warp_sum(ny * r); nz = warp_sum(nz * r);
+    M = Mw;
+  }
+};
+
+__device__ __forceinline__ void write_empty(float* out, const KParams& kp) {
+  out[0] = kp.d_max;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) out[k] = 0.f;
+}
+
+__device__ __forceinline__ void load_pose(const float* __restrict__ p, float R[9], float t[3]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = __ldg(p + i);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = __ldg(p + 9 + i);
+}
+
+// relative pose mapping feature-body coordinates into the SDF body frame:
+// Rr = R_S^T R_F, tr = R_S^T (t_F - t_S)
+__device__ __forceinline__ void relative_pose(const float RS[9], const float tS[3], const float RF[9],
+                                              const float tF[3], float Rr[9], float tr[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Rr[3 * i + j] = RS[i] * RF[j] + RS[3 + i] * RF[3 + j] + RS[6 + i] * RF[6 + j];
+  }
+  const float d0 = tF[0] - tS[0], d1 = tF[1] - tS[1], d2 = tF[2] - tS[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tr[i] = RS[i] * d0 + RS[3 + i] * d1 + RS[6 + i] * d2;
+}
+
+}  // namespace ccm

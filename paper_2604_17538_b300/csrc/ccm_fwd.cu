@@ -1,0 +1,362 @@
+// Forward contact-manifold kernel (Sec. 4.2-4.4 of arxiv 2604.17538).
+//
+// One warp computes one unit (pair, side): the blend groups of every convex
+// piece f of the feature body F against the SDF pieces s of the other body S
+// (side 0: F = A, S = B; side 1: F = B, S = A).  See ccm_unit.cuh for how the
+// work is flattened over directions (s, f).
+//
+// Exact culls (every culled contact has transition weight 0, Sec. 4.3):
+//   * piece pair: max_k phi_k(c_f) - r_f >= d_max proves phi_s >= d_max on
+//     all of f (phi >= max-plane and both are 1-Lipschitz);
+//   * vertex: max-plane value m >= d_max;
+//   * edge: (m_I + m_II - L) / 2 >= d_max, a lower bound of the max-plane
+//     value along the edge.
+// A pair's outputs depend only on that pair: bit-identical in any batch.
+#include "ccm_narrow.cuh"
+#include "ccm_unit.cuh"
+#include "ccm_fwd.h"
+
+namespace ccm {
+
+// relative pose S <- F in double precision, computed by lanes 0..11 and
+// broadcast: Rr = R_S^T R_F, tr = R_S^T (t_F - t_S)
+__device__ __forceinline__ void rel_pose_f64(const float* pF, const float* pS, int lane,
+                                             float Rr[9], float tr[3]) {
+  float v = 0.f;
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) acc += (double)__ldg(pS + 3 * k + i) * (double)__ldg(pF + 3 * k + j);
+    v = (float)acc;
+  } else if (lane < 12) {
+    const int i = lane - 9;
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k)
+      acc += (double)__ldg(pS + 3 * k + i) * ((double)__ldg(pF + 9 + k) - (double)__ldg(pS + 9 + k));
+    v = (float)acc;
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Rr[q] = __shfl_sync(kFull, v, q);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) tr[q] = __shfl_sync(kFull, v, 9 + q);
+}
+
+__device__ __forceinline__ float3 xform(const float R[9], const float t[3], float4 v) {
+  return make_float3(fmaf(R[0], v.x, fmaf(R[1], v.y, fmaf(R[2], v.z, t[0]))),
+                     fmaf(R[3], v.x, fmaf(R[4], v.y, fmaf(R[5], v.z, t[1]))),
+                     fmaf(R[6], v.x, fmaf(R[7], v.y, fmaf(R[8], v.z, t[2]))));
+}
+
+struct FwdCounts {
+  unsigned long long dirs = 0, gate = 0, live = 0, maxp = 0, eg = 0, ev = 0, con = 0, feat = 0;
+};
+
+// Narrow phase of the live directions sl.dsub[0..nd) whose vertex / edge items
+// are numbered by the exclusive prefixes sl.pv / sl.pe (totals TV, TE).
+template <bool kCount>
+__device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE,
+                         const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
+  // exact max-plane value of every (direction, vertex) item
+  for (int t = lane; t < TV; t += 32) {
+    const int r = find_dir(sl.pv, nd, t);
+    const int code = dsub[r];
+    const int4 f = sl.fp[code >> 16];
+    const int2 s = sl.sp[code & 0xffff];
+    const float4 x = sl.xs[f.x + t - sl.pv[r]];
+    sl.m[t] = max_plane(sl.planes + s.x, s.y, x.x, x.y, x.z);
+    sl.need[t] = 0;
+    if (kCount) cnt.maxp += s.y;
+  }
+  __syncwarp();
+  // edge cull: every point of an edge is at distance a from v_I and L - a
+  // from v_II, so its max-plane value is >= (m_I + m_II - L) / 2
+  int n_e = 0;
+  for (int t0 = 0; t0 < TE; t0 += 32) {
+    const int t = t0 + lane;
+    bool live = false;
+    if (t < TE) {
+      const int r = find_dir(sl.pe, nd, t);
+      const int code = dsub[r];
+      const int4 f = sl.fp[code >> 16];
+      const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+      const int i0 = e & 0xffff, i1 = e >> 16;
+      const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
+      const float4 a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
+      const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+      const float L = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      live = no_cull || 0.5f * (sl.m[t0v] + sl.m[t1v] - L) < kp.d_max;
+      if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
+    }
+    const unsigned bal = __ballot_sync(kFull, live);
+    if (live) sl.elist[n_e + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+    n_e += __popc(bal);
+  }
+  __syncwarp();
+  int n_v = 0;
+  for (int t0 = 0; t0 < TV; t0 += 32) {
+    const int t = t0 + lane;
+    const bool live = t < TV && (no_cull || sl.m[t] < kp.d_max || sl.need[t]);
+    const unsigned bal = __ballot_sync(kFull, live);
+    if (live) sl.vlist[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+    n_v += __popc(bal);
+  }
+  __syncwarp();
+  // V-SDF contacts (and the SDF at vertices that start a sphere trace)
+  for (int k0 = 0; k0 < n_v; k0 += 32) {
+    const int k = k0 + lane;
+    LaneContact c;
+    contact_to_partial(c, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kp.c_blend);
+    int key = 0xffff;
+    if (k < n_v) {
+      const int t = sl.vlist[k];
+      const int r = find_dir(sl.pv, nd, t);
+      const int code = dsub[r];
+      const int4 f = sl.fp[code >> 16];
+      const int2 s = sl.sp[code & 0xffff];
+      const float4 x = sl.xs[f.x + t - sl.pv[r]];
+      const float m = sl.m[t];
+      const SdfGrad g = sdf_grad(sl.planes + s.x, s.y, x.x, x.y, x.z, m, kp);
+      sl.phi[t] = g.phi;
+      key = code >> 16;
+      if (no_cull || m < kp.d_max) {
+        const float w = transition(g.phi, kp);
+        const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
+        contact_to_partial(c, w, dc, x.x, x.y, x.z, g.gx, g.gy, g.gz, kp.c_blend);
+        if (kCount) cnt.con += w > 0.f;
+      }
+      if (kCount) cnt.eg += s.y;
+    }
+    fold_contacts(c, key, sl.acc, lane);
+  }
+  __syncwarp();
+  // E-SDF contacts: sphere trace from both corners, soft clip, midpoint
+  for (int k0 = 0; k0 < n_e; k0 += 32) {
+    const int k = k0 + lane;
+    LaneContact c;
+    contact_to_partial(c, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kp.c_blend);
+    int key = 0xffff;
+    if (k < n_e) {
+      const int t = sl.elist[k];
+      const int r = find_dir(sl.pe, nd, t);
+      const int code = dsub[r];
+      const int4 f = sl.fp[code >> 16];
+      const int2 s = sl.sp[code & 0xffff];
+      const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+      const int i0 = e & 0xffff, i1 = e >> 16;
+      const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
+      const EdgeContact ec = edge_contact(sl.planes + s.x, s.y, sl.xs[f.x + i0], sl.xs[f.x + i1],
+                                          sl.m[t0v], sl.m[t1v], sl.phi[t0v], sl.phi[t1v], kp);
+      const float w = transition(ec.phi, kp);
+      const float dc = fmaf(w, ec.phi - kp.d_max, kp.d_max);
+      contact_to_partial(c, w, dc, ec.px, ec.py, ec.pz, ec.gx, ec.gy, ec.gz, kp.c_blend);
+      key = code >> 16;
+      if (kCount) {
+        cnt.con += w > 0.f;
+        cnt.eg += s.y;
+        cnt.ev += (unsigned long long)s.y * 2 * (kp.trace_iters > 0 ? kp.trace_iters - 1 : 0);
+      }
+    }
+    fold_contacts(c, key, sl.acc, lane);
+  }
+  __syncwarp();
+}
+
+// Splits the pending directions sl.dir[0..np) into lists that fit the item
+// budgets and runs each.
+template <bool kCount>
+__device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitShape& us,
+                           const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
+  int start = 0;
+  while (start < np) {
+    const int r = start + lane;
+    int nvr = 0, ner = 0, code = 0;
+    if (r < np) {
+      code = sl.dir[r];
+      const int4 f = sl.fp[code >> 16];
+      nvr = f.y;
+      ner = f.w;
+    }
+    int iv = nvr, ie = ner;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
+      if (lane >= o) { iv += a; ie += b; }
+    }
+    const bool fits = r < np && iv <= us.item_v && ie <= us.item_e;
+    const int nd = __popc(__ballot_sync(kFull, fits));   // >= 1: budgets hold any one piece
+    if (lane < nd) {
+      dsub[lane] = code;
+      sl.pv[lane] = iv - nvr;
+      sl.pe[lane] = ie - ner;
+      if (kCount) { cnt.live += 1; cnt.feat += nvr + ner; }
+    }
+    const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
+    __syncwarp();
+    run_list<kCount>(sl, dsub, nd, TV, TE, kp, no_cull, lane, cnt);
+    start += nd;
+  }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(64)
+unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
+                const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
+                UnitShape us, float* __restrict__ y, unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const UnitSlice sl = unit_slice(smem_raw + (size_t)warp * us.slice_bytes, us);
+  int* dsub = sl.dsub;
+  const bool no_cull = (kp.flags & 1u) != 0;
+  const int64_t n_units = 2 * n_pairs;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  FwdCounts cnt;
+
+  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n_units; u += nwarps) {
+    const int64_t pi = u >> 1;
+    const int side = (int)(u & 1);
+    const PairRec pr = pairs[pi];
+    const BodyRec bA = g.bodies[pr.bodyA], bB = g.bodies[pr.bodyB];
+    const BodyRec F = side == 0 ? bA : bB, S = side == 0 ? bB : bA;
+    const int64_t row0 = pr.goff + (side == 0 ? 0 : bA.np);
+    const float* pF = (side == 0 ? pose_a : pose_b) + 12 * pi;
+    const float* pS = (side == 0 ? pose_b : pose_a) + 12 * pi;
+    float Rr[9], tr[3];
+    rel_pose_f64(pF, pS, lane, Rr, tr);
+    const float margin = 1e-6f * (1.0f + fabsf(tr[0]) + fabsf(tr[1]) + fabsf(tr[2]));
+
+    for (int fc0 = 0; fc0 < F.np;) {
+      // F chunk [fc0, fc1): up to 32 pieces within the vertex / edge budgets
+      int fc1 = fc0, V = 0, E = 0;
+      while (fc1 < F.np && fc1 - fc0 < kGroupsPerChunk) {
+        const PieceRec p = g.pieces[F.p0 + fc1];
+        if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
+        V += p.nv;
+        E += p.ne;
+        ++fc1;
+      }
+      const int nfc = fc1 - fc0;
+      if (nfc == 0) break;   // unreachable: the host sizes the budgets >= every piece
+      const PieceRec pfirst = g.pieces[F.p0 + fc0];
+      __syncwarp();   // the previous chunk's data is no longer read
+      if (lane < nfc) {
+        const PieceRec p = g.pieces[F.p0 + fc0 + lane];
+        sl.fp[lane] = make_int4(p.v0 - pfirst.v0, p.nv, p.e0 - pfirst.e0, p.ne);
+        const float3 c = xform(Rr, tr, p.sphere);
+        sl.fs[lane] = make_float4(c.x, c.y, c.z, p.sphere.w);
+        float* a = sl.acc + 10 * lane;
+        a[0] = -INFINITY;
+#pragma unroll
+        for (int q = 1; q < 10; ++q) a[q] = 0.f;
+      }
+      for (int i = lane; i < V; i += 32) {
+        const float3 x = xform(Rr, tr, g.verts[pfirst.v0 + i]);
+        sl.xs[i] = make_float4(x.x, x.y, x.z, 0.f);
+      }
+      for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
+
+      for (int sc0 = 0; sc0 < S.np;) {
+        // S chunk [sc0, sc1) within the plane / piece budgets
+        int sc1 = sc0, P = 0;
+        while (sc1 < S.np && sc1 - sc0 < us.spiece_budget) {
+          const int nf = g.pieces[S.p0 + sc1].nf;
+          if (P + nf > us.plane_budget) break;
+          P += nf;
+          ++sc1;
+        }
+        const int nsc = sc1 - sc0;
+        if (nsc == 0) break;   // unreachable, as above
+        const int f_first = g.pieces[S.p0 + sc0].f0;
+        __syncwarp();   // the previous S chunk's planes are no longer read
+        for (int q = lane; q < nsc; q += 32) {
+          const PieceRec p = g.pieces[S.p0 + sc0 + q];
+          sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
+        }
+        for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
+        __syncwarp();
+
+        // gate the directions (fc, sc), 32 at a time, collecting live ones
+        int np = 0;
+        const int ndir = nfc * nsc;
+        for (int d0 = 0; d0 < ndir; d0 += 32) {
+          const int d = d0 + lane;
+          bool live = false;
+          int code = 0;
+          if (d < ndir) {
+            const int fcd = d / nsc, scd = d - fcd * nsc;
+            const float4 c = sl.fs[fcd];
+            const int2 s = sl.sp[scd];
+            const float mc = max_plane(sl.planes + s.x, s.y, c.x, c.y, c.z);
+            live = no_cull || mc - c.w - margin < kp.d_max;
+            code = (fcd << 16) | scd;
+            if (kCount) { cnt.dirs += 1; cnt.gate += s.y; }
+          }
+          const unsigned bal = __ballot_sync(kFull, live);
+          const int nl = __popc(bal);
+          if (np + nl > kPending) {
+            run_pending<kCount>(sl, dsub, np, us, kp, no_cull, lane, cnt);
+            np = 0;
+          }
+          if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
+          np += nl;
+          __syncwarp();
+        }
+        if (np > 0) run_pending<kCount>(sl, dsub, np, us, kp, no_cull, lane, cnt);
+        sc0 = sc1;
+      }
+      __syncwarp();
+      if (lane < nfc) {
+        const float* a = sl.acc + 10 * lane;
+        BlendAcc acc;
+        acc.M = a[0]; acc.U = a[1]; acc.D = a[2]; acc.A = a[3];
+        acc.px = a[4]; acc.py = a[5]; acc.pz = a[6]; acc.nx = a[7]; acc.ny = a[8]; acc.nz = a[9];
+        float RS[9], tS[3];
+        load_pose(pS, RS, tS);
+        write_group(y + 8 * (row0 + fc0 + lane), acc, RS, tS, kp);
+      }
+      fc0 = fc1;
+    }
+  }
+
+  if (kCount) {
+    unsigned long long v[8] = {cnt.dirs, cnt.live, cnt.maxp, cnt.gate, cnt.eg, cnt.ev, cnt.con,
+                               cnt.feat};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      unsigned long long x = v[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0) atomicAdd(counters + q, x);
+    }
+  }
+}
+
+cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
+  const size_t smem = (size_t)L.us.warps * L.us.slice_bytes;
+  const int threads = 32 * L.us.warps;
+  if (L.counters)
+    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+                                                             L.pose_b, L.kp, L.us, L.y, L.counters);
+  else
+    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+                                                              L.pose_b, L.kp, L.us, L.y, L.counters);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_forward(const UnitShape& us, int* blocks_per_sm) {
+  const int smem = us.warps * us.slice_bytes;
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(unit_fwd_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(unit_fwd_kernel<true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, unit_fwd_kernel<false>,
+                                                32 * us.warps, smem);
+  return cudaGetLastError();
+}
+
+}  // namespace ccm

@@ -1,0 +1,25 @@
+// Launch description of the forward kernels (ccm_fwd.cu).
+#pragma once
+#include "../../include/ccm.h"
+#include "ccm_device.cuh"
+#include "ccm_unit.cuh"
+
+namespace ccm {
+
+struct FwdLaunch {
+  DevGeom g;
+  const PairRec* pairs;
+  int64_t n_pairs;
+  const float* pose_a;
+  const float* pose_b;
+  KParams kp;
+  UnitShape us;
+  float* y;
+  unsigned long long* counters;   // optional work counters (CCM_CNT_*)
+  int grid;
+};
+
+cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);
+cudaError_t configure_forward(const UnitShape& us, int* blocks_per_sm);
+
+}  // namespace ccm

@@ -1,0 +1,180 @@
+// The forward pass of one unit (pair, side) for one warp: the N_F blend groups
+// of body F's convex pieces against the pieces of body S (Sec. 4.2-4.4).
+//
+// Work is flattened so that all 32 lanes stay busy although only a few
+// features of a live piece pair survive the exact culls:
+//   * S's planes and F's vertices (moved into S's frame) and edges are staged
+//     in the warp's shared-memory slice -- in chunks when a body is large;
+//   * directions (f, s) are gated 32 at a time (lane per direction) and the
+//     live ones are collected in (f, s) order into a pending list;
+//   * for a list of live directions, the max-plane pass runs over all their
+//     (direction, vertex) items, the edge cull over all (direction, edge)
+//     items, and the SDF evaluations over the compacted survivors of all of
+//     them; items stay sorted by group, so after each round of 32 contacts a
+//     segmented warp reduction (online softmax) folds them into the groups'
+//     accumulators kept in shared memory -- one head lane per group, in a
+//     fixed order, so the result is deterministic.
+#pragma once
+#include "ccm_device.cuh"
+
+namespace ccm {
+
+// Per-batch budgets of the per-warp shared-memory slice.
+struct UnitShape {
+  int32_t plane_budget;   // planes of one S chunk (>= largest piece)
+  int32_t spiece_budget;  // pieces of one S chunk
+  int32_t vert_budget;    // vertices of one F chunk (>= largest piece)
+  int32_t edge_budget;    // edges of one F chunk (>= largest piece)
+  int32_t item_v;         // (direction, vertex) items per direction list
+  int32_t item_e;         // (direction, edge) items per direction list
+  int32_t slice_bytes;    // bytes per warp
+  int32_t warps;          // warps per block
+};
+
+constexpr int kGroupsPerChunk = 32;   // groups of one F chunk (lane-indexed)
+constexpr int kPending = 32;          // live directions per list
+
+struct UnitSlice {
+  float4* planes;     // [plane_budget]
+  int2* sp;           // [spiece_budget] (first plane, plane count) per S piece
+  float4* xs;         // [vert_budget] F vertices in the S frame
+  uint32_t* edges;    // [edge_budget]
+  int4* fp;           // [32] (first vertex, nv, first edge, ne) per F piece
+  float4* fs;         // [32] bounding sphere (S frame) per F piece
+  float* acc;         // [32 * 10] group accumulators (M, U, D, A, P, N)
+  int* dir;           // [32] pending live directions: fc << 16 | sc
+  int* dsub;          // [32] directions of the list being run
+  int* pv;            // [33] prefix of vertex items per pending direction
+  int* pe;            // [33] prefix of edge items
+  float* m;           // [item_v] max-plane value per (direction, vertex)
+  float* phi;         // [item_v] SDF per (direction, vertex)
+  uint16_t* vlist;    // [item_v] surviving vertex items
+  uint16_t* elist;    // [item_e] surviving edge items
+  uint8_t* need;      // [item_v]
+};
+
+__host__ __device__ inline int align16i(int b) { return (b + 15) & ~15; }
+
+__host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
+  int b = 0;
+  b += 16 * u.plane_budget;
+  b += align16i(8 * u.spiece_budget);
+  b += 16 * u.vert_budget;
+  b += align16i(4 * u.edge_budget);
+  b += 16 * kGroupsPerChunk;                 // fp
+  b += 16 * kGroupsPerChunk;                 // fs
+  b += align16i(4 * 10 * kGroupsPerChunk);   // acc
+  b += align16i(4 * kPending) * 2;           // dir, dsub
+  b += align16i(4 * (kPending + 1)) * 2;     // pv, pe
+  b += align16i(4 * u.item_v) * 2;           // m, phi
+  b += align16i(2 * u.item_v);               // vlist
+  b += align16i(2 * u.item_e);               // elist
+  b += align16i(u.item_v);                   // need
+  return b;
+}
+
+__device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
+  UnitSlice s;
+  s.planes = reinterpret_cast<float4*>(p);           p += 16 * u.plane_budget;
+  s.sp = reinterpret_cast<int2*>(p);                 p += align16i(8 * u.spiece_budget);
+  s.xs = reinterpret_cast<float4*>(p);               p += 16 * u.vert_budget;
+  s.edges = reinterpret_cast<uint32_t*>(p);          p += align16i(4 * u.edge_budget);
+  s.fp = reinterpret_cast<int4*>(p);                 p += 16 * kGroupsPerChunk;
+  s.fs = reinterpret_cast<float4*>(p);               p += 16 * kGroupsPerChunk;
+  s.acc = reinterpret_cast<float*>(p);               p += align16i(4 * 10 * kGroupsPerChunk);
+  s.dir = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
+  s.dsub = reinterpret_cast<int*>(p);                p += align16i(4 * kPending);
+  s.pv = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));
+  s.pe = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));
+  s.m = reinterpret_cast<float*>(p);                 p += align16i(4 * u.item_v);
+  s.phi = reinterpret_cast<float*>(p);               p += align16i(4 * u.item_v);
+  s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
+  s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
+  s.need = reinterpret_cast<uint8_t*>(p);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// one contact in a lane, and the segmented online-softmax fold into groups
+// ---------------------------------------------------------------------------
+struct LaneContact {
+  float M, U, D, A, px, py, pz, nx, ny, nz;   // partial blend of this lane
+};
+
+__device__ __forceinline__ void contact_to_partial(LaneContact& c, float f, float dc, float qx,
+                                                   float qy, float qz, float gx, float gy,
+                                                   float gz, float c_blend) {
+  if (f > 0.f) {
+    c.M = -dc * c_blend;   // logit in log2 units; the lane's only term has weight 2^0
+    c.U = f;
+    c.D = f * dc;
+    c.A = f * f;
+    c.px = f * qx; c.py = f * qy; c.pz = f * qz;
+    c.nx = f * gx; c.ny = f * gy; c.nz = f * gz;
+  } else {
+    c.M = -INFINITY;
+    c.U = c.D = c.A = c.px = c.py = c.pz = c.nx = c.ny = c.nz = 0.f;
+  }
+}
+
+// a <- a (+) b for online-softmax partials
+__device__ __forceinline__ void combine(LaneContact& a, const LaneContact& b) {
+  const float M = fmaxf(a.M, b.M);
+  if (M == -INFINITY) return;
+  const float ra = ex2(a.M - M), rb = ex2(b.M - M);
+  a.U = a.U * ra + b.U * rb;
+  a.D = a.D * ra + b.D * rb;
+  a.A = a.A * ra + b.A * rb;
+  a.px = a.px * ra + b.px * rb; a.py = a.py * ra + b.py * rb; a.pz = a.pz * ra + b.pz * rb;
+  a.nx = a.nx * ra + b.nx * rb; a.ny = a.ny * ra + b.ny * rb; a.nz = a.nz * ra + b.nz * rb;
+  a.M = M;
+}
+
+__device__ __forceinline__ LaneContact shfl_down_contact(const LaneContact& c, int o) {
+  LaneContact r;
+  r.M = __shfl_down_sync(kFull, c.M, o);
+  r.U = __shfl_down_sync(kFull, c.U, o);
+  r.D = __shfl_down_sync(kFull, c.D, o);
+  r.A = __shfl_down_sync(kFull, c.A, o);
+  r.px = __shfl_down_sync(kFull, c.px, o);
+  r.py = __shfl_down_sync(kFull, c.py, o);
+  r.pz = __shfl_down_sync(kFull, c.pz, o);
+  r.nx = __shfl_down_sync(kFull, c.nx, o);
+  r.ny = __shfl_down_sync(kFull, c.ny, o);
+  r.nz = __shfl_down_sync(kFull, c.nz, o);
+  return r;
+}
+
+// Lanes hold contacts sorted by `key` (group in the F chunk; 0xffff for an
+// idle lane, always after the others).  The first lane of each key's run
+// folds the run's total into that group's accumulator.
+__device__ inline void fold_contacts(LaneContact c, int key, float* acc, int lane) {
+  const unsigned seg = __match_any_sync(kFull, key);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const LaneContact b = shfl_down_contact(c, o);
+    if (lane + o < 32 && ((seg >> (lane + o)) & 1u)) combine(c, b);
+  }
+  const bool head = (__ffs(seg) - 1) == lane;
+  if (head && key != 0xffff && c.M != -INFINITY) {
+    float* a = acc + 10 * key;
+    LaneContact g;
+    g.M = a[0]; g.U = a[1]; g.D = a[2]; g.A = a[3];
+    g.px = a[4]; g.py = a[5]; g.pz = a[6]; g.nx = a[7]; g.ny = a[8]; g.nz = a[9];
+    combine(g, c);
+    a[0] = g.M; a[1] = g.U; a[2] = g.D; a[3] = g.A;
+    a[4] = g.px; a[5] = g.py; a[6] = g.pz; a[7] = g.nx; a[8] = g.ny; a[9] = g.nz;
+  }
+}
+
+// largest r in [0, n) with pre[r] <= t (pre is an exclusive prefix, pre[0] = 0)
+__device__ __forceinline__ int find_dir(const int* pre, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace ccm

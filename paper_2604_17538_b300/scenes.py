@@ -397,10 +397,14 @@ def _make_env(args):
 
 
 def _map_envs(jobs, workers):
-    if workers is None:
+    """Runs the per-environment jobs; ``workers`` None or 1 = serial, 0 = one
+    spawned process per host core (at most 32).  A script that asks for worker
+    processes must guard its entry point with ``if __name__ == "__main__"``,
+    since spawned workers import the main module."""
+    if workers == 0:
         import os
         workers = min(len(os.sched_getaffinity(0)), 32)
-    if workers <= 1 or len(jobs) < 64:
+    if workers is None or workers <= 1 or len(jobs) < 64:
         return [_make_env(j) for j in jobs]
     import multiprocessing as mp
     # spawn: never fork a process that may already hold a CUDA context

@@ -1,0 +1,70 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI on a
+seeded scene and compare it with the FP64 oracle."""
+import numpy as np
+
+# Tolerances of the parity bar: |gpu - oracle| <= ATOL + RTOL |oracle| per
+# element for the depth and the weight, and per component with |oracle| the
+# vector norm for the point and the unit normal (a relative error of a vector
+# is measured against its length); derivatives
+# ||gpu - oracle||_inf <= GRAD_RTOL ||oracle||_inf per pair.
+ATOL, RTOL = 1e-6, 1e-5
+GRAD_RTOL = 1e-3
+
+
+def gpu_forward(scene, params=None, counters=False, ctx=None):
+    import torch
+    from paper_2604_17538_b300 import api
+    own = ctx is None
+    ctx = ctx or api.Context(0)
+    batch, pa, pb = api.scene_to_device(scene, ctx)
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda") if counters else None
+    y = batch.contacts(pa, pb, params, counters=cnt)
+    torch.cuda.synchronize()
+    out = y.double().cpu().numpy()
+    c = cnt.cpu().numpy() if counters else None
+    batch.close()
+    if own:
+        ctx.close()
+    return (out, c) if counters else out
+
+
+def oracle_params(params):
+    import oracle
+    return oracle.params(**(params or {}))
+
+
+def weight_slack(scene, params=None):
+    """FP32 conditioning term of the blend weight a = sum w f_t(phi).
+
+    f_t changes at up to 15 / (8 eps) per unit of SDF value (the quintic
+    transition's largest slope), and float32 rounds a coordinate of
+    magnitude X by up to 2^-24 X, so a weight can legitimately move by
+    2^-24 X 15 / (8 eps) between an FP32 and an FP64 evaluation of the same
+    inputs; X is bounded by the largest body-frame vertex norm plus the
+    largest distance between the two bodies of a pair."""
+    eps = (params or {}).get("gate_width", 0.01)
+    X = float(np.linalg.norm(scene.geom.verts, axis=1).max() +
+              np.linalg.norm(scene.pose_a[:, 9:] - scene.pose_b[:, 9:], axis=1).max())
+    return 2.0 ** -24 * X * 15.0 / (8.0 * eps)
+
+
+def compare(y, ref, what="y", atol=ATOL, rtol=RTOL, a_slack=0.0):
+    """Max error per output column; raises with a report if over tolerance.
+    ``a_slack`` widens the weight column by its FP32 conditioning term."""
+    names = ["d", "a", "px", "py", "pz", "nx", "ny", "nz"]
+    err = np.abs(y - ref)
+    mag = np.abs(ref).copy()
+    if len(ref):
+        mag[:, 2:5] = np.linalg.norm(ref[:, 2:5], axis=1, keepdims=True)
+        mag[:, 5:8] = np.linalg.norm(ref[:, 5:8], axis=1, keepdims=True)
+    tol = atol + rtol * mag
+    if len(ref):
+        tol[:, 1] += a_slack
+    bad = err > tol
+    report = {names[k]: float(err[:, k].max()) if len(err) else 0.0 for k in range(8)}
+    if bad.any():
+        i, k = np.argwhere(bad)[0]
+        raise AssertionError(f"{what}: {int(bad.sum())} elements over tolerance; first at "
+                             f"group {i} col {names[k]}: gpu={y[i, k]!r} oracle={ref[i, k]!r}; "
+                             f"max err per output {report}")
+    return report
