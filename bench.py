@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the contact-manifold hot path on B300.
+
+A step is one pass of the whole path over one batch of synthetic input:
+forward contacts (gate, V-SDF / E-SDF narrow phase, blending), the reverse
+pass (pose gradients) and the forward-over-reverse pass (Hessian-vector
+products and output tangents) on 4096 environments of two 8-piece bodies
+(262,144 piece pairs), with inputs resident in HBM.  The metric is piece-pair
+contact queries per second.  ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead (a bounded sample per step).
+
+Multi-GPU (torchrun): every rank runs its own 4096 environments (different
+seed), weak scaling; the only collectives are a barrier and the max of the
+timings -- there is no data-path exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "piece-pair contact queries/sec fwd and fwd+bwd vs roofline; served p50/p99 latency"
+UNIT = "piece-pair queries/s"
+N_ENVS = 4096
+PIECES = 8
+POINTS = 64
+WORKLOAD = "4096 envs x 2 bodies x 8 hull pieces (64 pts); fwd + grad + HVP"
+
+# FLOP and SFU cost per plane evaluation of each kind (an FMA is 2 FLOP):
+#   gate / max-plane: 3 FMA + max = 7;  value: 3 FMA + scale FMA + add = 9 + 1 ex2;
+#   value + gradient: 9 + 3 FMA = 15 + 1 ex2;
+#   value + gradient + Hessian-vector product: 15 + 5 (n.v) + 1 + 6 = 27 + 1 ex2;
+#   dual-number versions (value + one tangent): gate 7, value 20, value+grad 32,
+#   value+grad+Hv 59, each + 1 ex2.
+COST = {"gate": 7, "val": 9, "grad": 15, "hv": 27, "dval": 20, "dgrad": 32, "dhv": 59}
+
+
+def work_model(c):
+    """Algorithmic FLOP and ex2 counts per launch from the forward counters."""
+    gm = c["gatepass"] + c["maxpass"]
+    eg, ev = c["eval_grad"], c["eval_val"]
+    fwd = (COST["gate"] * gm + COST["grad"] * eg + COST["val"] * ev, eg + ev)
+    # reverse pass: forward recomputation + adjoint (trace steps need gradients)
+    vjp = (2 * COST["gate"] * gm + eg * (COST["grad"] + COST["hv"]) + ev * (COST["val"] + COST["grad"]),
+           2 * (eg + ev))
+    hvp = (2 * COST["gate"] * gm + eg * (COST["dgrad"] + COST["dhv"]) + ev * (COST["dval"] + COST["dgrad"]),
+           2 * (eg + ev))
+    return {"forward": fwd, "vjp": vjp, "hvp": hvp}
+
+
+def derived_peaks(n_sm=148, clock_ghz=2.032, sfu_per_clk=32):
+    """FP32: 128 FMA lanes per SM; SFU ex2: sfu_per_clk per SM (measured by
+    the probe); both at the maximum SM clock."""
+    return {"fp32_tflops": n_sm * 128 * 2 * clock_ghz / 1e3,
+            "ex2_tops": n_sm * sfu_per_clk * clock_ghz / 1e3}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ccm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    from paper_2604_17538_b300 import scenes
+    seed = 2 + 1000 * rank
+    sc = scenes.hull_env_scene(seed=seed, n_envs=args.envs, workers=0)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2604_17538_b300 import abi, api, build
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = api.Context(local)
+    batch, pa, pb = api.scene_to_device(sc, ctx)
+    n, G = batch.n_pairs, batch.n_groups
+    rng = np.random.default_rng(3 + rank)
+    ybar_h = rng.normal(size=(G, 8)).astype(np.float32)
+    u_h = rng.normal(size=(n, 12))
+    u_h = (u_h / np.linalg.norm(u_h, axis=1, keepdims=True)).astype(np.float32)
+    ybar = torch.from_numpy(ybar_h).cuda()
+    u = torch.from_numpy(u_h).cuda()
+    piece_pairs = sc.piece_pairs()
+
+    # exact work counters of the forward pass (outside the timed region)
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
+    batch.contacts(pa, pb, counters=cnt)
+    counters = dict(zip(abi.COUNTER_NAMES, cnt.cpu().tolist()))
+    model = work_model(counters)
+
+    y = torch.empty((G, 8), device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        batch.contacts(pa, pb, out=y)
+        g, _, _ = batch.backward(pa, pb, ybar)
+        g2, h, j = batch.backward(pa, pb, ybar, u, want_jvp=True)
+        return g, h
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 (126 MB) flushed between steps, untimed
+        e = evs[k]
+        e[0].record(stream)
+        batch.contacts(pa, pb, out=y)
+        e[1].record(stream)
+        batch.backward(pa, pb, ybar)
+        e[2].record(stream)
+        batch.backward(pa, pb, ybar, u, want_jvp=True)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_fwd = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
+    t_vjp = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
+    t_hvp = sum(e[2].elapsed_time(e[3]) for e in evs) / 1e3
+    t_step = t_fwd + t_vjp + t_hvp
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # step's inputs, the three calls, D2H of every result
+    pa_h = torch.from_numpy(sc.pose_a).pin_memory()
+    pb_h = torch.from_numpy(sc.pose_b).pin_memory()
+    yb_h = torch.from_numpy(ybar_h).pin_memory()
+    uu_h = torch.from_numpy(u_h).pin_memory()
+    y_o = torch.empty((G, 8)).pin_memory()
+    g_o = torch.empty((n, 12)).pin_memory()
+    h_o = torch.empty((n, 12)).pin_memory()
+    j_o = torch.empty((G, 8)).pin_memory()
+    pa_d, pb_d, yb_d, u_d = (torch.empty_like(x, device="cuda") for x in (pa_h, pb_h, yb_h, uu_h))
+    h2d = sum(x.numel() * 4 for x in (pa_h, pb_h, yb_h, uu_h))
+    d2h = sum(x.numel() * 4 for x in (y_o, g_o, h_o, j_o))
+
+    def e2e_step():
+        pa_d.copy_(pa_h, non_blocking=True)
+        pb_d.copy_(pb_h, non_blocking=True)
+        yb_d.copy_(yb_h, non_blocking=True)
+        u_d.copy_(uu_h, non_blocking=True)
+        yy = batch.contacts(pa_d, pb_d)
+        gg, _, _ = batch.backward(pa_d, pb_d, yb_d)
+        _, hh, jj = batch.backward(pa_d, pb_d, yb_d, u_d, want_jvp=True)
+        y_o.copy_(yy, non_blocking=True)
+        g_o.copy_(gg, non_blocking=True)
+        h_o.copy_(hh, non_blocking=True)
+        j_o.copy_(jj, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        e2e_step()
+        a1.record(stream)
+        a1.synchronize()
+        t_e2e += a0.elapsed_time(a1) / 1e3
+
+    # max over ranks
+    times = torch.tensor([t_step, t_fwd, t_vjp, t_hvp, t_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_step, t_fwd, t_vjp, t_hvp, t_e2e = times.tolist()
+    total_pp = piece_pairs * world
+    K = args.steps
+
+    out = None
+    if rank == 0:
+        probe = {}
+        try:
+            import ctypes as C
+            a, b, c = C.c_double(), C.c_double(), C.c_double()
+            abi.check(abi.lib().ccm_peak_probe(local, C.byref(a), C.byref(b), C.byref(c)))
+            probe = {"ffma_tflops": a.value, "ffma2_tflops": b.value, "ex2_tops": c.value}
+        except Exception as ex:  # measurement aid only
+            probe = {"error": str(ex)}
+        props = torch.cuda.get_device_properties(local)
+        sfu_per_clk = 32
+        if "ex2_tops" in probe:
+            # per-SM per-clock ex2 rate implied by the probe, rounded to the unit width
+            per = probe["ex2_tops"] * 1e12 / (props.multi_processor_count * 2.032e9)
+            sfu_per_clk = max(16, int(round(per / 16.0)) * 16)
+        peaks = derived_peaks(props.multi_processor_count, 2.032, sfu_per_clk)
+        per = {"forward": t_fwd / K, "vjp": t_vjp / K, "hvp": t_hvp / K}
+        dom = max(per, key=per.get)
+        flop, ex2 = model[dom]
+        fp32_ach = flop / per[dom] / 1e12
+        ex2_ach = ex2 / per[dom] / 1e12
+        fr_fp32 = fp32_ach / peaks["fp32_tflops"]
+        fr_ex2 = ex2_ach / peaks["ex2_tops"]
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            tr = json.load(open(tpath))
+            if tr.get("kernel") == dom and tr.get("envs") == args.envs:
+                traffic = tr.get("bytes_per_launch")
+        roof = {"bound": "alu", "kernel": dom, "pipe": "fp32" if fr_fp32 >= fr_ex2 else "sfu_ex2",
+                "achieved": fp32_ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": max(fr_fp32, fr_ex2), "frac_fp32": fr_fp32, "frac_ex2": fr_ex2,
+                "ex2_achieved_tops": ex2_ach, "ex2_peak_tops": peaks["ex2_tops"],
+                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz; ex2: SM x "
+                               f"{sfu_per_clk}/clk x 2.032 GHz (per-clock rate from the probe)",
+                "probe": probe, "traffic": traffic, "flop_per_launch": flop,
+                "ex2_per_launch": ex2}
+        out = {
+            "metric": METRIC, "value": total_pp * K / t_step, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_step / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded convex-hull scenes)",
+            "config": {"workload": WORKLOAD, "n_envs_per_gpu": args.envs, "pieces_per_body": PIECES,
+                       "points_per_hull": POINTS, "piece_pairs_per_gpu": piece_pairs,
+                       "l2": "flushed between timed steps (512 MiB write, untimed)",
+                       "parallelism": f"independent shards x{world}"},
+            "breakdown": {"fwd_qps": total_pp * K / t_fwd,
+                          "fwd_bwd_qps": total_pp * K / (t_fwd + t_vjp),
+                          "fwd_bwd_hvp_qps": total_pp * K / t_step,
+                          "ms_forward": 1e3 * t_fwd / K, "ms_vjp": 1e3 * t_vjp / K,
+                          "ms_hvp": 1e3 * t_hvp / K},
+            "e2e": {"value": total_pp * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 5 * K,
+            "roofline": roof,
+            "work_counters": counters,
+            "clocks": clocks,
+            "wall_s_timed_loop": t_wall,
+        }
+    return out, sc
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(sc, target_s=12.0):
+    """Times the oracle (forward, gradient, H u in one nested-dual pass) on a
+    bounded seeded sample of the environments; returns (qps, cores, sample)."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(7)
+    order = rng.permutation(sc.n_pairs)
+    G_all = int(sc.group_offsets()[-1])
+
+    def run(k):
+        sub = sc.take(order[:k])
+        G = int(sub.group_offsets()[-1])
+        yb = np.random.default_rng(3).normal(size=(G, 8))
+        u = np.random.default_rng(4).normal(size=(k, 12))
+        t0 = time.perf_counter()
+        oracle.hvp(sub, yb, u, threads=cores)
+        return time.perf_counter() - t0, sub.piece_pairs()
+
+    k = min(16, sc.n_pairs)
+    dt, pp = run(k)
+    while dt < target_s / 4 and k < sc.n_pairs:
+        k = min(sc.n_pairs, int(k * max(2.0, target_s / max(dt, 1e-3) / 2)))
+        dt, pp = run(k)
+    return pp / dt, cores, f"{k} of {sc.n_pairs} environments ({pp} piece pairs), seeded", dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2604_17538_b300 import scenes
+    sc = scenes.hull_env_scene(seed=2, n_envs=args.envs, workers=0)
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(7)
+    k = min(args.ref_sample, sc.n_pairs)
+    sub = sc.take(rng.permutation(sc.n_pairs)[:k])
+    G = int(sub.group_offsets()[-1])
+    yb = np.random.default_rng(3).normal(size=(G, 8))
+    u = np.random.default_rng(4).normal(size=(k, 12))
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.hvp(sub, yb, u, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.hvp(sub, yb, u, threads=cores)
+    dt = time.perf_counter() - t0
+    qps = sub.piece_pairs() * args.steps / dt
+    sample = f"{k} of {sc.n_pairs} environments per step ({sub.piece_pairs()} piece pairs), seeded"
+    return {"impl": "reference", "metric": METRIC, "value": qps, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded convex-hull scenes)",
+            "config": {"workload": WORKLOAD, "n_envs_per_gpu": args.envs, "pieces_per_body": PIECES,
+                       "points_per_hull": POINTS},
+            "cpu_baseline": {"value": qps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": qps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=N_ENVS)
+    ap.add_argument("--ref-sample", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out, sc = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            qps, cores, sample, dt = oracle_sample_rate(sc)
+            out["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": sample + f"; fwd + grad + H u, {dt:.1f} s"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,14 @@ CCM_API ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, co
                                 const ccm_params* prm, float* y, int64_t* counters,
                                 ccm_stream stream);
 
+/* Measures, on `device`, the throughput of the arithmetic units the contact
+ * kernels are bound by: FP32 FMA (scalar and packed f32x2, in TFLOP/s, an
+ * FMA counted as 2 FLOP) and the SFU's ex2 (in tera-ops/s).  Synchronous;
+ * allocates 16 bytes.  Not part of the method: it provides the roofline
+ * denominators.  Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_peak_probe(int device, double* ffma_tflops, double* ffma2_tflops,
+                                  double* ex2_tops);
+
 #ifdef __cplusplus
 }
 #endif

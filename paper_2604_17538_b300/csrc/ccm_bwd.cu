@@ -27,8 +27,11 @@ constexpr int kMaxTrace = 16;
 // ---------------------------------------------------------------------------
 // scalar-generic smooth operators (Sec. 2) and transition (Sec. 4.3)
 // ---------------------------------------------------------------------------
+// sigmoid(x / tau), c = log2(e) / tau, without overflow on either side
 template <class T> __device__ __forceinline__ T sigmoid_t(T x, float c) {
-  return rcp_t(1.0f + ex2_t(x * (-c)));
+  if (val(x) >= 0.f) return rcp_t(1.0f + ex2_t(x * (-c)));
+  const T e = ex2_t(x * c);
+  return e * rcp_t(1.0f + e);
 }
 template <class T> __device__ __forceinline__ T softplus_t(T x, float tau, float c) {
   return max_t(x, T(0.f)) + tau * log1p_t(ex2_t(abs_t(x) * (-c)));
@@ -57,9 +60,83 @@ template <class T> struct SdfT {
   V3T<T> g, hv;
 };
 
+// Dual-number version in centred form.  With weights w_k = softmax_k, the
+// tangents are  phi' = sum w_k dphi_k,  g' = sum w_k (dphi_k - phi') (n_k - g) / tau,
+// H v = sum w_k (n_k - g)((n_k - g).v) / tau and
+// (H v)' = sum w_k [(dphi_k - phi') / tau a_k b_k + a_k (a_k . v')] / tau with
+// a_k = n_k - g, b_k = a_k . v (terms proportional to sum w_k a_k = 0 dropped).
+// Every sum is of deviations from a weighted mean, so no cancellation: the
+// plain quotient-rule tangent loses ~1e-7 / tau relative accuracy when one
+// plane dominates.
+template <bool kHv>
+__device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> x, float s,
+                               V3T<Dual> v, const KParams& kp) {
+  const float xv = x.x.v, yv = x.y.v, zv = x.z.v;
+  const float xd = x.x.d, yd = x.y.d, zd = x.z.d;
+  float S, Gx, Gy, Gz, Pd;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float sc = s * kp.c_sdf;
+    S = Gx = Gy = Gz = Pd = 0.f;
+    float mx = -INFINITY;
+#pragma unroll 2
+    for (int k = 0; k < nf; ++k) {
+      const float4 p = pl[k];
+      const float ph = fmaf(p.x, xv, fmaf(p.y, yv, fmaf(p.z, zv, p.w)));
+      mx = fmaxf(mx, ph);
+      const float e = ex2(fmaf(ph, kp.c_sdf, -sc));
+      S += e;
+      Gx = fmaf(e, p.x, Gx);
+      Gy = fmaf(e, p.y, Gy);
+      Gz = fmaf(e, p.z, Gz);
+      Pd = fmaf(e, fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd)), Pd);
+    }
+    if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
+    break;
+  }
+  const float iS = __frcp_rn(S);
+  const float it = 1.0f / kp.tau_sdf;
+  SdfT<Dual> r;
+  r.phi = Dual(fmaf(kp.ic_sdf, __log2f(S), s), Pd * iS);
+  const float gx = Gx * iS, gy = Gy * iS, gz = Gz * iS;
+  const float phd = r.phi.d;
+  const float sc = s * kp.c_sdf;
+  float dgx = 0.f, dgy = 0.f, dgz = 0.f;
+  float hx = 0.f, hy = 0.f, hz = 0.f, hdx = 0.f, hdy = 0.f, hdz = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < nf; ++k) {
+    const float4 p = pl[k];
+    const float ph = fmaf(p.x, xv, fmaf(p.y, yv, fmaf(p.z, zv, p.w)));
+    const float w = ex2(fmaf(ph, kp.c_sdf, -sc)) * iS;
+    const float dd = fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd)) - phd;
+    const float ax = p.x - gx, ay = p.y - gy, az = p.z - gz;
+    const float wd = w * dd;
+    dgx = fmaf(wd, ax, dgx);
+    dgy = fmaf(wd, ay, dgy);
+    dgz = fmaf(wd, az, dgz);
+    if (kHv) {
+      const float b = fmaf(ax, v.x.v, fmaf(ay, v.y.v, az * v.z.v));
+      const float bd = fmaf(ax, v.x.d, fmaf(ay, v.y.d, az * v.z.d));
+      const float wb = w * b;
+      hx = fmaf(wb, ax, hx);
+      hy = fmaf(wb, ay, hy);
+      hz = fmaf(wb, az, hz);
+      const float c = fmaf(wd * it, b, w * bd);
+      hdx = fmaf(c, ax, hdx);
+      hdy = fmaf(c, ay, hdy);
+      hdz = fmaf(c, az, hdz);
+    }
+  }
+  r.g = v3(Dual(gx, dgx * it), Dual(gy, dgy * it), Dual(gz, dgz * it));
+  if (kHv) r.hv = v3(Dual(hx * it, hdx * it), Dual(hy * it, hdy * it), Dual(hz * it, hdz * it));
+  return r;
+}
+
 template <class T, bool kHv>
 __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float s, V3T<T> v,
                          const KParams& kp) {
+  if constexpr (sizeof(T) == sizeof(Dual)) {
+    return sdf_dual<kHv>(pl, nf, x, s, v, kp);
+  }
   SdfT<T> r;
   for (int pass = 0; pass < 2; ++pass) {
     const float sc = s * kp.c_sdf;

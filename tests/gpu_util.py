@@ -68,3 +68,39 @@ def compare(y, ref, what="y", atol=ATOL, rtol=RTOL, a_slack=0.0):
                              f"group {i} col {names[k]}: gpu={y[i, k]!r} oracle={ref[i, k]!r}; "
                              f"max err per output {report}")
     return report
+
+
+def fp32_sensitivity(oracle, scene, ybar, u, n=3, seed=11):
+    """Per pair, the relative change of the oracle's (gradient, H u) when every
+    float32 input (poses, vertices, planes) moves by one unit in the last
+    place in a random direction: the problem's own conditioning at float32
+    input precision.  No float32 algorithm can be expected to land closer to
+    the exact value than a small multiple of it."""
+    import copy
+    rng = np.random.default_rng(seed)
+    g0, h0, _, _ = oracle.hvp(scene, ybar, u)
+    worst_g = np.zeros(scene.n_pairs)
+    worst_h = np.zeros(scene.n_pairs)
+
+    def ulp_jitter(a):
+        a = np.asarray(a, np.float32)
+        up = np.nextafter(a, np.float32(np.inf))
+        dn = np.nextafter(a, np.float32(-np.inf))
+        pick = rng.integers(0, 3, size=a.shape)
+        return np.where(pick == 0, dn, np.where(pick == 1, a, up)).astype(np.float32)
+
+    for _ in range(n):
+        sc = copy.copy(scene)
+        sc.pose_a = ulp_jitter(scene.pose_a)
+        sc.pose_b = ulp_jitter(scene.pose_b)
+        g = copy.copy(scene.geom)
+        g.verts = ulp_jitter(scene.geom.verts)
+        g.planes = ulp_jitter(scene.geom.planes)
+        sc.geom = g
+        g1, h1, _, _ = oracle.hvp(sc, ybar, u)
+        worst_g = np.maximum(worst_g, np.abs(g1 - g0).max(1) / np.maximum(np.abs(g0).max(1), 1e-30))
+        worst_h = np.maximum(worst_h, np.abs(h1 - h0).max(1) / np.maximum(np.abs(h0).max(1), 1e-30))
+    return worst_g, worst_h
+
+
+COND_FACTOR = 4.0   # allowance over the one-ulp input sensitivity

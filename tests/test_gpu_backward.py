@@ -4,7 +4,7 @@ the C ABI and through torch.autograd (double backward)."""
 import numpy as np
 import pytest
 
-from gpu_util import GRAD_RTOL
+from gpu_util import COND_FACTOR, GRAD_RTOL, fp32_sensitivity
 from paper_2604_17538_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -35,7 +35,8 @@ def _inputs(sc, seed=0):
 
 
 def _per_pair_check(g, o, what, rtol=GRAD_RTOL, floor=1e-6):
-    """||g - o||_inf <= rtol ||o||_inf per pair (rows)."""
+    """||g - o||_inf <= rtol ||o||_inf per pair (rows); rtol may be per pair."""
+    assert np.all(np.isfinite(g)), f"{what}: non-finite values"
     err = np.abs(g - o).max(1)
     scale = np.abs(o).max(1)
     bad = err > rtol * scale + floor
@@ -61,11 +62,19 @@ def test_gradient_hvp_jvp_match_oracle(oracle_lib, ctx, cases, name):
     torch.cuda.synchronize()
     # the oracle sees exactly the float32 values the GPU sees
     go, hvo, jvo, _ = oracle_lib.hvp(sc, ybar.astype(np.float32), u.astype(np.float32))
-    rg = _per_pair_check(g.double().cpu().numpy(), go, f"{name} gradient")
-    _per_pair_check(g2.double().cpu().numpy(), go, f"{name} gradient (dual pass)")
-    rh = _per_pair_check(hv.double().cpu().numpy(), hvo, f"{name} H u")
+    # bar: 1e-3 relative, widened per pair only where the problem's one-ulp
+    # float32 input sensitivity (times COND_FACTOR) exceeds it
+    kg, kh = fp32_sensitivity(oracle_lib, sc, ybar.astype(np.float32), u.astype(np.float32))
+    tol_g = np.maximum(GRAD_RTOL, COND_FACTOR * kg)
+    tol_h = np.maximum(GRAD_RTOL, COND_FACTOR * kh)
+    print(f"{name}: pairs with a widened bar: grad {int((tol_g > GRAD_RTOL).sum())}, "
+          f"hvp {int((tol_h > GRAD_RTOL).sum())} of {sc.n_pairs}")
+    rg = _per_pair_check(g.double().cpu().numpy(), go, f"{name} gradient", tol_g)
+    _per_pair_check(g2.double().cpu().numpy(), go, f"{name} gradient (dual pass)", tol_g)
+    rh = _per_pair_check(hv.double().cpu().numpy(), hvo, f"{name} H u", tol_h)
     off = sc.group_offsets()
     jvg = jv.double().cpu().numpy()
+    assert np.all(np.isfinite(jvg))
     jmax = np.array([np.abs(jvg[off[i]:off[i + 1]] - jvo[off[i]:off[i + 1]]).max()
                      for i in range(sc.n_pairs)])
     jsc = np.array([np.abs(jvo[off[i]:off[i + 1]]).max() for i in range(sc.n_pairs)])
@@ -107,6 +116,9 @@ def test_autograd_double_backward(oracle_lib, ctx, cases):
     ha, hb = torch.autograd.grad((g * ut).sum(), (ta, tb))
     h = torch.cat([ha, hb], 1)
     go, hvo, _, _ = oracle_lib.hvp(sc, ybar.astype(np.float32), u.astype(np.float32))
-    _per_pair_check(g.detach().double().cpu().numpy(), go, "autograd gradient")
-    _per_pair_check(h.double().cpu().numpy(), hvo, "autograd H u")
+    kg, kh = fp32_sensitivity(oracle_lib, sc, ybar.astype(np.float32), u.astype(np.float32))
+    _per_pair_check(g.detach().double().cpu().numpy(), go, "autograd gradient",
+                    np.maximum(GRAD_RTOL, COND_FACTOR * kg))
+    _per_pair_check(h.double().cpu().numpy(), hvo, "autograd H u",
+                    np.maximum(GRAD_RTOL, COND_FACTOR * kh))
     batch.close()
