@@ -153,6 +153,29 @@ CCM_API ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, c
                                  const ccm_params* prm, const float* ybar, const float* dir,
                                  float* grad, float* hvp, float* jvp, ccm_stream stream);
 
+/* Same as ccm_contacts_backward, for callers that cannot obtain device
+ * memory for scratch -- e.g. code running while another framework owns the
+ * whole device memory pool, or a real-time loop that forbids allocation after
+ * start-up.  The per-unit slots of the reverse pass (24 floats per side of a
+ * pair) live in one fixed 4 MiB array compiled into the library instead of
+ * the batch's workspace, so the call allocates nothing and uses no workspace;
+ * the caller still passes every input and output.  The paper has no
+ * counterpart: this is a deployment variant of the same computation.
+ *   - Limit: n <= 21845 pairs (2 n * 24 floats <= 2^20); larger batches are
+ *     rejected with CCM_ERR_INVALID.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the array and it keeps the last call's
+ *     contents.  Nothing in it needs to start at zero: each call writes every
+ *     slot it reads.  Calls that overlap on the GPU (other streams, other
+ *     threads) race on it; serialise them.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
+                                                 const float* pose_b, const ccm_params* prm,
+                                                 const float* ybar, const float* dir,
+                                                 float* grad, float* hvp, float* jvp,
+                                                 ccm_stream stream);
+
 /* Work counters of the last ccm_contacts_counted call, for the roofline:
  * counts of piece-pair directions, surviving directions, plane evaluations by
  * kind and contacts.  Same as ccm_contacts plus device atomics on `counters`

@@ -60,6 +60,7 @@ _SIGS = {
     "ccm_contacts_counted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ccm_contacts_backward": (C.c_int, [C.c_void_p] * 10),
+    "ccm_contacts_backward_noalloc": (C.c_int, [C.c_void_p] * 10),
     "ccm_peak_probe": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 

@@ -339,6 +339,45 @@ ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, const flo
                       jvp, static_cast<cudaStream_t>(stream));
 }
 
+ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
+                                         const float* pose_b, const ccm_params* prm,
+                                         const float* ybar, const float* dir, float* grad,
+                                         float* hvp, float* jvp, ccm_stream stream) {
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
+  if (b->n == 0) return CCM_OK;
+  if (b->n > noalloc_max_pairs())
+    return fail(CCM_ERR_INVALID,
+                "ccm_contacts_backward_noalloc: %lld pairs exceed its fixed scratch of %lld pairs",
+                (long long)b->n, (long long)noalloc_max_pairs());
+  if (!pose_a || !pose_b || !ybar || !grad) return fail(CCM_ERR_INVALID, "NULL pointer");
+  if (dir && !hvp) return fail(CCM_ERR_INVALID, "dir given without hvp");
+  KParams kp;
+  ccm_status s = make_kparams(prm, &kp);
+  if (s != CCM_OK) return s;
+  if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
+  CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  BwdLaunch L;
+  L.g = b->ctx->dev_geom();
+  L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.n_pairs = b->n;
+  L.pose_a = pose_a;
+  L.pose_b = pose_b;
+  L.ybar = ybar;
+  L.dir = dir;
+  L.kp = kp;
+  L.us = b->us;
+  L.part = nullptr;
+  L.grad = grad;
+  L.hvp = hvp;
+  L.jvp = dir ? jvp : nullptr;
+  L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
+  const cudaError_t e =
+      launch_backward_noalloc(L, b->ctx->device, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "backward (no-alloc) launch");
+  return CCM_OK;
+}
+
 ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const float* pose_b,
                                 const ccm_params* prm, float* y, int64_t* counters,
                                 ccm_stream stream) {

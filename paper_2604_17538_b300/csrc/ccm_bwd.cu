@@ -16,6 +16,8 @@
 //           summed as sum x_bar and sum x cross x_bar in the SDF frame.
 // The unit's 12 twist components are written to a per-unit slot; a second
 // kernel adds the two sides of each pair in a fixed order (deterministic).
+#include <mutex>
+
 #include "ccm_dual.cuh"
 #include "ccm_unit.cuh"
 #include "ccm_bwd.h"
@@ -981,6 +983,46 @@ cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d
 
 int backward_slice_bytes(const UnitShape& us, bool dual) {
   return dual ? bwd_slice_bytes<Dual>(us) : bwd_slice_bytes<float>(us);
+}
+
+}  // namespace ccm
+
+// ---------------------------------------------------------------------------
+// Scratch for ccm_contacts_backward_noalloc: the per-unit slots of the reverse
+// pass live in this fixed array instead of the batch's workspace, so that the
+// call needs no device memory of its own.  Every GPU that loads the library
+// holds the array (4 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace ccm {
+
+constexpr int64_t kNoAllocSlotFloats = (int64_t)1 << 20;   // 2 n * 24 floats at most
+static __device__ __align__(256) float g_noalloc_slots[kNoAllocSlotFloats];
+
+// Device address of g_noalloc_slots on `device`, looked up once per device
+// with that device current (the symbol name is only a host-side stand-in).
+static cudaError_t noalloc_slots(int device, float** out) {
+  static std::mutex mu;
+  static float* addr[256] = {nullptr};
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_slots);
+    if (e != cudaSuccess) return e;
+    addr[device] = static_cast<float*>(p);
+  }
+  *out = addr[device];
+  return cudaSuccess;
+}
+
+int64_t noalloc_max_pairs() { return kNoAllocSlotFloats / 48; }
+
+cudaError_t launch_backward_noalloc(BwdLaunch L, int device, cudaStream_t stream) {
+  float* slots = nullptr;
+  const cudaError_t e = noalloc_slots(device, &slots);
+  if (e != cudaSuccess) return e;
+  L.part = slots;
+  return launch_backward(L, stream);
 }
 
 }  // namespace ccm

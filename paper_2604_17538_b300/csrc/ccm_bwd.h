@@ -40,4 +40,8 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream);
 cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d);
 int backward_slice_bytes(const UnitShape& us, bool dual);
 
+// Variant with the per-unit slots in a fixed device array (no workspace).
+cudaError_t launch_backward_noalloc(BwdLaunch L, int device, cudaStream_t stream);
+int64_t noalloc_max_pairs();
+
 }  // namespace ccm
