@@ -57,6 +57,15 @@ def work_model(c):
     return {"forward": fwd, "vjp": vjp, "hvp": hvp}
 
 
+def kernel_source_hash():
+    """sha256 of the CUDA sources, to tell whether recorded ncu counters still apply."""
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_2604_17538_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(d, "*.cu*"))) + sorted(glob.glob(os.path.join(d, "*.h")))
+    return hashlib.sha256(b"".join(open(f, "rb").read() for f in files)).hexdigest()
+
+
 def derived_peaks(n_sm=148, clock_ghz=2.032, sfu_per_clk=32):
     """FP32: 128 FMA lanes per SM; SFU ex2: sfu_per_clk per SM (measured by
     the probe); both at the maximum SM clock."""
@@ -265,7 +274,9 @@ def run_ours(args, rank, world):
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
             tr = json.load(open(tpath))
-            if tr.get("kernel") == dom and tr.get("envs") == args.envs:
+            # counters only count while the kernel sources are the ones captured
+            if (tr.get("kernel") == dom and tr.get("envs") == args.envs
+                    and tr.get("source_sha256") == kernel_source_hash()):
                 traffic = tr.get("bytes_per_launch")
         roof = {"bound": "alu", "kernel": dom, "pipe": "fp32" if fr_fp32 >= fr_ex2 else "sfu_ex2",
                 "achieved": fp32_ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
