@@ -136,6 +136,23 @@ CCM_API void ccm_batch_destroy(ccm_batch batch);
  * offsets off[n+1] copied to host memory. */
 CCM_API ccm_status ccm_batch_info(ccm_batch batch, int64_t* n_pairs, int64_t* n_groups, int64_t* off);
 
+/* Launch shape of a batch.  The kernels gather the live piece pairs of a body
+ * pair into lists whose vertex and edge items fill the warp's shared-memory
+ * budgets below; larger lists keep more lanes busy, smaller ones leave room
+ * for more resident warps.  Defaults: 256 / 512 / 256 / 512 items, 2 forward
+ * warps per block.  Budgets below the batch's largest piece are raised to it.
+ * Results do not depend on the tuning beyond float rounding order. */
+typedef struct {
+  int32_t item_v, item_e;     /* forward: vertex / edge items per list */
+  int32_t item_vb, item_eb;   /* reverse pass: vertex / edge items per list */
+  int32_t fwd_warps;          /* forward warps per block, 1..4 */
+  int32_t reserved[3];
+} ccm_tuning;
+CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
+/* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of
+ * range or too large for shared memory), CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t);
+
 /* Forward pass (Sec. 4.2-4.4).  pose_a, pose_b: device [n,12] float32; y:
  * device [G,8] float32, fully overwritten.  Asynchronous on `stream`.
  * Errors: CCM_ERR_INVALID (NULL pointer, bad params), CCM_ERR_CUDA. */

@@ -44,6 +44,11 @@ class ccm_body_desc(C.Structure):
                 ("edges", C.c_void_p)]
 
 
+class ccm_tuning(C.Structure):
+    _fields_ = [("item_v", C.c_int32), ("item_e", C.c_int32), ("item_vb", C.c_int32),
+                ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
 _SIGS = {
     "ccm_default_params": (None, [C.c_void_p]),
     "ccm_create": (C.c_int, [C.c_int, C.c_size_t, C.c_void_p]),
@@ -55,6 +60,8 @@ _SIGS = {
     "ccm_batch_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ccm_batch_destroy": (None, [C.c_void_p]),
     "ccm_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ccm_batch_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ccm_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ccm_contacts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     "ccm_contacts_counted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

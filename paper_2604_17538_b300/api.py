@@ -91,6 +91,18 @@ class Batch:
         self.group_offsets = np.zeros(self.n_pairs + 1, np.int64)
         check(lib().ccm_batch_info(h, None, None, ptr(self.group_offsets)))
 
+    def get_tuning(self) -> dict:
+        t = abi.ccm_tuning()
+        check(lib().ccm_batch_get_tuning(self.handle, C.byref(t)))
+        return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps")}
+
+    def set_tuning(self, **kw):
+        t = abi.ccm_tuning()
+        check(lib().ccm_batch_get_tuning(self.handle, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        check(lib().ccm_batch_set_tuning(self.handle, C.byref(t)))
+
     def close(self):
         if self.handle:
             lib().ccm_batch_destroy(self.handle)

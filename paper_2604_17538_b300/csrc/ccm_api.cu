@@ -326,6 +326,19 @@ ccm_status ccm_batch_info(ccm_batch batch, int64_t* n_pairs, int64_t* n_groups, 
   return CCM_OK;
 }
 
+ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out) {
+  if (!batch || !out) return fail(CCM_ERR_INVALID, "bad arguments");
+  *out = reinterpret_cast<Batch*>(batch)->tuning;
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t) {
+  if (!batch || !t) return fail(CCM_ERR_INVALID, "bad arguments");
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  return apply_tuning(b->ctx, b, *t);
+}
+
 ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
                         const ccm_params* prm, float* y, ccm_stream stream) {
   return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr,
@@ -398,6 +411,7 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
   bt->goff.assign(n + 1, 0);
   int64_t G = 0;
   int vmax = 1, fmax = 1, emax = 1, s_planes = 1, s_pieces = 1, f_verts = 1, f_edges = 1;
+  int s_pieces_max_any = 1;
   for (int64_t i = 0; i < n; ++i) {
     int32_t a, b;
     ccm_status s;
@@ -426,44 +440,75 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
         sp += pr.nf;
         if (p < kGroupsPerChunk) { cv += pr.nv; ce += pr.ne; }
       }
+      s_pieces_max_any = std::max(s_pieces_max_any, br.np);
       s_planes = std::max(s_planes, sp);
       s_pieces = std::max(s_pieces, br.np);
       f_verts = std::max(f_verts, cv);
       f_edges = std::max(f_edges, ce);
     }
   }
+  BatchMaxima& mx = bt->mx;
+  mx.vmax = vmax; mx.fmax = fmax; mx.emax = emax; mx.s_planes = s_planes;
+  mx.s_pieces = s_pieces; mx.f_verts = f_verts; mx.f_edges = f_edges;
+  mx.pieces_any = s_pieces_max_any;
+  ccm_status s;
+  if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
+  std::vector<float> zeros_part((size_t)std::max<int64_t>(1, 2 * n) * 24, 0.f);
+  if ((s = upload(bt->d_part, zeros_part, "reverse-pass slots")) != CCM_OK) return s;
+  ccm_tuning t;
+  default_tuning(&t);
+  return apply_tuning(c, bt, t);
+}
+
+void default_tuning(ccm_tuning* t) {
+  std::memset(t, 0, sizeof(*t));
+  t->item_v = 256;
+  t->item_e = 512;
+  t->item_vb = 256;
+  t->item_eb = 512;
+  t->fwd_warps = 2;
+}
+
+// Shared-memory budgets and launch shapes of a batch for the tuning `t`
+// (budgets are raised to hold the largest piece of the batch).
+ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
+  if (t.item_v < 1 || t.item_e < 1 || t.item_vb < 1 || t.item_eb < 1 || t.item_v > 8192 ||
+      t.item_e > 16384 || t.item_vb > 8192 || t.item_eb > 16384 || t.fwd_warps < 1 ||
+      t.fwd_warps > 4)
+    return fail(CCM_ERR_INVALID, "tuning out of range");
+  const BatchMaxima& mx = bt->mx;
   UnitShape us{};
-  us.plane_budget = std::max(fmax, std::min(s_planes, 1024));
-  us.spiece_budget = std::min(s_pieces, 256);
-  us.vert_budget = std::max(vmax, std::min(f_verts, 512));
-  us.edge_budget = std::max(emax, std::min(f_edges, 1536));
-  us.item_v = std::max(vmax, 256);
-  us.item_e = std::max(emax, 512);
+  us.plane_budget = std::max(mx.fmax, std::min(mx.s_planes, 1024));
+  us.spiece_budget = std::min(mx.s_pieces, 256);
+  us.vert_budget = std::max(mx.vmax, std::min(mx.f_verts, 512));
+  us.edge_budget = std::max(mx.emax, std::min(mx.f_edges, 1536));
+  us.item_v = std::max(mx.vmax, t.item_v);
+  us.item_e = std::max(mx.emax, t.item_e);
+  us.item_vb = std::max(mx.vmax, t.item_vb);
+  us.item_eb = std::max(mx.emax, t.item_eb);
+  us.groups = std::min(kGroupsPerChunk, mx.pieces_any);
   us.slice_bytes = unit_slice_bytes(us);
-  us.warps = 2;
-  if (us.warps * us.slice_bytes > c->smem_optin) us.warps = 1;
+  us.warps = t.fwd_warps;
+  while (us.warps > 1 && us.warps * us.slice_bytes > c->smem_optin) --us.warps;
   if (us.slice_bytes > c->smem_optin)
     return fail(CCM_ERR_INVALID, "pieces too large: %d bytes of shared memory per warp",
                 us.slice_bytes);
-  bt->us = us;
-  ccm_status s;
-  if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
+  if (backward_slice_bytes(us, true) > c->smem_optin)
+    return fail(CCM_ERR_INVALID, "pieces too large for the reverse pass");
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
   int per_sm = 1;
   cudaError_t e = configure_forward(us, &per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "configure_forward");
-  const int64_t units = 2 * n;
-  bt->grid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((units + us.warps - 1) / us.warps, (int64_t)c->n_sm * std::max(1, per_sm)));
-  // reverse pass: one warp per block, its own slice layout
-  if (backward_slice_bytes(us, true) > c->smem_optin)
-    return fail(CCM_ERR_INVALID, "pieces too large for the reverse pass");
   int per_f = 1, per_d = 1;
   e = configure_backward(us, &per_f, &per_d);
   if (e != cudaSuccess) return cuda_fail(e, "configure_backward");
+  const int64_t units = 2 * bt->n;
+  bt->us = us;
+  bt->tuning = t;
+  bt->grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((units + us.warps - 1) / us.warps, (int64_t)c->n_sm * std::max(1, per_sm)));
   bt->bwd_grid_f = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_f)));
   bt->bwd_grid_d = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_d)));
-  std::vector<float> zeros_part((size_t)std::max<int64_t>(1, units) * 24, 0.f);
-  if ((s = upload(bt->d_part, zeros_part, "reverse-pass slots")) != CCM_OK) return s;
   return CCM_OK;
 }
 

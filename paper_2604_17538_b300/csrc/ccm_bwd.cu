@@ -24,7 +24,6 @@
 
 namespace ccm {
 
-constexpr int kMaxTrace = 16;
 
 // ---------------------------------------------------------------------------
 // scalar-generic smooth operators (Sec. 2) and transition (Sec. 4.3)
@@ -70,9 +69,11 @@ template <class T> struct SdfT {
 // Every sum is of deviations from a weighted mean, so no cancellation: the
 // plain quotient-rule tangent loses ~1e-7 / tau relative accuracy when one
 // plane dominates.
-template <bool kHv>
+// kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian-vector product
+template <int kMode>
 __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> x, float s,
                                V3T<Dual> v, const KParams& kp) {
+  constexpr bool kHv = kMode == 2;
   const float xv = x.x.v, yv = x.y.v, zv = x.z.v;
   const float xd = x.x.d, yd = x.y.d, zd = x.z.d;
   float S, Gx, Gy, Gz, Pd;
@@ -99,6 +100,7 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
   const float it = 1.0f / kp.tau_sdf;
   SdfT<Dual> r;
   r.phi = Dual(fmaf(kp.ic_sdf, __log2f(S), s), Pd * iS);
+  if (kMode == 0) return r;
   const float gx = Gx * iS, gy = Gy * iS, gz = Gz * iS;
   const float phd = r.phi.d;
   const float sc = s * kp.c_sdf;
@@ -133,12 +135,14 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
   return r;
 }
 
-template <class T, bool kHv>
+template <class T, int kMode>
 __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float s, V3T<T> v,
                          const KParams& kp) {
   if constexpr (sizeof(T) == sizeof(Dual)) {
-    return sdf_dual<kHv>(pl, nf, x, s, v, kp);
+    return sdf_dual<kMode>(pl, nf, x, s, v, kp);
   }
+  constexpr bool kHv = kMode == 2;
+  constexpr bool kGrad = kMode >= 1;
   SdfT<T> r;
   for (int pass = 0; pass < 2; ++pass) {
     const float sc = s * kp.c_sdf;
@@ -151,9 +155,11 @@ __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float 
       mx = fmaxf(mx, val(ph));
       const T e = ex2_t(fma_t(ph, kp.c_sdf, T(-sc)));
       S += e;
-      gx = fma_t(e, p.x, gx);
-      gy = fma_t(e, p.y, gy);
-      gz = fma_t(e, p.z, gz);
+      if (kGrad) {
+        gx = fma_t(e, p.x, gx);
+        gy = fma_t(e, p.y, gy);
+        gz = fma_t(e, p.z, gz);
+      }
       if (kHv) {
         const T en = e * fma_t(p.x, v.x, fma_t(p.y, v.y, p.z * v.z));
         hx = fma_t(en, p.x, hx);
@@ -164,6 +170,7 @@ __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float 
     if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
     const T inv = rcp_t(S);
     r.phi = fma_t(T(kp.ic_sdf), log2_t(S), T(s));
+    if (!kGrad) break;
     r.g = v3(gx * inv, gy * inv, gz * inv);
     if (kHv) {
       const T gv = dot3(r.g, v);
@@ -360,17 +367,17 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
   b += align16i(8 * u.spiece_budget);
   b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   b += align16i(4 * u.edge_budget);
-  b += 16 * kGroupsPerChunk * 2;
-  b += align16i((int)sizeof(PartT<T>) * kGroupsPerChunk);
-  b += align16i((int)sizeof(Coef<T>) * kGroupsPerChunk);
+  b += 16 * u.groups * 2;
+  b += align16i((int)sizeof(PartT<T>) * u.groups);
+  b += align16i((int)sizeof(Coef<T>) * u.groups);
   b += align16i(4 * kPending) * 2;
   b += align16i(4 * (kPending + 1)) * 2;
-  b += align16i(4 * u.item_v);
-  b += align16i((int)sizeof(T) * u.item_v);
-  b += align16i((int)sizeof(V3T<T>) * u.item_v);
-  b += align16i(2 * u.item_v);
-  b += align16i(2 * u.item_e);
-  b += align16i(u.item_v);
+  b += align16i(4 * u.item_vb);
+  b += align16i((int)sizeof(T) * u.item_vb);
+  b += align16i((int)sizeof(V3T<T>) * u.item_vb);
+  b += align16i(2 * u.item_vb);
+  b += align16i(2 * u.item_eb);
+  b += align16i(u.item_vb);
   return b;
 }
 
@@ -380,19 +387,19 @@ template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, con
   s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * u.spiece_budget);
   s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   s.edges = reinterpret_cast<uint32_t*>(p);    p += align16i(4 * u.edge_budget);
-  s.fp = reinterpret_cast<int4*>(p);           p += 16 * kGroupsPerChunk;
-  s.fs = reinterpret_cast<float4*>(p);         p += 16 * kGroupsPerChunk;
-  s.acc = reinterpret_cast<PartT<T>*>(p);      p += align16i((int)sizeof(PartT<T>) * kGroupsPerChunk);
-  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i((int)sizeof(Coef<T>) * kGroupsPerChunk);
+  s.fp = reinterpret_cast<int4*>(p);           p += 16 * u.groups;
+  s.fs = reinterpret_cast<float4*>(p);         p += 16 * u.groups;
+  s.acc = reinterpret_cast<PartT<T>*>(p);      p += align16i((int)sizeof(PartT<T>) * u.groups);
+  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i((int)sizeof(Coef<T>) * u.groups);
   s.dir = reinterpret_cast<int*>(p);           p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);          p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
   s.pe = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
-  s.m = reinterpret_cast<float*>(p);           p += align16i(4 * u.item_v);
-  s.phi = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * u.item_v);
-  s.grad = reinterpret_cast<V3T<T>*>(p);       p += align16i((int)sizeof(V3T<T>) * u.item_v);
-  s.vlist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_v);
-  s.elist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_e);
+  s.m = reinterpret_cast<float*>(p);           p += align16i(4 * u.item_vb);
+  s.phi = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * u.item_vb);
+  s.grad = reinterpret_cast<V3T<T>*>(p);       p += align16i((int)sizeof(V3T<T>) * u.item_vb);
+  s.vlist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_vb);
+  s.elist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_eb);
   s.need = reinterpret_cast<uint8_t*>(p);
   return s;
 }
@@ -408,7 +415,7 @@ template <class T> __device__ __forceinline__ T gstep_d(T phi, float c) {  // it
   return fma_t(phi * (c * kLn2), s * (1.0f - s), s);
 }
 
-template <class T, bool kAdj>
+template <class T, bool kAdj, int kK>
 __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> xII, float mI0,
                        float mII0, T phI0, T phII0, V3T<T> gI0, V3T<T> gII0, const Coef<T>& k,
                        const KParams& kp, SdfT<T>& c, V3T<T>& pe, V3T<T>& xbI, V3T<T>& xbII) {
@@ -416,9 +423,12 @@ __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> 
   const T L = sqrt_t(dot3(d, d));
   const T iL = rcp_t(L);
   const V3T<T> e = v3(d.x * iL, d.y * iL, d.z * iL);
-  const int K = kp.trace_iters;
-  T a[kMaxTrace + 1], b[kMaxTrace + 1], pa[kMaxTrace], pb[kMaxTrace];
-  V3T<T> ga[kMaxTrace], gb[kMaxTrace];
+  // kK > 0: exactly kK steps (compile-time, fully unrolled, registers);
+  // kK == 0: trace_iters steps (up to 16) with arrays in local memory
+  constexpr int kN = kK > 0 ? kK : 16;
+  const int K = kK > 0 ? kK : kp.trace_iters;
+  T a[kN + 1], b[kN + 1], pa[kN], pb[kN];
+  V3T<T> ga[kN], gb[kN];
   a[0] = T(0.f);
   b[0] = L;
   pa[0] = phI0;
@@ -435,21 +445,23 @@ __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> 
                          fma_t(a[s + 1], e.z, xI.z));
     const V3T<T> qb = v3(fma_t(b[s + 1], e.x, xI.x), fma_t(b[s + 1], e.y, xI.y),
                          fma_t(b[s + 1], e.z, xI.z));
-    const SdfT<T> ra = sdf_t<T, false>(pl, nf, qa, ma - fabsf(val(sa)), qa, kp);
-    const SdfT<T> rb = sdf_t<T, false>(pl, nf, qb, mb - fabsf(val(sb)), qb, kp);
-    pa[s + 1] = ra.phi; ga[s + 1] = ra.g;
-    pb[s + 1] = rb.phi; gb[s + 1] = rb.g;
+    const SdfT<T> ra = sdf_t<T, kAdj ? 1 : 0>(pl, nf, qa, ma - fabsf(val(sa)), qa, kp);
+    const SdfT<T> rb = sdf_t<T, kAdj ? 1 : 0>(pl, nf, qb, mb - fabsf(val(sb)), qb, kp);
+    pa[s + 1] = ra.phi;
+    pb[s + 1] = rb.phi;
+    if (kAdj) { ga[s + 1] = ra.g; gb[s + 1] = rb.g; }
     // exact max-plane values are not tracked here; a looser lower bound only
     // risks the (exact) repeat pass inside sdf_t
     ma = val(ra.phi) - kp.tau_sdf * logf((float)nf) - 1e-6f;
     mb = val(rb.phi) - kp.tau_sdf * logf((float)nf) - 1e-6f;
   }
-  const T cI = softclip0_t(a[K], L, kp.tau_clip, kp.c_clip);
-  const T cII = softclip0_t(b[K], L, kp.tau_clip, kp.c_clip);
+  const T aK = a[K], bK = b[K];
+  const T cI = softclip0_t(aK, L, kp.tau_clip, kp.c_clip);
+  const T cII = softclip0_t(bK, L, kp.tau_clip, kp.c_clip);
   const T am = 0.5f * (cI + cII);
   pe = v3(fma_t(am, e.x, xI.x), fma_t(am, e.y, xI.y), fma_t(am, e.z, xI.z));
   const float lb = fmaxf(mI0 - val(am), mII0 - (val(L) - val(am)));
-  c = sdf_t<T, kAdj>(pl, nf, pe, lb, k.nb, kp);
+  c = sdf_t<T, kAdj ? 2 : 1>(pl, nf, pe, lb, k.nb, kp);
   if (!kAdj) return;
   // ---- reverse sweep ----
   const V3T<T> xb = contact_adjoint(c, pe, k, kp);
@@ -457,8 +469,8 @@ __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> 
   V3T<T> eb = v3(am * xb.x, am * xb.y, am * xb.z);  // d pe / d e = am I
   const T amb = dot3(xb, e);
   // soft clip: d sc/d alpha = sig(alpha/tc) - sig((alpha - L)/tc), d sc/dL = sig((alpha - L)/tc)
-  const T sIa = sigmoid_t(a[K], kp.c_clip), sIb = sigmoid_t(a[K] - L, kp.c_clip);
-  const T sJa = sigmoid_t(b[K], kp.c_clip), sJb = sigmoid_t(b[K] - L, kp.c_clip);
+  const T sIa = sigmoid_t(aK, kp.c_clip), sIb = sigmoid_t(aK - L, kp.c_clip);
+  const T sJa = sigmoid_t(bK, kp.c_clip), sJb = sigmoid_t(bK - L, kp.c_clip);
   T abar = 0.5f * amb * (sIa - sIb);
   T bbar = 0.5f * amb * (sJa - sJb);
   T Lb = 0.5f * amb * (sIb + sJb);
@@ -494,7 +506,7 @@ template <class T> struct Accum {
   V3T<T> X1, X2;   // sum x_bar, sum x cross x_bar (S frame)
 };
 
-template <class T, int kPass>
+template <class T, int kPass, int kK>
 __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, const KParams& kp,
                              int lane, Accum<T>& ac) {
   const int* dsub = sl.dsub;
@@ -555,7 +567,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
       const float m = sl.m[t];
       key = g;
       if (kPass == 1) {
-        const SdfT<T> e = sdf_t<T, false>(sl.planes + s.x, s.y, x, m, x, kp);
+        const SdfT<T> e = sdf_t<T, 1>(sl.planes + s.x, s.y, x, m, x, kp);
         sl.phi[t] = e.phi;
         if (m < kp.d_max) {
           T w, wp;
@@ -565,7 +577,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
         }
       } else {
         const Coef<T>& cf = sl.coef[g];
-        const SdfT<T> e = sdf_t<T, true>(sl.planes + s.x, s.y, x, m, cf.nb, kp);
+        const SdfT<T> e = sdf_t<T, 2>(sl.planes + s.x, s.y, x, m, cf.nb, kp);
         sl.phi[t] = e.phi;
         sl.grad[t] = e.g;
         if (m < kp.d_max && cf.live) {
@@ -602,14 +614,14 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
       const Coef<T>& cf = sl.coef[g];
       if (kPass == 1) {
         const V3T<T> z = v3(T(0.f), T(0.f), T(0.f));
-        edge_t<T, false>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
+        edge_t<T, false, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
                          sl.phi[t1v], z, z, cf, kp, sc, pe, xbI, xbII);
         T w, wp;
         transition_t(sc.phi, kp, w, wp);
         const T dc = fma_t(w, sc.phi - kp.d_max, T(kp.d_max));
         part_from_contact(c, w, dc, pe, sc.g, kp.c_blend);
       } else if (cf.live) {
-        edge_t<T, true>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
+        edge_t<T, true, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
                         sl.phi[t1v], sl.grad[t0v], sl.grad[t1v], cf, kp, sc, pe, xbI, xbII);
         ac.X1 = v3(ac.X1.x + xbI.x + xbII.x, ac.X1.y + xbI.y + xbII.y, ac.X1.z + xbI.z + xbII.z);
         ac.X2 = v3(ac.X2.x + (a.y * xbI.z - a.z * xbI.y) + (b.y * xbII.z - b.z * xbII.y),
@@ -622,7 +634,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
   __syncwarp();
 }
 
-template <class T, int kPass>
+template <class T, int kPass, int kK>
 __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& us,
                                 const KParams& kp, int lane, Accum<T>& ac) {
   int start = 0;
@@ -641,7 +653,7 @@ __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& 
       const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
       if (lane >= o) { iv += a; ie += b; }
     }
-    const bool fits = r < np && iv <= us.item_v && ie <= us.item_e;
+    const bool fits = r < np && iv <= us.item_vb && ie <= us.item_eb;
     const int nd = __popc(__ballot_sync(kFull, fits));
     if (lane < nd) {
       sl.dsub[lane] = code;
@@ -650,13 +662,13 @@ __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& 
     }
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
-    bwd_run_list<T, kPass>(sl, nd, TV, TE, kp, lane, ac);
+    bwd_run_list<T, kPass, kK>(sl, nd, TV, TE, kp, lane, ac);
     start += nd;
   }
 }
 
 // all live directions of the staged F chunk against S, chunk by chunk
-template <class T, int kPass>
+template <class T, int kPass, int kK>
 __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec& S, int nfc,
                           float margin, const UnitShape& us, const KParams& kp, int lane,
                           Accum<T>& ac) {
@@ -695,14 +707,14 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
       const unsigned bal = __ballot_sync(kFull, live);
       const int nl = __popc(bal);
       if (np + nl > kPending) {
-        bwd_run_pending<T, kPass>(sl, np, us, kp, lane, ac);
+        bwd_run_pending<T, kPass, kK>(sl, np, us, kp, lane, ac);
         np = 0;
       }
       if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
       np += nl;
       __syncwarp();
     }
-    if (np > 0) bwd_run_pending<T, kPass>(sl, np, us, kp, lane, ac);
+    if (np > 0) bwd_run_pending<T, kPass, kK>(sl, np, us, kp, lane, ac);
     sc0 = sc1;
   }
 }
@@ -753,8 +765,8 @@ __device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(32)
+template <class T, int kK>
+__global__ void __launch_bounds__(32, 1)
 bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b,
                 const float* __restrict__ ybar, const float* __restrict__ dir, KParams kp,
@@ -795,7 +807,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
 
     for (int fc0 = 0; fc0 < F.np;) {
       int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < F.np && fc1 - fc0 < kGroupsPerChunk) {
+      while (fc1 < F.np && fc1 - fc0 < us.groups) {
         const PieceRec p = g.pieces[F.p0 + fc1];
         if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
         V += p.nv;
@@ -827,7 +839,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
       for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
       __syncwarp();
 
-      bwd_sweep<T, 1>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      bwd_sweep<T, 1, kK>(g, sl, S, nfc, margin, us, kp, lane, ac);
       __syncwarp();
 
       // group outputs, adjoint coefficients and output-transform terms
@@ -886,7 +898,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
         sl.coef[lane] = cf;
       }
       __syncwarp();
-      bwd_sweep<T, 2>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      bwd_sweep<T, 2, kK>(g, sl, S, nfc, margin, us, kp, lane, ac);
       fc0 = fc1;
     }
 
@@ -945,17 +957,23 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part, int64_t n_pair
   if (hvp) hvp[i] = part[24 * (2 * p) + 12 + q] + part[24 * (2 * p + 1) + 12 + q];
 }
 
+template <class T, int kK>
+static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
+  const int smem = bwd_slice_bytes<T>(L.us);
+  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a, L.pose_b,
+                                                       L.ybar, L.dir, L.kp, L.us, L.part,
+                                                       L.jvp);
+}
+
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
+  const bool small_k = L.kp.trace_iters == 3;   // the paper's three steps: unrolled
   if (L.dir) {
-    const int smem = bwd_slice_bytes<Dual>(L.us);
-    bwd_unit_kernel<Dual><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
-                                                        L.pose_b, L.ybar, L.dir, L.kp, L.us,
-                                                        L.part, L.jvp);
+    if (small_k) launch_unit<Dual, 3>(L, stream); else launch_unit<Dual, 0>(L, stream);
   } else {
-    const int smem = bwd_slice_bytes<float>(L.us);
-    bwd_unit_kernel<float><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
-                                                         L.pose_b, L.ybar, nullptr, L.kp, L.us,
-                                                         L.part, nullptr);
+    BwdLaunch M = L;
+    M.dir = nullptr;
+    M.jvp = nullptr;
+    if (small_k) launch_unit<float, 3>(M, stream); else launch_unit<float, 0>(M, stream);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -965,20 +983,24 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+template <class T, int kK>
+static cudaError_t configure_unit(int bytes, int* per_sm) {
+  cudaError_t e = cudaSuccess;
+  if (bytes > 48 * 1024)
+    e = cudaFuncSetAttribute(bwd_unit_kernel<T, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bwd_unit_kernel<T, kK>, 32, bytes);
+}
+
 cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d) {
   const int sf = bwd_slice_bytes<float>(us), sd = bwd_slice_bytes<Dual>(us);
+  int tmp = 0;
   cudaError_t e;
-  if (sf > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(bwd_unit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                sf)) != cudaSuccess)
-    return e;
-  if (sd > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(bwd_unit_kernel<Dual>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                sd)) != cudaSuccess)
-    return e;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_f, bwd_unit_kernel<float>, 32, sf);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_d, bwd_unit_kernel<Dual>, 32, sd);
-  return cudaGetLastError();
+  if ((e = configure_unit<float, 0>(sf, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_unit<Dual, 0>(sd, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_unit<float, 3>(sf, per_sm_f)) != cudaSuccess) return e;
+  return configure_unit<Dual, 3>(sd, per_sm_d);
 }
 
 int backward_slice_bytes(const UnitShape& us, bool dual) {

@@ -198,7 +198,7 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitSh
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(128)
 unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, unsigned long long* __restrict__ counters) {
@@ -228,7 +228,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
     for (int fc0 = 0; fc0 < F.np;) {
       // F chunk [fc0, fc1): up to 32 pieces within the vertex / edge budgets
       int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < F.np && fc1 - fc0 < kGroupsPerChunk) {
+      while (fc1 < F.np && fc1 - fc0 < us.groups) {
         const PieceRec p = g.pieces[F.p0 + fc1];
         if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
         V += p.nv;

@@ -43,6 +43,11 @@ struct Context {
   void shutdown_serving();
 };
 
+struct BatchMaxima {      // largest pieces / bodies a batch touches
+  int vmax = 1, fmax = 1, emax = 1, s_planes = 1, s_pieces = 1, f_verts = 1, f_edges = 1;
+  int pieces_any = 1;
+};
+
 struct Batch {
   Context* ctx = nullptr;
   int64_t n = 0;
@@ -50,6 +55,8 @@ struct Batch {
   std::vector<int64_t> goff;
   DevBuf d_pairs;                // pair table
   DevBuf d_part;                 // [2n, 24] per-unit slots of the reverse pass
+  BatchMaxima mx;
+  ccm_tuning tuning{};
   UnitShape us{};
   int grid = 1;
   int bwd_grid_f = 1, bwd_grid_d = 1;
@@ -60,6 +67,8 @@ ccm_status fail(ccm_status s, const char* fmt, ...);
 ccm_status cuda_fail(cudaError_t e, const char* what);
 ccm_status make_kparams(const ccm_params* p, KParams* k);
 ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom* B, Batch* bt);
+void default_tuning(ccm_tuning* t);
+ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t);
 ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
                        float* y, unsigned long long* counters, cudaStream_t stream);
 ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,

@@ -29,9 +29,12 @@ struct UnitShape {
   int32_t item_e;         // (direction, edge) items per direction list
   int32_t slice_bytes;    // bytes per warp
   int32_t warps;          // warps per block
+  int32_t groups;         // feature pieces (groups) per chunk, <= kGroupsPerChunk
+  int32_t item_vb;        // item budgets of the reverse pass
+  int32_t item_eb;
 };
 
-constexpr int kGroupsPerChunk = 32;   // groups of one F chunk (lane-indexed)
+constexpr int kGroupsPerChunk = 32;   // most groups of one F chunk (lane-indexed)
 constexpr int kPending = 32;          // live directions per list
 
 struct UnitSlice {
@@ -39,9 +42,9 @@ struct UnitSlice {
   int2* sp;           // [spiece_budget] (first plane, plane count) per S piece
   float4* xs;         // [vert_budget] F vertices in the S frame
   uint32_t* edges;    // [edge_budget]
-  int4* fp;           // [32] (first vertex, nv, first edge, ne) per F piece
-  float4* fs;         // [32] bounding sphere (S frame) per F piece
-  float* acc;         // [32 * 10] group accumulators (M, U, D, A, P, N)
+  int4* fp;           // [groups] (first vertex, nv, first edge, ne) per F piece
+  float4* fs;         // [groups] bounding sphere (S frame) per F piece
+  float* acc;         // [groups * 10] group accumulators (M, U, D, A, P, N)
   int* dir;           // [32] pending live directions: fc << 16 | sc
   int* dsub;          // [32] directions of the list being run
   int* pv;            // [33] prefix of vertex items per pending direction
@@ -61,9 +64,9 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += align16i(8 * u.spiece_budget);
   b += 16 * u.vert_budget;
   b += align16i(4 * u.edge_budget);
-  b += 16 * kGroupsPerChunk;                 // fp
-  b += 16 * kGroupsPerChunk;                 // fs
-  b += align16i(4 * 10 * kGroupsPerChunk);   // acc
+  b += 16 * u.groups;                        // fp
+  b += 16 * u.groups;                        // fs
+  b += align16i(4 * 10 * u.groups);          // acc
   b += align16i(4 * kPending) * 2;           // dir, dsub
   b += align16i(4 * (kPending + 1)) * 2;     // pv, pe
   b += align16i(4 * u.item_v) * 2;           // m, phi
@@ -79,9 +82,9 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.sp = reinterpret_cast<int2*>(p);                 p += align16i(8 * u.spiece_budget);
   s.xs = reinterpret_cast<float4*>(p);               p += 16 * u.vert_budget;
   s.edges = reinterpret_cast<uint32_t*>(p);          p += align16i(4 * u.edge_budget);
-  s.fp = reinterpret_cast<int4*>(p);                 p += 16 * kGroupsPerChunk;
-  s.fs = reinterpret_cast<float4*>(p);               p += 16 * kGroupsPerChunk;
-  s.acc = reinterpret_cast<float*>(p);               p += align16i(4 * 10 * kGroupsPerChunk);
+  s.fp = reinterpret_cast<int4*>(p);                 p += 16 * u.groups;
+  s.fs = reinterpret_cast<float4*>(p);               p += 16 * u.groups;
+  s.acc = reinterpret_cast<float*>(p);               p += align16i(4 * 10 * u.groups);
   s.dir = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);                p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));

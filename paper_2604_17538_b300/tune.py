@@ -1,0 +1,68 @@
+"""Autotuner of a batch's launch shape (``ccm_batch_set_tuning``).
+
+Times the forward, the reverse pass and the forward-over-reverse pass of a
+batch on its own poses for a few shared-memory budgets and keeps, for each
+pass, the fastest shape; the choice is written back into the batch.  The
+candidate set is small because the budgets only trade lane utilisation
+(bigger lists of live piece pairs) against resident warps (smaller slices).
+"""
+from __future__ import annotations
+
+import itertools
+
+FWD_CANDIDATES = [dict(item_v=v, item_e=e, fwd_warps=w)
+                  for (v, e), w in itertools.product([(128, 256), (256, 512), (512, 1024)], [1, 2, 4])]
+BWD_CANDIDATES = [dict(item_vb=v, item_eb=e) for v, e in [(64, 128), (128, 256), (256, 512), (512, 1024)]]
+
+
+def _time(fn, reps=5):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verbose=False):
+    """Picks the fastest forward shape, then the fastest reverse-pass shape
+    (timed with a direction when one is given, i.e. on the dual kernel)."""
+    import torch
+    log = {"forward": {}, "reverse": {}}
+    best = None
+    for cand in FWD_CANDIDATES:
+        try:
+            batch.set_tuning(**cand)
+            t = _time(lambda: batch.contacts(pose_a, pose_b, params))
+        except Exception as ex:   # a shape the device cannot hold
+            log["forward"][str(cand)] = repr(ex)
+            continue
+        log["forward"][str(cand)] = t
+        if best is None or t < best[0]:
+            best = (t, cand)
+    batch.set_tuning(**best[1])
+    if ybar is None:
+        ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
+    bbest = None
+    for cand in BWD_CANDIDATES:
+        try:
+            batch.set_tuning(**cand)
+            t = _time(lambda: batch.backward(pose_a, pose_b, ybar, direction, params))
+        except Exception as ex:
+            log["reverse"][str(cand)] = repr(ex)
+            continue
+        log["reverse"][str(cand)] = t
+        if bbest is None or t < bbest[0]:
+            bbest = (t, cand)
+    batch.set_tuning(**bbest[1])
+    if verbose:
+        for k, v in log.items():
+            for c, t in sorted(v.items(), key=lambda x: (isinstance(x[1], str), x[1])):
+                print(f"{k:8s} {t if isinstance(t, str) else f'{t:8.3f} ms'}  {c}")
+    return batch.get_tuning(), log
