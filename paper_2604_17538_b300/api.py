@@ -137,21 +137,27 @@ class Batch:
                                              C.byref(prm), ptr(out), ptr(counters), s))
         return out
 
-    def backward(self, pose_a, pose_b, ybar, direction=None, params=None, want_jvp=False):
+    def backward(self, pose_a, pose_b, ybar, direction=None, params=None, want_jvp=False,
+                 out=None):
         """(grad [n,12], hvp [n,12] | None, jvp [G,8] | None) of <ybar, y> in
-        the twist chart (w_A, v_A, w_B, v_B)."""
+        the twist chart (w_A, v_A, w_B, v_B); ``out`` = preallocated
+        (grad, hvp, jvp) tensors (any may be None)."""
         import torch
         self._check_pose(pose_a)
         self._check_pose(pose_b)
         dev = pose_a.device
         ybar = ybar.contiguous()
-        grad = torch.empty((self.n_pairs, 12), device=dev, dtype=torch.float32)
+        o_g, o_h, o_j = out if out is not None else (None, None, None)
+        grad = o_g if o_g is not None else torch.empty((self.n_pairs, 12), device=dev,
+                                                       dtype=torch.float32)
         hvp = jvp = None
         if direction is not None:
             direction = direction.contiguous()
-            hvp = torch.empty((self.n_pairs, 12), device=dev, dtype=torch.float32)
+            hvp = o_h if o_h is not None else torch.empty((self.n_pairs, 12), device=dev,
+                                                          dtype=torch.float32)
             if want_jvp:
-                jvp = torch.empty((self.n_groups, 8), device=dev, dtype=torch.float32)
+                jvp = o_j if o_j is not None else torch.empty((self.n_groups, 8), device=dev,
+                                                              dtype=torch.float32)
         prm = _params(params)
         check(lib().ccm_contacts_backward(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
                                           ptr(ybar), ptr(direction), ptr(grad), ptr(hvp),

@@ -373,6 +373,7 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.order = static_cast<const int32_t*>(b->d_order.ptr);
   L.n_pairs = b->n;
   L.pose_a = pose_a;
   L.pose_b = pose_b;
@@ -453,6 +454,25 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
   mx.pieces_any = s_pieces_max_any;
   ccm_status s;
   if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
+  // unit (pair, side) order by decreasing estimated cost: directions plus
+  // features times SDF pieces; ties keep the natural order
+  {
+    std::vector<int64_t> cost(2 * n);
+    for (int64_t i = 0; i < n; ++i) {
+      for (int side = 0; side < 2; ++side) {
+        const BodyRec& F = c->bodies[side == 0 ? pairs[i].bodyA : pairs[i].bodyB];
+        const BodyRec& S = c->bodies[side == 0 ? pairs[i].bodyB : pairs[i].bodyA];
+        int64_t feats = 0;
+        for (int p = 0; p < F.np; ++p) feats += c->pieces[F.p0 + p].nv + c->pieces[F.p0 + p].ne;
+        cost[2 * i + side] = (int64_t)F.np * S.np + feats * S.np / 8;
+      }
+    }
+    std::vector<int32_t> order(2 * n);
+    for (int64_t u = 0; u < 2 * n; ++u) order[u] = (int32_t)u;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    if ((s = upload(bt->d_order, order, "unit order")) != CCM_OK) return s;
+  }
   std::vector<float> zeros_part((size_t)std::max<int64_t>(1, 2 * n) * 24, 0.f);
   if ((s = upload(bt->d_part, zeros_part, "reverse-pass slots")) != CCM_OK) return s;
   ccm_tuning t;
@@ -527,6 +547,7 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.order = static_cast<const int32_t*>(b->d_order.ptr);
   L.n_pairs = b->n;
   L.pose_a = pose_a;
   L.pose_b = pose_b;
@@ -546,6 +567,7 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
 
 void Batch::release() {
   d_pairs.release();
+  d_order.release();
   d_part.release();
 }
 
@@ -561,6 +583,7 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   FwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+  L.order = static_cast<const int32_t*>(b->d_order.ptr);
   L.n_pairs = b->n;
   L.pose_a = pose_a;
   L.pose_b = pose_b;

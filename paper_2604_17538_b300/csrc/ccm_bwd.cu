@@ -767,7 +767,8 @@ __device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 // ---------------------------------------------------------------------------
 template <class T, int kK>
 __global__ void __launch_bounds__(32, 1)
-bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
+bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
+                const int32_t* __restrict__ order, int64_t n_pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b,
                 const float* __restrict__ ybar, const float* __restrict__ dir, KParams kp,
                 UnitShape us, float* __restrict__ part, float* __restrict__ jvp) {
@@ -775,7 +776,8 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
   const int lane = threadIdx.x & 31;
   const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
   const int64_t n_units = 2 * n_pairs;
-  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+  for (int64_t k = blockIdx.x; k < n_units; k += gridDim.x) {
+    const int64_t u = order[k];   // heaviest units first, round-robin
     const int64_t pi = u >> 1;
     const int side = (int)(u & 1);
     const PairRec pr = pairs[pi];
@@ -960,7 +962,7 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part, int64_t n_pair
 template <class T, int kK>
 static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
-  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a, L.pose_b,
+  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a, L.pose_b,
                                                        L.ybar, L.dir, L.kp, L.us, L.part,
                                                        L.jvp);
 }

@@ -22,6 +22,7 @@ namespace ccm {
 struct BwdLaunch {
   DevGeom g;
   const PairRec* pairs;
+  const int32_t* order;   // units by decreasing estimated cost
   int64_t n_pairs;
   const float* pose_a;
   const float* pose_b;

@@ -199,7 +199,8 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitSh
 
 template <bool kCount>
 __global__ void __launch_bounds__(128)
-unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
+unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
+                const int32_t* __restrict__ order, int64_t n_pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,7 +213,9 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, int64_t n_pairs,
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   FwdCounts cnt;
 
-  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n_units; u += nwarps) {
+  // heaviest units first, dealt round-robin to the warps (balanced, no atomics)
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < n_units; k += nwarps) {
+    const int64_t u = order[k];
     const int64_t pi = u >> 1;
     const int side = (int)(u & 1);
     const PairRec pr = pairs[pi];
@@ -335,10 +338,10 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   const size_t smem = (size_t)L.us.warps * L.us.slice_bytes;
   const int threads = 32 * L.us.warps;
   if (L.counters)
-    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a,
                                                              L.pose_b, L.kp, L.us, L.y, L.counters);
   else
-    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.n_pairs, L.pose_a,
+    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a,
                                                               L.pose_b, L.kp, L.us, L.y, L.counters);
   return cudaGetLastError();
 }

@@ -9,6 +9,7 @@ namespace ccm {
 struct FwdLaunch {
   DevGeom g;
   const PairRec* pairs;
+  const int32_t* order;   // units (2 pair + side) by decreasing estimated cost
   int64_t n_pairs;
   const float* pose_a;
   const float* pose_b;

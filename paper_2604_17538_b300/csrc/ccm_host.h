@@ -54,6 +54,7 @@ struct Batch {
   int64_t G = 0;
   std::vector<int64_t> goff;
   DevBuf d_pairs;                // pair table
+  DevBuf d_order;                // units by decreasing estimated cost
   DevBuf d_part;                 // [2n, 24] per-unit slots of the reverse pass
   BatchMaxima mx;
   ccm_tuning tuning{};

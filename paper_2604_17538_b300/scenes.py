@@ -448,16 +448,117 @@ def hull_env_scene(seed=2, n_envs=4096, pieces_per_body=8, points_per_hull=64,
                   "separated": np.array([r[6] for r in res])})
 
 
+def _sup_offset_pruned(bodyF, bodyS, RF, RS, u_w, target):
+    """_sup_contact_offset restricted to the piece pairs that can matter.
+
+    For a vertex of piece f to reach max-plane level -target inside piece s,
+    the vertex (within r_f of the centre c_f) must come within r_s +
+    max(0, -target) of c_s, so along the ray its offset is at most
+    (c_s - c_f).u + r_s + r_f + max(0, -target) (all in S's frame).  Piece
+    pairs are visited by decreasing bound and the scan stops once the bound
+    falls below the best offset found: the result equals the full search.
+    """
+    VF, FF, cF, rF = bodyF
+    VS, FS, cS, rS = bodyS
+    Rrel = RS.T @ RF
+    du = RS.T @ u_w
+    cFs = cF @ Rrel.T                      # feature piece centres in S frame (at s = 0)
+    bound = (cS @ du)[:, None] - (cFs @ du)[None, :] + rS[:, None] + rF[None, :] + max(0.0, -target)
+    order = np.argsort(-bound, axis=None)
+    best = -np.inf
+    lvl = -target
+    for k in order:
+        a, b = divmod(int(k), bound.shape[1])
+        if bound[a, b] <= best:
+            break
+        x0 = VF[b] @ Rrel.T                                     # [V, 3]
+        n = FS[a][:, :3]
+        h = FS[a][:, 3]
+        c = x0 @ n.T + h                                        # [V, F]
+        d = np.broadcast_to(n @ du, c.shape)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = (lvl - c) / d
+            hi = np.where(d > 0, r, np.inf).min(-1)
+            lo = np.where(d < 0, r, -np.inf).max(-1)
+            ok0 = np.where(d == 0, c <= lvl, True).all(-1)
+        feas = ok0 & (lo <= hi) & np.isfinite(hi)
+        if feas.any():
+            best = max(best, hi[feas].max())
+    return best
+
+
+def _body_arrays(pieces):
+    """(vertices, planes, centres, radii) lists of one body for the placement."""
+    V = [p[0].astype(np.float64) for p in pieces]
+    F = [p[1].astype(np.float64) for p in pieces]
+    c = np.array([v.mean(0) for v in V])
+    r = np.array([np.linalg.norm(v - cc, axis=1).max() for v, cc in zip(V, c)])
+    return V, F, c, r
+
+
+def _make_pool_body(args):
+    seed, k, P, lo, hi = args
+    rng = np.random.default_rng([seed, 1 << 20, k])
+    npts = log_uniform_int(rng, lo, hi, size=P)
+    return _random_hull_body(rng, P, npts)
+
+
+def _place_pool_pair(args):
+    seed, i, bodyA, bodyB, sep_frac, depth_range, gap_range = args
+    rng = np.random.default_rng([seed, 1 << 21, i])
+    RA = random_rotations(rng, 1)[0]
+    RB = random_rotations(rng, 1)[0]
+    u = random_unit_vectors(rng, 1)[0]
+    separated = bool(rng.uniform() < sep_frac)
+    target = -rng.uniform(*gap_range) if separated else rng.uniform(*depth_range)
+    sB = _sup_offset_pruned(bodyB, bodyA, RB, RA, u, target)      # B's vertices in A
+    sA = _sup_offset_pruned(bodyA, bodyB, RA, RB, -u, target)     # A's vertices in B
+    tB = max(sA, sB) * u
+    RA2, tA2, RB2, tB2 = _world_frame(rng, RA[None], np.zeros((1, 3)), RB[None], tB[None])
+    return RA2[0], tA2[0], RB2[0], tB2[0], target, separated
+
+
+def _pmap(fn, jobs, workers):
+    if workers == 0:
+        import os
+        workers = min(len(os.sched_getaffinity(0)), 32)
+    if workers is None or workers <= 1 or len(jobs) < 64:
+        return [fn(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(fn, jobs, chunksize=max(1, len(jobs) // (8 * workers)))
+
+
 def uneven_scene(seed=4, n_pairs=65536, max_pieces=64, min_points=8, max_points=512,
-                 workers=None):
+                 pool_bodies=8192, sep_frac=0.3, depth_range=(0.0, 0.02),
+                 gap_range=(0.0, 0.02), workers=None):
     """Uneven batch: pieces per body log-uniform in [1, max_pieces], hull
-    points per piece log-uniform in [min_points, max_points], same hull
-    generation and placement as ``hull_env_scene``."""
+    points per piece log-uniform in [min_points, max_points], the Gaussian
+    hull generation and placement of ``hull_env_scene``.
+
+    Bodies come from a seeded pool of ``pool_bodies`` distinct bodies (drawn
+    with replacement for the two sides of every pair) so that generating
+    65,536 pairs does not need ~2M convex hulls; every pair gets its own
+    rotations, direction and target depth.  Returns a Scene whose geometry is
+    the pool (pair_a / pair_b index into it)."""
     rng = np.random.default_rng(seed)
-    pieces = log_uniform_int(rng, 1, max_pieces, size=(n_pairs, 2))
-    sc = hull_env_scene(seed=seed, n_envs=n_pairs, pieces_per_body=pieces,
-                        points_per_hull=("log-uniform", min_points, max_points),
-                        workers=workers)
-    sc.meta["workload"] = "uneven"
-    sc.meta["seed"] = seed
-    return sc
+    pool_n = min(pool_bodies, 2 * n_pairs)
+    pieces = log_uniform_int(rng, 1, max_pieces, size=pool_n)
+    bodies = _pmap(_make_pool_body, [(seed, k, int(pieces[k]), min_points, max_points)
+                                     for k in range(pool_n)], workers)
+    arrays = [_body_arrays(b) for b in bodies]
+    pa = rng.integers(0, pool_n, size=n_pairs)
+    pb = rng.integers(0, pool_n, size=n_pairs)
+    jobs = [(seed, i, arrays[pa[i]], arrays[pb[i]], sep_frac, depth_range, gap_range)
+            for i in range(n_pairs)]
+    res = _pmap(_place_pool_pair, jobs, workers)
+    geom = geometry_from_bodies(bodies)
+    RA = np.stack([r[0] for r in res])
+    tA = np.stack([r[1] for r in res])
+    RB = np.stack([r[2] for r in res])
+    tB = np.stack([r[3] for r in res])
+    return Scene(geom, pa.astype(np.int64), pb.astype(np.int64), pack_pose(RA, tA),
+                 pack_pose(RB, tB),
+                 {"workload": "uneven", "seed": seed, "pool_bodies": pool_n,
+                  "target_depth": np.array([r[4] for r in res]),
+                  "separated": np.array([r[5] for r in res])})
