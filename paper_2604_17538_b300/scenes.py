@@ -448,7 +448,7 @@ def hull_env_scene(seed=2, n_envs=4096, pieces_per_body=8, points_per_hull=64,
                   "separated": np.array([r[6] for r in res])})
 
 
-def _sup_offset_pruned(bodyF, bodyS, RF, RS, u_w, target):
+def _sup_offset_pruned(bodyF, bodyS, RF, RS, u_w, target, shift_w=None):
     """_sup_contact_offset restricted to the piece pairs that can matter.
 
     For a vertex of piece f to reach max-plane level -target inside piece s,
@@ -457,12 +457,14 @@ def _sup_offset_pruned(bodyF, bodyS, RF, RS, u_w, target):
     (c_s - c_f).u + r_s + r_f + max(0, -target) (all in S's frame).  Piece
     pairs are visited by decreasing bound and the scan stops once the bound
     falls below the best offset found: the result equals the full search.
+    ``shift_w`` (world) translates body F before the motion along u_w.
     """
     VF, FF, cF, rF = bodyF
     VS, FS, cS, rS = bodyS
     Rrel = RS.T @ RF
     du = RS.T @ u_w
-    cFs = cF @ Rrel.T                      # feature piece centres in S frame (at s = 0)
+    sh = np.zeros(3) if shift_w is None else RS.T @ shift_w
+    cFs = cF @ Rrel.T + sh                 # feature piece centres in S frame (at s = 0)
     bound = (cS @ du)[:, None] - (cFs @ du)[None, :] + rS[:, None] + rF[None, :] + max(0.0, -target)
     order = np.argsort(-bound, axis=None)
     best = -np.inf
@@ -471,7 +473,7 @@ def _sup_offset_pruned(bodyF, bodyS, RF, RS, u_w, target):
         a, b = divmod(int(k), bound.shape[1])
         if bound[a, b] <= best:
             break
-        x0 = VF[b] @ Rrel.T                                     # [V, 3]
+        x0 = VF[b] @ Rrel.T + sh                                # [V, 3]
         n = FS[a][:, :3]
         h = FS[a][:, 3]
         c = x0 @ n.T + h                                        # [V, F]
@@ -513,7 +515,26 @@ def _place_pool_pair(args):
     target = -rng.uniform(*gap_range) if separated else rng.uniform(*depth_range)
     sB = _sup_offset_pruned(bodyB, bodyA, RB, RA, u, target)      # B's vertices in A
     sA = _sup_offset_pruned(bodyA, bodyB, RA, RB, -u, target)     # A's vertices in B
-    tB = max(sA, sB) * u
+    p = np.zeros(3)
+    tries = 0
+    while not np.isfinite(max(sA, sB)):
+        # no vertex line along u meets the other body (small pieces far off
+        # the line through the origin), or the target is deeper than any
+        # piece can hold: shift B across u so that a random piece of each
+        # body lies on one line, and halve a penetration target every four
+        # tries
+        if tries == 64:
+            raise RuntimeError(f"pair {i}: no placement found")
+        if tries % 4 == 3 and target > 0:
+            target *= 0.5
+        tries += 1
+        a = int(rng.integers(0, len(bodyA[2])))
+        b = int(rng.integers(0, len(bodyB[2])))
+        delta = RA @ bodyA[2][a] - RB @ bodyB[2][b]
+        p = delta - (delta @ u) * u
+        sB = _sup_offset_pruned(bodyB, bodyA, RB, RA, u, target, p)
+        sA = _sup_offset_pruned(bodyA, bodyB, RA, RB, -u, target, -p)
+    tB = max(sA, sB) * u + p
     RA2, tA2, RB2, tB2 = _world_frame(rng, RA[None], np.zeros((1, 3)), RB[None], tB[None])
     return RA2[0], tA2[0], RB2[0], tB2[0], target, separated
 
