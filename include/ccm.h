@@ -136,17 +136,21 @@ CCM_API void ccm_batch_destroy(ccm_batch batch);
  * offsets off[n+1] copied to host memory. */
 CCM_API ccm_status ccm_batch_info(ccm_batch batch, int64_t* n_pairs, int64_t* n_groups, int64_t* off);
 
-/* Launch shape of a batch.  The kernels gather the live piece pairs of a body
- * pair into lists whose vertex and edge items fill the warp's shared-memory
- * budgets below; larger lists keep more lanes busy, smaller ones leave room
- * for more resident warps.  Defaults: 256 / 512 / 256 / 512 items, 2 forward
- * warps per block.  Budgets below the batch's largest piece are raised to it.
- * Results do not depend on the tuning beyond float rounding order. */
+/* Launch shape of a batch.  Each (pair, side) is cut into work items of at
+ * most `groups` feature pieces (one warp each, heaviest first), so that large
+ * bodies spread over many warps.  The kernels gather the live piece pairs of
+ * an item into lists whose vertex and edge items fill the warp's
+ * shared-memory budgets below; larger lists keep more lanes busy, smaller ones
+ * leave room for more resident warps.  Defaults: 256 / 512 / 256 / 512 items,
+ * 2 forward warps per block, 16 groups per work item.  Budgets below the
+ * batch's largest piece are raised to it.  Results do not depend on the
+ * tuning beyond float rounding order. */
 typedef struct {
   int32_t item_v, item_e;     /* forward: vertex / edge items per list */
   int32_t item_vb, item_eb;   /* reverse pass: vertex / edge items per list */
   int32_t fwd_warps;          /* forward warps per block, 1..4 */
-  int32_t reserved[3];
+  int32_t groups;             /* feature pieces per work item, 1..32 */
+  int32_t reserved[2];
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
 /* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of
@@ -219,6 +223,110 @@ CCM_API ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, co
  * denominators.  Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_peak_probe(int device, double* ffma_tflops, double* ffma2_tflops,
                                   double* ex2_tops);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of small requests (Sec. 5 workloads, where
+ * many environments each ask for the contacts of a few body pairs).
+ *
+ * Requests are queued by ccm_submit and packed, first come first served, by a
+ * scheduler thread inside the library into waves of at most max_wave_pairs
+ * pairs and max_wave_requests requests.  A wave is one replay of a CUDA graph
+ * that gathers every request's poses (and cotangents), runs the forward pass
+ * over all of the wave's pairs and the reverse pass over the pairs of the
+ * requests that asked for the gradient, and scatters the results into each
+ * request's own buffers.  Two waves can be in flight at once.  The launch
+ * shape is fixed by ccm_serve_start from the geometry resident at that moment,
+ * so a request's results are bitwise the same whatever else shares its wave.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t max_wave_pairs;      /* pairs per wave (and largest request); 0 = the
+                                  most that the context's HBM budget holds */
+  int64_t max_wave_requests;   /* requests per wave */
+  int64_t max_queued;          /* queued (not yet running) requests */
+  ccm_params params;           /* parameters of every request */
+  ccm_tuning tuning;           /* launch shape (raised to the resident pieces) */
+} ccm_serve_config;
+
+/* Defaults: 16384 pairs and 1024 requests per wave, 65536 queued requests,
+ * ccm_default_params, the default tuning. */
+CCM_API void ccm_default_serve_config(ccm_serve_config* cfg);
+
+/* Starts the scheduler of `ctx`: allocates two sets of wave buffers (device
+ * and pinned host), captures one graph per set and starts the scheduler
+ * thread.  Synchronous.  Bodies loaded later may be requested if no piece of
+ * theirs has more vertices, planes or edges than the largest resident at start.
+ * Device memory: two sets of wave buffers of 368 bytes per pair plus
+ * 64 bytes per output group, which must fit the context's HBM budget.
+ * Errors: CCM_ERR_INVALID (already started, bad capacities or params, no
+ * resident geometry), CCM_ERR_OOM (the wave buffers do
+ * not fit the context's HBM budget or cudaMalloc failed), CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_serve_start(ccm_ctx ctx, const ccm_serve_config* cfg);
+
+/* Runs every queued request to completion, stops the thread and frees the
+ * wave buffers; tickets not yet polled become unknown.  ccm_destroy does the
+ * same.  Errors: CCM_ERR_INVALID (not started). */
+CCM_API ccm_status ccm_serve_stop(ccm_ctx ctx);
+
+/* One request: the contacts of n_pairs body pairs (A[i], B[i]).
+ *   A, B    host arrays of n_pairs handles, read before ccm_submit returns;
+ *   pose_a, pose_b  device [n_pairs, 12] float32, holding their values when
+ *           ccm_submit is called (synchronize the producing stream first);
+ *   y       device [G, 8] float32 outputs, G = ccm_output_size of the pairs;
+ *   ybar    device [G, 8] float32 cotangent, or NULL for the forward pass only;
+ *   grad    device [n_pairs, 12] float32 gradient of <ybar, y> in the twist
+ *           chart (w_A, v_A, w_B, v_B); required with ybar, else ignored.
+ * The device buffers stay owned by the caller and must stay valid and
+ * untouched until ccm_poll reports the ticket done. */
+typedef struct {
+  int64_t n_pairs;
+  const ccm_geom* A;
+  const ccm_geom* B;
+  const float* pose_a;
+  const float* pose_b;
+  float* y;
+  const float* ybar;
+  float* grad;
+} ccm_request;
+
+/* Queues a request; never blocks on the GPU.  *ticket identifies it for
+ * ccm_poll.  Errors: CCM_ERR_INVALID (not started, bad request or handle, a
+ * body with a piece larger than the start-time launch shape holds),
+ * CCM_ERR_OOM (request larger than a wave), CCM_ERR_BUSY (queue full: retry
+ * after polling), CCM_ERR_CUDA (an earlier wave failed). */
+CCM_API ccm_status ccm_submit(ccm_ctx ctx, const ccm_request* req, ccm_ticket* ticket);
+
+/* Non-blocking.  *done = 1 once the request's outputs are in its buffers
+ * (visible to any stream), after which the ticket is retired; *latency_s
+ * (optional) then receives submit-to-completion time in seconds as seen by the
+ * scheduler.  *done = 0 while it is queued or running.  Errors:
+ * CCM_ERR_INVALID, CCM_ERR_UNKNOWN_TICKET (never issued or already retired),
+ * CCM_ERR_CUDA (a wave failed). */
+CCM_API ccm_status ccm_poll(ccm_ctx ctx, ccm_ticket ticket, int* done, double* latency_s);
+
+/* Non-blocking completion queue: retires up to `capacity` completed requests
+ * in completion order and writes their tickets (host array) and, if
+ * latency_s != NULL, their submit-to-completion times in seconds; *n gets how
+ * many.  Tickets already retired by ccm_poll are skipped.  Errors:
+ * CCM_ERR_INVALID, CCM_ERR_CUDA (a wave failed). */
+CCM_API ccm_status ccm_poll_completed(ccm_ctx ctx, ccm_ticket* tickets, double* latency_s,
+                                      int64_t capacity, int64_t* n);
+
+/* hold != 0: queued requests form no new wave until called with hold = 0
+ * (waves already running finish).  ccm_serve_stop releases a hold.
+ * Errors: CCM_ERR_INVALID (not started). */
+CCM_API ccm_status ccm_serve_hold(ccm_ctx ctx, int hold);
+
+/* Counters since ccm_serve_start (tracing of the serving loop). */
+typedef struct {
+  int64_t waves;        /* waves launched */
+  int64_t served;       /* requests completed */
+  int64_t wave_pairs;   /* body pairs run, summed over waves */
+  int64_t wave_items;   /* work items run, summed over waves */
+  double gpu_s;         /* device time of the finished waves' graphs (CUDA events) */
+  double form_s;        /* host time spent forming waves (tables, order, copies) */
+} ccm_serve_counters;
+/* Errors: CCM_ERR_INVALID (not started). */
+CCM_API ccm_status ccm_serve_stats(ccm_ctx ctx, ccm_serve_counters* out);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,24 @@ class ccm_body_desc(C.Structure):
 
 class ccm_tuning(C.Structure):
     _fields_ = [("item_v", C.c_int32), ("item_e", C.c_int32), ("item_vb", C.c_int32),
-                ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("groups", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
+class ccm_serve_config(C.Structure):
+    _fields_ = [("max_wave_pairs", C.c_int64), ("max_wave_requests", C.c_int64),
+                ("max_queued", C.c_int64), ("params", ccm_params), ("tuning", ccm_tuning)]
+
+
+class ccm_serve_counters(C.Structure):
+    _fields_ = [("waves", C.c_int64), ("served", C.c_int64), ("wave_pairs", C.c_int64),
+                ("wave_items", C.c_int64), ("gpu_s", C.c_double), ("form_s", C.c_double)]
+
+
+class ccm_request(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("A", C.c_void_p), ("B", C.c_void_p),
+                ("pose_a", C.c_void_p), ("pose_b", C.c_void_p), ("y", C.c_void_p),
+                ("ybar", C.c_void_p), ("grad", C.c_void_p)]
 
 
 _SIGS = {
@@ -69,6 +86,14 @@ _SIGS = {
     "ccm_contacts_backward": (C.c_int, [C.c_void_p] * 10),
     "ccm_contacts_backward_noalloc": (C.c_int, [C.c_void_p] * 10),
     "ccm_peak_probe": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ccm_default_serve_config": (None, [C.c_void_p]),
+    "ccm_serve_start": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ccm_serve_stop": (C.c_int, [C.c_void_p]),
+    "ccm_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ccm_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "ccm_serve_hold": (C.c_int, [C.c_void_p, C.c_int]),
+    "ccm_poll_completed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "ccm_serve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -109,6 +134,14 @@ def default_params(**kw) -> ccm_params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def default_serve_config(**kw) -> ccm_serve_config:
+    c = ccm_serve_config()
+    lib().ccm_default_serve_config(C.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
 
 
 def ptr(t):

@@ -94,7 +94,8 @@ class Batch:
     def get_tuning(self) -> dict:
         t = abi.ccm_tuning()
         check(lib().ccm_batch_get_tuning(self.handle, C.byref(t)))
-        return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps")}
+        return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps",
+                                           "groups")}
 
     def set_tuning(self, **kw):
         t = abi.ccm_tuning()
@@ -174,3 +175,100 @@ def scene_to_device(scene, ctx: Context, device="cuda"):
     pa = torch.from_numpy(np.ascontiguousarray(scene.pose_a, np.float32)).to(device)
     pb = torch.from_numpy(np.ascontiguousarray(scene.pose_b, np.float32)).to(device)
     return batch, pa, pb
+
+
+class Server:
+    """Continuous batching over a context (``ccm_serve_start`` .. ``ccm_serve_stop``).
+
+    ``submit`` queues the contacts (and optionally the pose gradient) of a list
+    of body pairs and returns a ticket; ``poll`` reports completion without
+    blocking.  The tensors of a request are kept alive here until its ticket is
+    retired."""
+
+    def __init__(self, ctx: Context, params=None, tuning: dict | None = None, **capacities):
+        self.ctx = ctx
+        cfg = abi.default_serve_config(**capacities)
+        cfg.params = _params(params)
+        for k, v in (tuning or {}).items():
+            setattr(cfg.tuning, k, int(v))
+        check(lib().ccm_serve_start(ctx.handle, C.byref(cfg)))
+        self.config = cfg
+        self._live = {}
+
+    def submit(self, A, B, pose_a, pose_b, ybar=None, y=None, grad=None, sync=True):
+        """Queues one request.  pose_a / pose_b: cuda float32 [n, 12]; ybar:
+        cuda float32 [G, 8] for the gradient, else None.  ``sync`` waits for
+        the current stream first so that the poses hold their values.
+        Returns (ticket, y, grad); y and grad are filled once ``poll`` says done."""
+        import torch
+        A = np.ascontiguousarray(A, np.uint64)
+        B = np.ascontiguousarray(B, np.uint64)
+        n = len(A)
+        dev = pose_a.device
+        for p in (pose_a, pose_b):
+            if not (p.is_cuda and p.dtype == torch.float32 and p.is_contiguous()
+                    and tuple(p.shape) == (n, 12)):
+                raise ValueError(f"pose must be a contiguous cuda float32 [{n}, 12] tensor")
+        if y is None:
+            y = torch.empty((self.ctx.output_size(A, B), 8), device=dev, dtype=torch.float32)
+        if ybar is not None:
+            ybar = ybar.contiguous()
+            if grad is None:
+                grad = torch.empty((n, 12), device=dev, dtype=torch.float32)
+        if sync:
+            torch.cuda.current_stream(dev).synchronize()
+        req = abi.ccm_request(n, ptr(A), ptr(B), ptr(pose_a), ptr(pose_b), ptr(y), ptr(ybar),
+                              ptr(grad) if ybar is not None else None)
+        t = C.c_uint64()
+        check(lib().ccm_submit(self.ctx.handle, C.byref(req), C.byref(t)))
+        self._live[t.value] = (pose_a, pose_b, y, ybar, grad)
+        return t.value, y, grad
+
+    def poll(self, ticket):
+        """(done, latency in seconds or None)."""
+        done = C.c_int()
+        lat = C.c_double()
+        check(lib().ccm_poll(self.ctx.handle, C.c_uint64(ticket), C.byref(done), C.byref(lat)))
+        if done.value:
+            self._live.pop(ticket, None)
+            return True, lat.value
+        return False, None
+
+    def completed(self, max_n=4096):
+        """Retires the requests completed so far, in completion order:
+        a list of (ticket, latency in seconds)."""
+        t = np.zeros(max_n, np.uint64)
+        lat = np.zeros(max_n, np.float64)
+        n = C.c_int64()
+        check(lib().ccm_poll_completed(self.ctx.handle, ptr(t), ptr(lat), max_n, C.byref(n)))
+        out = list(zip(t[:n.value].tolist(), lat[:n.value].tolist()))
+        for tk, _ in out:
+            self._live.pop(tk, None)
+        return out
+
+    def wait(self, ticket, timeout_s=60.0):
+        """Polls until done; returns the latency.  Raises TimeoutError."""
+        import time
+        t_end = time.perf_counter() + timeout_s
+        while True:
+            done, lat = self.poll(ticket)
+            if done:
+                return lat
+            if time.perf_counter() > t_end:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout_s} s")
+            time.sleep(20e-6)
+
+    def stats(self):
+        c = abi.ccm_serve_counters()
+        check(lib().ccm_serve_stats(self.ctx.handle, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in abi.ccm_serve_counters._fields_}
+
+    def hold(self, on: bool):
+        """While held, queued requests form no new wave."""
+        check(lib().ccm_serve_hold(self.ctx.handle, 1 if on else 0))
+
+    def close(self):
+        if self.ctx is not None and self.ctx.handle:
+            check(lib().ccm_serve_stop(self.ctx.handle))
+        self._live.clear()
+        self.ctx = None

@@ -36,12 +36,6 @@ ccm_status cuda_fail(cudaError_t e, const char* what) {
   return fail(CCM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CCM_CUDA(call, what)                         \
-  do {                                               \
-    cudaError_t e_ = (call);                         \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
-
 // ---------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------
@@ -359,10 +353,10 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   Batch* b = reinterpret_cast<Batch*>(batch);
   if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
   if (b->n == 0) return CCM_OK;
-  if (b->n > noalloc_max_pairs())
+  if (b->n_items > noalloc_max_items())
     return fail(CCM_ERR_INVALID,
-                "ccm_contacts_backward_noalloc: %lld pairs exceed its fixed scratch of %lld pairs",
-                (long long)b->n, (long long)noalloc_max_pairs());
+                "ccm_contacts_backward_noalloc: %lld work items exceed its fixed scratch of %lld",
+                (long long)b->n_items, (long long)noalloc_max_items());
   if (!pose_a || !pose_b || !ybar || !grad) return fail(CCM_ERR_INVALID, "NULL pointer");
   if (dir && !hvp) return fail(CCM_ERR_INVALID, "dir given without hvp");
   KParams kp;
@@ -373,7 +367,11 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
-  L.order = static_cast<const int32_t*>(b->d_order.ptr);
+  L.items = static_cast<const WorkItem*>(b->d_items.ptr);
+  L.order = static_cast<const int32_t*>(b->d_item_order.ptr);
+  L.n_items = b->n_items;
+  L.item_off = static_cast<const int64_t*>(b->d_item_off.ptr);
+  L.dev_items = nullptr;
   L.n_pairs = b->n;
   L.pose_a = pose_a;
   L.pose_b = pose_b;
@@ -383,6 +381,7 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   L.us = b->us;
   L.part = nullptr;
   L.grad = grad;
+  L.dev_pairs = nullptr;
   L.hvp = hvp;
   L.jvp = dir ? jvp : nullptr;
   L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
@@ -405,14 +404,81 @@ ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const floa
 
 namespace ccm {
 
+BatchMaxima body_maxima(const Context& c, int32_t body) {
+  BatchMaxima m;
+  const BodyRec& br = c.bodies[body];
+  int sp = 0, cv = 0, ce = 0;
+  for (int p = 0; p < br.np; ++p) {
+    const PieceRec& pr = c.pieces[br.p0 + p];
+    m.vmax = std::max(m.vmax, pr.nv);
+    m.fmax = std::max(m.fmax, pr.nf);
+    m.emax = std::max(m.emax, pr.ne);
+    sp += pr.nf;
+    if (p < kGroupsPerChunk) { cv += pr.nv; ce += pr.ne; }
+  }
+  m.s_planes = std::max(1, sp);
+  m.s_pieces = std::max(1, br.np);
+  m.pieces_any = m.s_pieces;
+  m.f_verts = std::max(1, cv);
+  m.f_edges = std::max(1, ce);
+  return m;
+}
+
+void merge_maxima(BatchMaxima* m, const BatchMaxima& b) {
+  m->vmax = std::max(m->vmax, b.vmax);
+  m->fmax = std::max(m->fmax, b.fmax);
+  m->emax = std::max(m->emax, b.emax);
+  m->s_planes = std::max(m->s_planes, b.s_planes);
+  m->s_pieces = std::max(m->s_pieces, b.s_pieces);
+  m->pieces_any = std::max(m->pieces_any, b.pieces_any);
+  m->f_verts = std::max(m->f_verts, b.f_verts);
+  m->f_edges = std::max(m->f_edges, b.f_edges);
+}
+
+void make_items(const Context& c, const PairRec* pairs, int64_t n, int64_t unit_pair0,
+                const UnitShape& us, std::vector<WorkItem>* items, std::vector<int64_t>* cost,
+                std::vector<int64_t>* item_off) {
+  for (int64_t i = 0; i < n; ++i) {
+    for (int side = 0; side < 2; ++side) {
+      const BodyRec& F = c.bodies[side == 0 ? pairs[i].bodyA : pairs[i].bodyB];
+      const BodyRec& S = c.bodies[side == 0 ? pairs[i].bodyB : pairs[i].bodyA];
+      // the kernels' chunking: at most us.groups pieces within the budgets
+      for (int fc0 = 0; fc0 < F.np;) {
+        int fc1 = fc0, V = 0, E = 0;
+        int64_t feats = 0;
+        while (fc1 < F.np && fc1 - fc0 < us.groups) {
+          const PieceRec& p = c.pieces[F.p0 + fc1];
+          if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
+          V += p.nv;
+          E += p.ne;
+          feats += p.nv + p.ne;
+          ++fc1;
+        }
+        items->push_back(WorkItem{(int32_t)(2 * (unit_pair0 + i) + side), (uint16_t)fc0,
+                                  (uint16_t)fc1});
+        // directions, plus features times SDF pieces, plus staging S
+        cost->push_back((int64_t)(fc1 - fc0) * S.np + feats * S.np / 8 + S.np);
+        fc0 = fc1;
+      }
+    }
+    if (item_off) item_off->push_back((int64_t)items->size());
+  }
+}
+
+std::vector<int32_t> items_by_cost(const std::vector<int64_t>& cost) {
+  std::vector<int32_t> order(cost.size());
+  for (size_t k = 0; k < cost.size(); ++k) order[k] = (int32_t)k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  return order;
+}
+
 ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom* B, Batch* bt) {
   std::lock_guard<std::mutex> lk(c->mu);
   CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
   std::vector<PairRec> pairs(n);
   bt->goff.assign(n + 1, 0);
   int64_t G = 0;
-  int vmax = 1, fmax = 1, emax = 1, s_planes = 1, s_pieces = 1, f_verts = 1, f_edges = 1;
-  int s_pieces_max_any = 1;
   for (int64_t i = 0; i < n; ++i) {
     int32_t a, b;
     ccm_status s;
@@ -427,54 +493,18 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
   bt->G = G;
   // budgets of the per-warp shared-memory slice, from the bodies in the batch
   std::vector<uint8_t> seen(c->bodies.size(), 0);
+  BatchMaxima mx;
   for (int64_t i = 0; i < n; ++i) {
     for (int32_t bi : {pairs[i].bodyA, pairs[i].bodyB}) {
       if (seen[bi]) continue;
       seen[bi] = 1;
-      const BodyRec& br = c->bodies[bi];
-      int sp = 0, cv = 0, ce = 0;
-      for (int p = 0; p < br.np; ++p) {
-        const PieceRec& pr = c->pieces[br.p0 + p];
-        vmax = std::max(vmax, pr.nv);
-        fmax = std::max(fmax, pr.nf);
-        emax = std::max(emax, pr.ne);
-        sp += pr.nf;
-        if (p < kGroupsPerChunk) { cv += pr.nv; ce += pr.ne; }
-      }
-      s_pieces_max_any = std::max(s_pieces_max_any, br.np);
-      s_planes = std::max(s_planes, sp);
-      s_pieces = std::max(s_pieces, br.np);
-      f_verts = std::max(f_verts, cv);
-      f_edges = std::max(f_edges, ce);
+      merge_maxima(&mx, body_maxima(*c, bi));
     }
   }
-  BatchMaxima& mx = bt->mx;
-  mx.vmax = vmax; mx.fmax = fmax; mx.emax = emax; mx.s_planes = s_planes;
-  mx.s_pieces = s_pieces; mx.f_verts = f_verts; mx.f_edges = f_edges;
-  mx.pieces_any = s_pieces_max_any;
+  bt->mx = mx;
   ccm_status s;
   if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
-  // unit (pair, side) order by decreasing estimated cost: directions plus
-  // features times SDF pieces; ties keep the natural order
-  {
-    std::vector<int64_t> cost(2 * n);
-    for (int64_t i = 0; i < n; ++i) {
-      for (int side = 0; side < 2; ++side) {
-        const BodyRec& F = c->bodies[side == 0 ? pairs[i].bodyA : pairs[i].bodyB];
-        const BodyRec& S = c->bodies[side == 0 ? pairs[i].bodyB : pairs[i].bodyA];
-        int64_t feats = 0;
-        for (int p = 0; p < F.np; ++p) feats += c->pieces[F.p0 + p].nv + c->pieces[F.p0 + p].ne;
-        cost[2 * i + side] = (int64_t)F.np * S.np + feats * S.np / 8;
-      }
-    }
-    std::vector<int32_t> order(2 * n);
-    for (int64_t u = 0; u < 2 * n; ++u) order[u] = (int32_t)u;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-    if ((s = upload(bt->d_order, order, "unit order")) != CCM_OK) return s;
-  }
-  std::vector<float> zeros_part((size_t)std::max<int64_t>(1, 2 * n) * 24, 0.f);
-  if ((s = upload(bt->d_part, zeros_part, "reverse-pass slots")) != CCM_OK) return s;
+  bt->pairs = std::move(pairs);
   ccm_tuning t;
   default_tuning(&t);
   return apply_tuning(c, bt, t);
@@ -487,6 +517,7 @@ void default_tuning(ccm_tuning* t) {
   t->item_vb = 256;
   t->item_eb = 512;
   t->fwd_warps = 2;
+  t->groups = 16;
 }
 
 // Shared-memory budgets and launch shapes of a batch for the tuning `t`
@@ -494,7 +525,7 @@ void default_tuning(ccm_tuning* t) {
 ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   if (t.item_v < 1 || t.item_e < 1 || t.item_vb < 1 || t.item_eb < 1 || t.item_v > 8192 ||
       t.item_e > 16384 || t.item_vb > 8192 || t.item_eb > 16384 || t.fwd_warps < 1 ||
-      t.fwd_warps > 4)
+      t.fwd_warps > 4 || t.groups < 1 || t.groups > kGroupsPerChunk)
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -506,7 +537,7 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   us.item_e = std::max(mx.emax, t.item_e);
   us.item_vb = std::max(mx.vmax, t.item_vb);
   us.item_eb = std::max(mx.emax, t.item_eb);
-  us.groups = std::min(kGroupsPerChunk, mx.pieces_any);
+  us.groups = std::min(t.groups, mx.pieces_any);
   us.slice_bytes = unit_slice_bytes(us);
   us.warps = t.fwd_warps;
   while (us.warps > 1 && us.warps * us.slice_bytes > c->smem_optin) --us.warps;
@@ -517,12 +548,29 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
     return fail(CCM_ERR_INVALID, "pieces too large for the reverse pass");
   CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
   int per_sm = 1;
-  cudaError_t e = configure_forward(us, &per_sm);
+  cudaError_t e = configure_forward(us, c->smem_optin, &per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "configure_forward");
   int per_f = 1, per_d = 1;
-  e = configure_backward(us, &per_f, &per_d);
+  e = configure_backward(us, c->smem_optin, &per_f, &per_d);
   if (e != cudaSuccess) return cuda_fail(e, "configure_backward");
-  const int64_t units = 2 * bt->n;
+  // work items of the pairs for this shape, heaviest first
+  std::vector<WorkItem> items;
+  std::vector<int64_t> cost, item_off(1, 0);
+  items.reserve(2 * bt->pairs.size());
+  make_items(*c, bt->pairs.data(), (int64_t)bt->pairs.size(), 0, us, &items, &cost, &item_off);
+  if ((int64_t)items.size() >= ((int64_t)1 << 31))
+    return fail(CCM_ERR_INVALID, "too many work items (%zu)", items.size());
+  ccm_status st;
+  if ((st = upload(bt->d_items, items, "work items")) != CCM_OK) return st;
+  if ((st = upload(bt->d_item_order, items_by_cost(cost), "item order")) != CCM_OK) return st;
+  if ((st = upload(bt->d_item_off, item_off, "item offsets")) != CCM_OK) return st;
+  if ((int64_t)items.size() != bt->n_items || !bt->d_part.ptr) {
+    bt->d_part.release();
+    std::vector<float> zeros((size_t)std::max<size_t>(1, items.size()) * 24, 0.f);
+    if ((st = upload(bt->d_part, zeros, "reverse-pass slots")) != CCM_OK) return st;
+  }
+  bt->n_items = (int64_t)items.size();
+  const int64_t units = bt->n_items;
   bt->us = us;
   bt->tuning = t;
   bt->grid = (int)std::max<int64_t>(
@@ -547,7 +595,11 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
-  L.order = static_cast<const int32_t*>(b->d_order.ptr);
+  L.items = static_cast<const WorkItem*>(b->d_items.ptr);
+  L.order = static_cast<const int32_t*>(b->d_item_order.ptr);
+  L.n_items = b->n_items;
+  L.item_off = static_cast<const int64_t*>(b->d_item_off.ptr);
+  L.dev_items = nullptr;
   L.n_pairs = b->n;
   L.pose_a = pose_a;
   L.pose_b = pose_b;
@@ -557,6 +609,7 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.us = b->us;
   L.part = static_cast<float*>(b->d_part.ptr);
   L.grad = grad;
+  L.dev_pairs = nullptr;
   L.hvp = hvp;
   L.jvp = dir ? jvp : nullptr;
   L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
@@ -567,7 +620,9 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
 
 void Batch::release() {
   d_pairs.release();
-  d_order.release();
+  d_items.release();
+  d_item_order.release();
+  d_item_off.release();
   d_part.release();
 }
 
@@ -583,8 +638,10 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   FwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
-  L.order = static_cast<const int32_t*>(b->d_order.ptr);
-  L.n_pairs = b->n;
+  L.items = static_cast<const WorkItem*>(b->d_items.ptr);
+  L.order = static_cast<const int32_t*>(b->d_item_order.ptr);
+  L.n_items = b->n_items;
+  L.dev_items = nullptr;
   L.pose_a = pose_a;
   L.pose_b = pose_b;
   L.kp = kp;

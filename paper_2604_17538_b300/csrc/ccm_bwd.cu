@@ -4,8 +4,9 @@
 // poses; with T = Dual (poses seeded with the tangent of a direction u) the
 // same code yields, forward-over-reverse, H u and the output tangents J u.
 //
-// One warp runs one unit (pair, side) like the forward kernel and re-derives
-// everything it needs -- the per-vertex SDF is recomputed, never stored:
+// One warp runs one work item (a unit (pair, side) or a slice of its feature
+// pieces) like the forward kernel and re-derives everything it needs -- the
+// per-vertex SDF is recomputed, never stored:
 //   pass 1  recomputes the blends of the unit's groups (online softmax);
 //   then    each group's adjoint coefficients are formed from ybar;
 //   pass 2  recomputes every contact and back-propagates through the blend,
@@ -14,8 +15,9 @@
 //           the soft clip, midpoint and sphere-trace steps of an edge
 //           (Sec. 4.2) into the feature points, whose adjoints x_bar are
 //           summed as sum x_bar and sum x cross x_bar in the SDF frame.
-// The unit's 12 twist components are written to a per-unit slot; a second
-// kernel adds the two sides of each pair in a fixed order (deterministic).
+// The item's 12 twist components are written to a per-item slot; a second
+// kernel adds the slots of each pair in a fixed order (deterministic).
+#include <algorithm>
 #include <mutex>
 
 #include "ccm_dual.cuh"
@@ -768,16 +770,19 @@ __device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 template <class T, int kK>
 __global__ void __launch_bounds__(32, 1)
 bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
-                const int32_t* __restrict__ order, int64_t n_pairs,
+                const WorkItem* __restrict__ items, const int32_t* __restrict__ order,
+                int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b,
                 const float* __restrict__ ybar, const float* __restrict__ dir, KParams kp,
                 UnitShape us, float* __restrict__ part, float* __restrict__ jvp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
-  const int64_t n_units = 2 * n_pairs;
-  for (int64_t k = blockIdx.x; k < n_units; k += gridDim.x) {
-    const int64_t u = order[k];   // heaviest units first, round-robin
+  const int64_t n_run = dev_items ? *dev_items : n_items;
+  for (int64_t k = blockIdx.x; k < n_run; k += gridDim.x) {
+    const int32_t item = order[k];   // heaviest items first, round-robin
+    const WorkItem it = items[item];
+    const int64_t u = it.unit;
     const int64_t pi = u >> 1;
     const int side = (int)(u & 1);
     const PairRec pr = pairs[pi];
@@ -807,9 +812,9 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
     ac.X2 = ac.X1;
     V3T<T> gws = ac.X1, gvs = ac.X1;   // output-transform terms of this lane's groups
 
-    for (int fc0 = 0; fc0 < F.np;) {
+    for (int fc0 = it.fc0; fc0 < it.fc1;) {
       int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < F.np && fc1 - fc0 < us.groups) {
+      while (fc1 < it.fc1 && fc1 - fc0 < us.groups) {
         const PieceRec p = g.pieces[F.p0 + fc1];
         if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
         V += p.nv;
@@ -920,7 +925,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
       T gS[6] = {gws.x - X2w.x, gws.y - X2w.y, gws.z - X2w.z,
                  gvs.x - X1w.x, gvs.y - X1w.y, gvs.z - X1w.z};
       // slot layout per unit: [grad (w_A, v_A, w_B, v_B) | H u (same layout)]
-      float* o = part + 24 * u;
+      float* o = part + 24 * (int64_t)item;
       const int offF = side == 0 ? 0 : 6, offS = side == 0 ? 6 : 0;
       for (int q = 0; q < 6; ++q) {
         o[offF + q] = val(gF[q]);
@@ -949,20 +954,32 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 }
 
 // grad / hvp of pair i = the two units' slots, side 0 then side 1
-__global__ void bwd_reduce_kernel(const float* __restrict__ part, int64_t n_pairs,
+// grad / hvp of pair p: the sum of its items' slots [item_off[p], item_off[p+1])
+// in index order.
+__global__ void bwd_reduce_kernel(const float* __restrict__ part,
+                                  const int64_t* __restrict__ item_off, int64_t n_pairs,
+                                  const int64_t* __restrict__ dev_pairs,
                                   float* __restrict__ grad, float* __restrict__ hvp) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pairs * 12) return;
-  const int64_t p = i / 12;
-  const int q = (int)(i - p * 12);
-  grad[i] = part[24 * (2 * p) + q] + part[24 * (2 * p + 1) + q];
-  if (hvp) hvp[i] = part[24 * (2 * p) + 12 + q] + part[24 * (2 * p + 1) + 12 + q];
+  const int64_t n = (dev_pairs ? *dev_pairs : n_pairs) * 12;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / 12;
+    const int q = (int)(i - p * 12);
+    const int64_t i0 = item_off[p], i1 = item_off[p + 1];
+    float g = 0.f, h = 0.f;
+    for (int64_t j = i0; j < i1; ++j) {
+      g += part[24 * j + q];
+      if (hvp) h += part[24 * j + 12 + q];
+    }
+    grad[i] = g;
+    if (hvp) hvp[i] = h;
+  }
 }
 
 template <class T, int kK>
 static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
-  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a, L.pose_b,
+  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b,
                                                        L.ybar, L.dir, L.kp, L.us, L.part,
                                                        L.jvp);
 }
@@ -980,29 +997,32 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = L.n_pairs * 12;
-  bwd_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, stream>>>(L.part, L.n_pairs, L.grad,
-                                                                L.dir ? L.hvp : nullptr);
+  const int blocks = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (n + 255) / 256));
+  bwd_reduce_kernel<<<blocks, 256, 0, stream>>>(L.part, L.item_off, L.n_pairs, L.dev_pairs, L.grad,
+                                                L.dir ? L.hvp : nullptr);
   return cudaGetLastError();
 }
 
+// The limit is raised to the device's opt-in maximum, not to this shape's size:
+// the attribute is shared by every batch and captured graph of the process.
 template <class T, int kK>
-static cudaError_t configure_unit(int bytes, int* per_sm) {
+static cudaError_t configure_unit(int bytes, int smem_limit, int* per_sm) {
   cudaError_t e = cudaSuccess;
   if (bytes > 48 * 1024)
     e = cudaFuncSetAttribute(bwd_unit_kernel<T, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes);
+                             smem_limit);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bwd_unit_kernel<T, kK>, 32, bytes);
 }
 
-cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d) {
+cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_f, int* per_sm_d) {
   const int sf = bwd_slice_bytes<float>(us), sd = bwd_slice_bytes<Dual>(us);
   int tmp = 0;
   cudaError_t e;
-  if ((e = configure_unit<float, 0>(sf, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_unit<Dual, 0>(sd, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_unit<float, 3>(sf, per_sm_f)) != cudaSuccess) return e;
-  return configure_unit<Dual, 3>(sd, per_sm_d);
+  if ((e = configure_unit<float, 0>(sf, smem_limit, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_unit<Dual, 0>(sd, smem_limit, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_unit<float, 3>(sf, smem_limit, per_sm_f)) != cudaSuccess) return e;
+  return configure_unit<Dual, 3>(sd, smem_limit, per_sm_d);
 }
 
 int backward_slice_bytes(const UnitShape& us, bool dual) {
@@ -1012,14 +1032,14 @@ int backward_slice_bytes(const UnitShape& us, bool dual) {
 }  // namespace ccm
 
 // ---------------------------------------------------------------------------
-// Scratch for ccm_contacts_backward_noalloc: the per-unit slots of the reverse
+// Scratch for ccm_contacts_backward_noalloc: the per-item slots of the reverse
 // pass live in this fixed array instead of the batch's workspace, so that the
 // call needs no device memory of its own.  Every GPU that loads the library
 // holds the array (4 MiB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace ccm {
 
-constexpr int64_t kNoAllocSlotFloats = (int64_t)1 << 20;   // 2 n * 24 floats at most
+constexpr int64_t kNoAllocSlotFloats = (int64_t)1 << 20;   // 24 floats per work item
 static __device__ __align__(256) float g_noalloc_slots[kNoAllocSlotFloats];
 
 // Device address of g_noalloc_slots on `device`, looked up once per device
@@ -1039,7 +1059,7 @@ static cudaError_t noalloc_slots(int device, float** out) {
   return cudaSuccess;
 }
 
-int64_t noalloc_max_pairs() { return kNoAllocSlotFloats / 48; }
+int64_t noalloc_max_items() { return kNoAllocSlotFloats / 24; }
 
 cudaError_t launch_backward_noalloc(BwdLaunch L, int device, cudaStream_t stream) {
   float* slots = nullptr;

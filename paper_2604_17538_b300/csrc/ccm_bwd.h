@@ -22,15 +22,20 @@ namespace ccm {
 struct BwdLaunch {
   DevGeom g;
   const PairRec* pairs;
-  const int32_t* order;   // units by decreasing estimated cost
+  const WorkItem* items;      // work items (unit, feature-piece range)
+  const int32_t* order;       // item indices by decreasing estimated cost
+  int64_t n_items;
+  const int64_t* item_off;    // [n_pairs + 1] items of pair p: [item_off[p], item_off[p+1])
   int64_t n_pairs;
+  const int64_t* dev_items;   // if set: entries of `order` to run, read on device
+  const int64_t* dev_pairs;   // if set: pairs to reduce, read on device
   const float* pose_a;
   const float* pose_b;
   const float* ybar;    // [G, 8]
   const float* dir;     // [n, 12] or NULL
   KParams kp;
   UnitShape us;
-  float* part;          // [2n, 24] per-unit slots (workspace)
+  float* part;          // [n_items, 24] per-item slots (workspace)
   float* grad;          // [n, 12]
   float* hvp;           // [n, 12] or NULL
   float* jvp;           // [G, 8] or NULL
@@ -38,11 +43,11 @@ struct BwdLaunch {
 };
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream);
-cudaError_t configure_backward(const UnitShape& us, int* per_sm_f, int* per_sm_d);
+cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_f, int* per_sm_d);
 int backward_slice_bytes(const UnitShape& us, bool dual);
 
-// Variant with the per-unit slots in a fixed device array (no workspace).
+// Variant with the per-item slots in a fixed device array (no workspace).
 cudaError_t launch_backward_noalloc(BwdLaunch L, int device, cudaStream_t stream);
-int64_t noalloc_max_pairs();
+int64_t noalloc_max_items();
 
 }  // namespace ccm

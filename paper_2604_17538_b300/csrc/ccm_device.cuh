@@ -26,6 +26,15 @@ struct PairRec {
   int64_t goff;
 };
 
+// One warp's task: the feature pieces [fc0, fc1) of body F of unit
+// `unit` = 2 pair + side (side 0: F = A, S = B) against every piece of S.  A
+// unit is split into items of at most UnitShape::groups pieces so that large
+// bodies spread over many warps; items never share an output group.
+struct WorkItem {
+  int32_t unit;
+  uint16_t fc0, fc1;
+};
+
 struct DevGeom {
   const PieceRec* __restrict__ pieces;
   const BodyRec* __restrict__ bodies;

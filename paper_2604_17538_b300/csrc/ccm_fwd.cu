@@ -200,7 +200,8 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitSh
 template <bool kCount>
 __global__ void __launch_bounds__(128)
 unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
-                const int32_t* __restrict__ order, int64_t n_pairs,
+                const WorkItem* __restrict__ items, const int32_t* __restrict__ order,
+                int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -209,13 +210,14 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
   const UnitSlice sl = unit_slice(smem_raw + (size_t)warp * us.slice_bytes, us);
   int* dsub = sl.dsub;
   const bool no_cull = (kp.flags & 1u) != 0;
-  const int64_t n_units = 2 * n_pairs;
+  const int64_t n_run = dev_items ? *dev_items : n_items;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   FwdCounts cnt;
 
-  // heaviest units first, dealt round-robin to the warps (balanced, no atomics)
-  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < n_units; k += nwarps) {
-    const int64_t u = order[k];
+  // heaviest items first, dealt round-robin to the warps (balanced, no atomics)
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < n_run; k += nwarps) {
+    const WorkItem it = items[order[k]];
+    const int64_t u = it.unit;
     const int64_t pi = u >> 1;
     const int side = (int)(u & 1);
     const PairRec pr = pairs[pi];
@@ -228,10 +230,11 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
     rel_pose_f64(pF, pS, lane, Rr, tr);
     const float margin = 1e-6f * (1.0f + fabsf(tr[0]) + fabsf(tr[1]) + fabsf(tr[2]));
 
-    for (int fc0 = 0; fc0 < F.np;) {
-      // F chunk [fc0, fc1): up to 32 pieces within the vertex / edge budgets
+    for (int fc0 = it.fc0; fc0 < it.fc1;) {
+      // F chunk [fc0, fc1): up to us.groups pieces within the vertex / edge
+      // budgets (the host cut the item to one such chunk)
       int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < F.np && fc1 - fc0 < us.groups) {
+      while (fc1 < it.fc1 && fc1 - fc0 < us.groups) {
         const PieceRec p = g.pieces[F.p0 + fc1];
         if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
         V += p.nv;
@@ -338,23 +341,26 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   const size_t smem = (size_t)L.us.warps * L.us.slice_bytes;
   const int threads = 32 * L.us.warps;
   if (L.counters)
-    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a,
+    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
                                                              L.pose_b, L.kp, L.us, L.y, L.counters);
   else
-    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.order, L.n_pairs, L.pose_a,
+    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
                                                               L.pose_b, L.kp, L.us, L.y, L.counters);
   return cudaGetLastError();
 }
 
-cudaError_t configure_forward(const UnitShape& us, int* blocks_per_sm) {
+cudaError_t configure_forward(const UnitShape& us, int smem_limit, int* blocks_per_sm) {
   const int smem = us.warps * us.slice_bytes;
   cudaError_t e;
+  // The limit is raised to the device's opt-in maximum (not to this shape's
+  // size): the attribute is shared by every batch and captured graph of the
+  // process, and lowering it would invalidate their larger launches.
   if (smem > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(unit_fwd_kernel<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit)) != cudaSuccess)
       return e;
     if ((e = cudaFuncSetAttribute(unit_fwd_kernel<true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit)) != cudaSuccess)
       return e;
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, unit_fwd_kernel<false>,

@@ -9,8 +9,10 @@ namespace ccm {
 struct FwdLaunch {
   DevGeom g;
   const PairRec* pairs;
-  const int32_t* order;   // units (2 pair + side) by decreasing estimated cost
-  int64_t n_pairs;
+  const WorkItem* items;  // work items (unit, feature-piece range)
+  const int32_t* order;   // item indices by decreasing estimated cost
+  int64_t n_items;
+  const int64_t* dev_items;   // if set: number of entries of `order` to run, read on device
   const float* pose_a;
   const float* pose_b;
   KParams kp;
@@ -21,6 +23,6 @@ struct FwdLaunch {
 };
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);
-cudaError_t configure_forward(const UnitShape& us, int* blocks_per_sm);
+cudaError_t configure_forward(const UnitShape& us, int smem_limit, int* blocks_per_sm);
 
 }  // namespace ccm

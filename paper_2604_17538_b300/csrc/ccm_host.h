@@ -53,9 +53,13 @@ struct Batch {
   int64_t n = 0;
   int64_t G = 0;
   std::vector<int64_t> goff;
+  std::vector<PairRec> pairs;    // host copy of the pair table
   DevBuf d_pairs;                // pair table
-  DevBuf d_order;                // units by decreasing estimated cost
-  DevBuf d_part;                 // [2n, 24] per-unit slots of the reverse pass
+  int64_t n_items = 0;
+  DevBuf d_items;                // work items (depend on the tuning)
+  DevBuf d_item_order;           // item indices by decreasing estimated cost
+  DevBuf d_item_off;             // [n + 1] items of each pair
+  DevBuf d_part;                 // [n_items, 24] per-item slots of the reverse pass
   BatchMaxima mx;
   ccm_tuning tuning{};
   UnitShape us{};
@@ -66,7 +70,23 @@ struct Batch {
 
 ccm_status fail(ccm_status s, const char* fmt, ...);
 ccm_status cuda_fail(cudaError_t e, const char* what);
+
+#define CCM_CUDA(call, what)                           \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
 ccm_status make_kparams(const ccm_params* p, KParams* k);
+BatchMaxima body_maxima(const Context& c, int32_t body);
+void merge_maxima(BatchMaxima* m, const BatchMaxima& b);
+// Work items of the n pairs for shape `us`, appended in pair order: unit
+// indices are 2 (unit_pair0 + i) + side; cost[] gets each item's estimated
+// cost and item_off[] (if not NULL) the running item count after each pair.
+void make_items(const Context& c, const PairRec* pairs, int64_t n, int64_t unit_pair0,
+                const UnitShape& us, std::vector<WorkItem>* items, std::vector<int64_t>* cost,
+                std::vector<int64_t>* item_off);
+// Item indices by decreasing cost (ties: index order).
+std::vector<int32_t> items_by_cost(const std::vector<int64_t>& cost);
 ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom* B, Batch* bt);
 void default_tuning(ccm_tuning* t);
 ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t);

@@ -1,10 +1,12 @@
 """Autotuner of a batch's launch shape (``ccm_batch_set_tuning``).
 
-Times the forward, the reverse pass and the forward-over-reverse pass of a
-batch on its own poses for a few shared-memory budgets and keeps, for each
-pass, the fastest shape; the choice is written back into the batch.  The
-candidate set is small because the budgets only trade lane utilisation
-(bigger lists of live piece pairs) against resident warps (smaller slices).
+Times the passes of a batch on its own poses and keeps the fastest shape; the
+choice is written back into the batch.  First the work-item size (feature
+pieces per warp task: small items balance uneven bodies over the warps, large
+ones stage the SDF body's planes fewer times), timed on forward + reverse
+pass together since both passes run the same items; then the forward's and
+the reverse pass's shared-memory budgets, which trade lane utilisation (bigger
+lists of live piece pairs) against resident warps (smaller slices).
 """
 from __future__ import annotations
 
@@ -13,6 +15,7 @@ import itertools
 FWD_CANDIDATES = [dict(item_v=v, item_e=e, fwd_warps=w)
                   for (v, e), w in itertools.product([(128, 256), (256, 512), (512, 1024)], [1, 2, 4])]
 BWD_CANDIDATES = [dict(item_vb=v, item_eb=e) for v, e in [(64, 128), (128, 256), (256, 512), (512, 1024)]]
+GROUP_CANDIDATES = [dict(groups=g) for g in (4, 8, 16, 32)]
 
 
 def _time(fn, reps=5):
@@ -34,7 +37,22 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
     """Picks the fastest forward shape, then the fastest reverse-pass shape
     (timed with a direction when one is given, i.e. on the dual kernel)."""
     import torch
-    log = {"forward": {}, "reverse": {}}
+    log = {"items": {}, "forward": {}, "reverse": {}}
+    if ybar is None:
+        ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
+    gbest = None
+    for cand in GROUP_CANDIDATES:
+        try:
+            batch.set_tuning(**cand)
+            t = _time(lambda: (batch.contacts(pose_a, pose_b, params),
+                               batch.backward(pose_a, pose_b, ybar, direction, params)))
+        except Exception as ex:
+            log["items"][str(cand)] = repr(ex)
+            continue
+        log["items"][str(cand)] = t
+        if gbest is None or t < gbest[0]:
+            gbest = (t, cand)
+    batch.set_tuning(**gbest[1])
     best = None
     for cand in FWD_CANDIDATES:
         try:
@@ -47,8 +65,6 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
         if best is None or t < best[0]:
             best = (t, cand)
     batch.set_tuning(**best[1])
-    if ybar is None:
-        ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
     bbest = None
     for cand in BWD_CANDIDATES:
         try:

@@ -30,7 +30,7 @@ def test_header_declares_the_boundary():
     names = set(_declared())
     for n in ("ccm_create", "ccm_destroy", "ccm_load_geometry", "ccm_free_geometry",
               "ccm_output_size", "ccm_batch_create", "ccm_contacts", "ccm_contacts_backward",
-              "ccm_last_error"):
+              "ccm_last_error", "ccm_serve_start", "ccm_serve_stop", "ccm_submit", "ccm_poll"):
         assert n in names, n
 
 
@@ -45,6 +45,8 @@ def test_binding_matches_header(lib):
     for name, (_, args) in abi._SIGS.items():
         assert name in decl, f"{name} bound but not declared"
         assert len(args) == decl[name], (name, len(args), decl[name])
+    missing = set(decl) - set(abi._SIGS)
+    assert not missing, f"declared but not bound: {sorted(missing)}"
 
 
 def test_no_device_needed_for_defaults(lib):
@@ -52,3 +54,13 @@ def test_no_device_needed_for_defaults(lib):
     p = abi.default_params()
     assert abs(p.tau_sdf - 5e-3) < 1e-9 and p.trace_iters == 3 and p.d_max > 0
     assert lib.ccm_last_error() is not None
+
+
+def test_serve_config_layout_and_defaults(lib):
+    """The ctypes struct mirrors ccm_serve_config: the library's defaults land
+    in the right fields (a layout mismatch would scramble them)."""
+    from paper_2604_17538_b300 import abi
+    c = abi.default_serve_config()
+    assert (c.max_wave_pairs, c.max_wave_requests, c.max_queued) == (16384, 1024, 65536)
+    assert abs(c.params.tau_sdf - 5e-3) < 1e-9 and c.params.trace_iters == 3
+    assert (c.tuning.item_v, c.tuning.item_e, c.tuning.fwd_warps) == (256, 512, 2)

@@ -63,3 +63,33 @@ def test_uneven_derivatives_match_oracle(oracle_lib, ctx, uneven):
         tol = np.maximum(GRAD_RTOL, COND_FACTOR * k) * np.abs(ref).max(1) + 1e-6
         assert np.all(err <= tol), (name, float((err / (np.abs(ref).max(1) + 1e-30)).max()))
     batch.close()
+
+
+def test_work_item_size_and_budgets_change_only_rounding(ctx, uneven):
+    """Any launch shape gives the same contacts and gradients up to float
+    rounding order: items of 1, 3 or 32 feature pieces, small and large list
+    budgets, 1 or 4 forward warps.  Items of one piece split every body into
+    as many warp tasks as it has pieces, the most the reverse pass's per-pair
+    slot reduction ever adds up."""
+    import torch
+    from paper_2604_17538_b300 import api
+    batch, pa, pb = api.scene_to_device(uneven, ctx)
+    rng = np.random.default_rng(2)
+    ybar = torch.from_numpy(rng.normal(size=(batch.n_groups, 8)).astype(np.float32)).cuda()
+    y0 = batch.contacts(pa, pb).double().cpu().numpy()
+    g0, _, _ = batch.backward(pa, pb, ybar)
+    g0 = g0.double().cpu().numpy()
+    slack = weight_slack(uneven)
+    for t in (dict(groups=1), dict(groups=3, item_v=64, item_e=128, item_vb=64, item_eb=128),
+              dict(groups=32, item_v=1024, item_e=2048, item_vb=512, item_eb=1024, fwd_warps=1),
+              dict(groups=8, fwd_warps=4)):
+        batch.set_tuning(**t)
+        assert batch.get_tuning()["groups"] == t["groups"]
+        y = batch.contacts(pa, pb).double().cpu().numpy()
+        compare(y, y0, f"tuning {t}", a_slack=slack)
+        g, _, _ = batch.backward(pa, pb, ybar)
+        g = g.double().cpu().numpy()
+        assert np.all(np.isfinite(g))
+        err = np.abs(g - g0).max(1)
+        assert np.all(err <= GRAD_RTOL * np.abs(g0).max(1) + 1e-6), (t, float(err.max()))
+    batch.close()
