@@ -44,17 +44,20 @@ WORKLOAD = "4096 envs x 2 bodies x 8 hull pieces (64 pts); fwd + grad + HVP"
 COST = {"gate": 7, "val": 9, "grad": 15, "hv": 27, "dval": 20, "dgrad": 32, "dhv": 59}
 
 
-def work_model(c):
-    """Algorithmic FLOP and ex2 counts per launch from the forward counters."""
+def work_model(c, cv, ch):
+    """Algorithmic FLOP and ex2 counts per launch from exact device counters:
+    ``c`` of the forward, ``cv`` / ``ch`` of the reverse pass on float / on
+    dual numbers (plane evaluations by kind and pass)."""
     gm = c["gatepass"] + c["maxpass"]
     eg, ev = c["eval_grad"], c["eval_val"]
     fwd = (COST["gate"] * gm + COST["grad"] * eg + COST["val"] * ev, eg + ev)
-    # reverse pass: forward recomputation + adjoint (trace steps need gradients)
-    vjp = (2 * COST["gate"] * gm + eg * (COST["grad"] + COST["hv"]) + ev * (COST["val"] + COST["grad"]),
-           2 * (eg + ev))
-    hvp = (2 * COST["gate"] * gm + eg * (COST["dgrad"] + COST["dhv"]) + ev * (COST["dval"] + COST["dgrad"]),
-           2 * (eg + ev))
-    return {"forward": fwd, "vjp": vjp, "hvp": hvp}
+
+    def rev(k, dual):
+        g, v, h = ("dgrad", "dval", "dhv") if dual else ("grad", "val", "hv")
+        flop = (COST["gate"] * (k["gatepass"] + k["maxpass"]) + COST[g] * k["p1_grad"]
+                + COST[v] * k["p1_val"] + COST[h] * k["p2_hv"] + COST[g] * k["p2_grad"])
+        return flop, k["p1_grad"] + k["p1_val"] + k["p2_hv"] + k["p2_grad"]
+    return {"forward": fwd, "vjp": rev(cv, False), "hvp": rev(ch, True)}
 
 
 def kernel_source_hash():
@@ -150,20 +153,30 @@ def run_ours(args, rank, world):
     u = torch.from_numpy(u_h).cuda()
     piece_pairs = sc.piece_pairs()
 
-    # exact work counters of the forward pass (outside the timed region)
+    y = torch.empty((G, 8), device="cuda")
+    saved = batch.saved_buffer()
+
+    # exact work counters of the three passes (outside the timed region)
     cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
     batch.contacts(pa, pb, counters=cnt)
     counters = dict(zip(abi.COUNTER_NAMES, cnt.cpu().tolist()))
-    model = work_model(counters)
-
-    y = torch.empty((G, 8), device="cuda")
+    batch.contacts(pa, pb, out=y, saved=saved)
+    cnt_v = torch.zeros(8, dtype=torch.int64, device="cuda")
+    batch.backward(pa, pb, ybar, saved=saved, counters=cnt_v)
+    cnt_h = torch.zeros(8, dtype=torch.int64, device="cuda")
+    batch.backward(pa, pb, ybar, u, want_jvp=True, saved=saved, counters=cnt_h)
+    counters_vjp = dict(zip(abi.BWD_COUNTER_NAMES, cnt_v.cpu().tolist()))
+    counters_hvp = dict(zip(abi.BWD_COUNTER_NAMES, cnt_h.cpu().tolist()))
+    model = work_model(counters, counters_vjp, counters_hvp)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # one step: forward keeping its record for the reverse passes (as the
+    # autograd Function does), gradient, then H u and J u
     def step():
-        batch.contacts(pa, pb, out=y)
-        g, _, _ = batch.backward(pa, pb, ybar)
-        g2, h, j = batch.backward(pa, pb, ybar, u, want_jvp=True)
+        batch.contacts(pa, pb, out=y, saved=saved)
+        g, _, _ = batch.backward(pa, pb, ybar, saved=saved)
+        g2, h, j = batch.backward(pa, pb, ybar, u, want_jvp=True, saved=saved)
         return g, h
 
     for _ in range(args.warmup):
@@ -181,11 +194,11 @@ def run_ours(args, rank, world):
         flush.zero_()                       # L2 (126 MB) flushed between steps, untimed
         e = evs[k]
         e[0].record(stream)
-        batch.contacts(pa, pb, out=y)
+        batch.contacts(pa, pb, out=y, saved=saved)
         e[1].record(stream)
-        batch.backward(pa, pb, ybar)
+        batch.backward(pa, pb, ybar, saved=saved)
         e[2].record(stream)
-        batch.backward(pa, pb, ybar, u, want_jvp=True)
+        batch.backward(pa, pb, ybar, u, want_jvp=True, saved=saved)
         e[3].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -216,9 +229,9 @@ def run_ours(args, rank, world):
         pb_d.copy_(pb_h, non_blocking=True)
         yb_d.copy_(yb_h, non_blocking=True)
         u_d.copy_(uu_h, non_blocking=True)
-        yy = batch.contacts(pa_d, pb_d)
-        gg, _, _ = batch.backward(pa_d, pb_d, yb_d)
-        _, hh, jj = batch.backward(pa_d, pb_d, yb_d, u_d, want_jvp=True)
+        yy = batch.contacts(pa_d, pb_d, saved=saved)
+        gg, _, _ = batch.backward(pa_d, pb_d, yb_d, saved=saved)
+        _, hh, jj = batch.backward(pa_d, pb_d, yb_d, u_d, want_jvp=True, saved=saved)
         y_o.copy_(yy, non_blocking=True)
         g_o.copy_(gg, non_blocking=True)
         h_o.copy_(hh, non_blocking=True)
@@ -304,7 +317,7 @@ def run_ours(args, rank, world):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 5 * K,
             "roofline": roof,
-            "work_counters": counters,
+            "work_counters": {"forward": counters, "vjp": counters_vjp, "hvp": counters_hvp},
             "clocks": clocks,
             "wall_s_timed_loop": t_wall,
         }
@@ -395,18 +408,19 @@ def run_uneven(args, rank, world):
     tuning, _ = tune.autotune(batch, pa, pb, ybar)
     y = torch.empty((G, 8), device="cuda")
     grad = torch.empty((n, 12), device="cuda")
+    saved = batch.saved_buffer()
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):            # warm-up outside the capture
         for _ in range(args.warmup):
-            batch.contacts(pa, pb, out=y)
-            batch.backward(pa, pb, ybar, out=(grad, None, None))
+            batch.contacts(pa, pb, out=y, saved=saved)
+            batch.backward(pa, pb, ybar, out=(grad, None, None), saved=saved)
     torch.cuda.current_stream().wait_stream(stream)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        batch.contacts(pa, pb, out=y)
-        batch.backward(pa, pb, ybar, out=(grad, None, None))
+        batch.contacts(pa, pb, out=y, saved=saved)
+        batch.backward(pa, pb, ybar, out=(grad, None, None), saved=saved)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         graph.replay()

@@ -174,6 +174,31 @@ CCM_API ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, c
                                  const ccm_params* prm, const float* ybar, const float* dir,
                                  float* grad, float* hvp, float* jvp, ccm_stream stream);
 
+/* Floats per output group of the record ccm_contacts_save keeps for the
+ * reverse pass: the group's blend partial and which of the SDF body's pieces
+ * gave it a contact of non-zero weight. */
+#define CCM_SAVED_FLOATS 26
+
+/* ccm_contacts that also fills saved (device [G, CCM_SAVED_FLOATS] float32,
+ * fully overwritten) for ccm_contacts_backward_saved.  Asynchronous on
+ * `stream`.  Errors: CCM_ERR_INVALID, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_contacts_save(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                     const ccm_params* prm, float* y, float* saved,
+                                     ccm_stream stream);
+
+/* ccm_contacts_backward given the record of a ccm_contacts_save call with the
+ * same batch, poses and params: its passes visit only the (piece, piece)
+ * directions that gave a contact in the forward pass, the only ones with a
+ * non-zero adjoint, instead of re-running the broad phase over all of them.
+ * Results equal ccm_contacts_backward's up to float rounding order; a record
+ * of other poses gives wrong results.  Asynchronous on `stream`.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pose_a,
+                                               const float* pose_b, const ccm_params* prm,
+                                               const float* saved, const float* ybar,
+                                               const float* dir, float* grad, float* hvp,
+                                               float* jvp, ccm_stream stream);
+
 /* Same as ccm_contacts_backward, for callers that cannot obtain device
  * memory for scratch -- e.g. code running while another framework owns the
  * whole device memory pool, or a real-time loop that forbids allocation after
@@ -216,6 +241,29 @@ CCM_API ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, co
                                 const ccm_params* prm, float* y, int64_t* counters,
                                 ccm_stream stream);
 
+/* Work counters of one reverse pass, for the roofline: directions examined,
+ * directions in lists, and plane evaluations by kind -- pass-1 gate and
+ * max-plane tests, pass-1 evaluations with gradient and value-only trace
+ * steps, pass-2 evaluations with gradient and Hessian-vector product and
+ * pass-2 trace steps with gradient.  Same as ccm_contacts_backward_saved
+ * (saved may be NULL: ccm_contacts_backward) plus device atomics on
+ * `counters` (device, CCM_N_COUNTERS int64, zeroed by the caller). */
+enum {
+  CCM_BWD_CNT_DIRS = 0,       /* directions examined by a gate or the hit marks */
+  CCM_BWD_CNT_DIRS_LIVE = 1,  /* directions run through lists */
+  CCM_BWD_CNT_MAXPASS = 2,    /* plane evaluations of the max-plane passes */
+  CCM_BWD_CNT_GATEPASS = 3,   /* plane evaluations of piece-pair gates */
+  CCM_BWD_CNT_P1_GRAD = 4,    /* pass 1: plane evaluations with gradient */
+  CCM_BWD_CNT_P1_VAL = 5,     /* pass 1: value-only trace-step evaluations */
+  CCM_BWD_CNT_P2_HV = 6,      /* pass 2: evaluations with gradient and H v */
+  CCM_BWD_CNT_P2_GRAD = 7     /* pass 2: trace-step evaluations with gradient */
+};
+CCM_API ccm_status ccm_contacts_backward_counted(ccm_batch batch, const float* pose_a,
+                                                 const float* pose_b, const ccm_params* prm,
+                                                 const float* saved, const float* ybar,
+                                                 const float* dir, float* grad, float* hvp,
+                                                 float* jvp, int64_t* counters, ccm_stream stream);
+
 /* Measures, on `device`, the throughput of the arithmetic units the contact
  * kernels are bound by: FP32 FMA (scalar and packed f32x2, in TFLOP/s, an
  * FMA counted as 2 FLOP) and the SFU's ex2 (in tera-ops/s).  Synchronous;
@@ -255,8 +303,8 @@ CCM_API void ccm_default_serve_config(ccm_serve_config* cfg);
  * and pinned host), captures one graph per set and starts the scheduler
  * thread.  Synchronous.  Bodies loaded later may be requested if no piece of
  * theirs has more vertices, planes or edges than the largest resident at start.
- * Device memory: two sets of wave buffers of 368 bytes per pair plus
- * 64 bytes per output group, which must fit the context's HBM budget.
+ * Device memory: two sets of wave buffers of 168 bytes per pair, 112 per
+ * work item and 168 per output group, which must fit the context's HBM budget.
  * Errors: CCM_ERR_INVALID (already started, bad capacities or params, no
  * resident geometry), CCM_ERR_OOM (the wave buffers do
  * not fit the context's HBM budget or cudaMalloc failed), CCM_ERR_CUDA. */

@@ -22,8 +22,11 @@ STATUS_NAMES = ["CCM_OK", "CCM_ERR_INVALID", "CCM_ERR_OOM", "CCM_ERR_CUDA", "CCM
                 "CCM_ERR_BUSY", "CCM_ERR_NOT_READY", "CCM_ERR_UNKNOWN_TICKET"]
 CCM_FLAG_NO_CULL = 1
 CCM_N_COUNTERS = 8
+CCM_SAVED_FLOATS = 26
 COUNTER_NAMES = ["dirs", "dirs_live", "maxpass", "gatepass", "eval_grad", "eval_val",
                  "contacts", "features"]
+BWD_COUNTER_NAMES = ["dirs", "dirs_live", "maxpass", "gatepass", "p1_grad", "p1_val", "p2_hv",
+                     "p2_grad"]
 
 
 class CcmError(RuntimeError):
@@ -85,6 +88,9 @@ _SIGS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ccm_contacts_backward": (C.c_int, [C.c_void_p] * 10),
     "ccm_contacts_backward_noalloc": (C.c_int, [C.c_void_p] * 10),
+    "ccm_contacts_save": (C.c_int, [C.c_void_p] * 7),
+    "ccm_contacts_backward_saved": (C.c_int, [C.c_void_p] * 11),
+    "ccm_contacts_backward_counted": (C.c_int, [C.c_void_p] * 12),
     "ccm_peak_probe": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ccm_default_serve_config": (None, [C.c_void_p]),
     "ccm_serve_start": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -121,8 +121,16 @@ class Batch:
                 and tuple(p.shape) == (self.n_pairs, 12)):
             raise ValueError(f"pose must be a contiguous cuda float32 [{self.n_pairs}, 12] tensor")
 
-    def contacts(self, pose_a, pose_b, params=None, out=None, counters=None):
-        """Group outputs y [G, 8] (d, a, p, n) as a cuda tensor."""
+    def saved_buffer(self, device="cuda"):
+        """An uninitialised [G, CCM_SAVED_FLOATS] record for ``contacts(saved=...)``."""
+        import torch
+        return torch.empty((self.n_groups, abi.CCM_SAVED_FLOATS), device=device,
+                           dtype=torch.float32)
+
+    def contacts(self, pose_a, pose_b, params=None, out=None, counters=None, saved=None):
+        """Group outputs y [G, 8] (d, a, p, n) as a cuda tensor.  ``saved``: a
+        ``saved_buffer()`` that receives the record ``backward(saved=...)``
+        uses (``ccm_contacts_save``)."""
         import torch
         self._check_pose(pose_a)
         self._check_pose(pose_b)
@@ -130,19 +138,31 @@ class Batch:
             out = torch.empty((self.n_groups, 8), device=pose_a.device, dtype=torch.float32)
         prm = _params(params)
         s = abi.stream_of(pose_a)
-        if counters is None:
-            check(lib().ccm_contacts(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
-                                     ptr(out), s))
-        else:
+        if counters is not None:
             check(lib().ccm_contacts_counted(self.handle, ptr(pose_a), ptr(pose_b),
                                              C.byref(prm), ptr(out), ptr(counters), s))
+        elif saved is not None:
+            self._check_saved(saved)
+            check(lib().ccm_contacts_save(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
+                                          ptr(out), ptr(saved), s))
+        else:
+            check(lib().ccm_contacts(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
+                                     ptr(out), s))
         return out
 
+    def _check_saved(self, saved):
+        import torch
+        if not (saved.is_cuda and saved.dtype == torch.float32 and saved.is_contiguous()
+                and tuple(saved.shape) == (self.n_groups, abi.CCM_SAVED_FLOATS)):
+            raise ValueError("saved must be a contiguous cuda float32 "
+                             f"[{self.n_groups}, {abi.CCM_SAVED_FLOATS}] tensor")
+
     def backward(self, pose_a, pose_b, ybar, direction=None, params=None, want_jvp=False,
-                 out=None):
+                 out=None, saved=None, counters=None):
         """(grad [n,12], hvp [n,12] | None, jvp [G,8] | None) of <ybar, y> in
         the twist chart (w_A, v_A, w_B, v_B); ``out`` = preallocated
-        (grad, hvp, jvp) tensors (any may be None)."""
+        (grad, hvp, jvp) tensors (any may be None); ``saved`` = the record of
+        a ``contacts(saved=...)`` call with the same poses and params."""
         import torch
         self._check_pose(pose_a)
         self._check_pose(pose_b)
@@ -160,9 +180,24 @@ class Batch:
                 jvp = o_j if o_j is not None else torch.empty((self.n_groups, 8), device=dev,
                                                               dtype=torch.float32)
         prm = _params(params)
-        check(lib().ccm_contacts_backward(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
-                                          ptr(ybar), ptr(direction), ptr(grad), ptr(hvp),
-                                          ptr(jvp), abi.stream_of(pose_a)))
+        if saved is not None:
+            self._check_saved(saved)
+        if counters is not None:
+            check(lib().ccm_contacts_backward_counted(self.handle, ptr(pose_a), ptr(pose_b),
+                                                      C.byref(prm), ptr(saved), ptr(ybar),
+                                                      ptr(direction), ptr(grad), ptr(hvp),
+                                                      ptr(jvp), ptr(counters),
+                                                      abi.stream_of(pose_a)))
+        elif saved is None:
+            check(lib().ccm_contacts_backward(self.handle, ptr(pose_a), ptr(pose_b),
+                                              C.byref(prm), ptr(ybar), ptr(direction),
+                                              ptr(grad), ptr(hvp), ptr(jvp),
+                                              abi.stream_of(pose_a)))
+        else:
+            check(lib().ccm_contacts_backward_saved(self.handle, ptr(pose_a), ptr(pose_b),
+                                                    C.byref(prm), ptr(saved), ptr(ybar),
+                                                    ptr(direction), ptr(grad), ptr(hvp),
+                                                    ptr(jvp), abi.stream_of(pose_a)))
         return grad, hvp, jvp
 
 

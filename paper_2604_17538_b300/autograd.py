@@ -5,10 +5,11 @@ outputs y [G, 8] of ``ccm_contacts`` and is differentiable with respect to the
 twists (w_X, v_X) of the two bodies of every pair, in the chart
 R_X <- Exp([w_X]x) R_X, t_X <- t_X + v_X.  The twists must be zero: they are a
 local chart at the given poses.  The backward pass is the hand-written adjoint
-kernel (``ccm_contacts_backward``); its own backward -- double backward --
-calls the same kernel with a direction and returns the Hessian-vector product
-and the output tangents, so ``torch.autograd.grad(..., create_graph=True)``
-followed by a second ``grad`` gives H u.
+kernel (``ccm_contacts_backward_saved``, given the record the forward kept
+with ``ccm_contacts_save``); its own backward -- double backward -- calls the
+same kernel with a direction and returns the Hessian-vector product and the
+output tangents, so ``torch.autograd.grad(..., create_graph=True)`` followed
+by a second ``grad`` gives H u.
 """
 from __future__ import annotations
 
@@ -21,34 +22,36 @@ class _ContactsGrad(torch.autograd.Function):
     """grad(ybar) = d<ybar, y>/d(twist) at the current poses."""
 
     @staticmethod
-    def forward(ctx, ybar, twist_a, twist_b, batch, pose_a, pose_b, params):
-        grad, _, _ = batch.backward(pose_a, pose_b, ybar, None, params)
+    def forward(ctx, ybar, twist_a, twist_b, batch, pose_a, pose_b, params, saved):
+        grad, _, _ = batch.backward(pose_a, pose_b, ybar, None, params, saved=saved)
         ctx.batch, ctx.params = batch, params
-        ctx.save_for_backward(ybar, pose_a, pose_b)
+        ctx.save_for_backward(ybar, pose_a, pose_b, saved)
         return grad
 
     @staticmethod
     def backward(ctx, gbar):
-        ybar, pose_a, pose_b = ctx.saved_tensors
+        ybar, pose_a, pose_b, saved = ctx.saved_tensors
         u = gbar.contiguous()
-        _, hvp, jvp = ctx.batch.backward(pose_a, pose_b, ybar, u, ctx.params, want_jvp=True)
+        _, hvp, jvp = ctx.batch.backward(pose_a, pose_b, ybar, u, ctx.params, want_jvp=True,
+                                         saved=saved)
         # d<gbar, grad>/d ybar = J gbar ;  d<gbar, grad>/d twist = H gbar
-        return jvp, hvp[:, :6], hvp[:, 6:], None, None, None, None
+        return jvp, hvp[:, :6], hvp[:, 6:], None, None, None, None, None
 
 
 class _Contacts(torch.autograd.Function):
     @staticmethod
     def forward(ctx, twist_a, twist_b, batch, pose_a, pose_b, params):
-        y = batch.contacts(pose_a, pose_b, params)
+        saved = batch.saved_buffer(pose_a.device)
+        y = batch.contacts(pose_a, pose_b, params, saved=saved)
         ctx.batch, ctx.params = batch, params
-        ctx.save_for_backward(twist_a, twist_b, pose_a, pose_b)
+        ctx.save_for_backward(twist_a, twist_b, pose_a, pose_b, saved)
         return y
 
     @staticmethod
     def backward(ctx, ybar):
-        twist_a, twist_b, pose_a, pose_b = ctx.saved_tensors
+        twist_a, twist_b, pose_a, pose_b, saved = ctx.saved_tensors
         g = _ContactsGrad.apply(ybar.contiguous(), twist_a, twist_b, ctx.batch, pose_a, pose_b,
-                                ctx.params)
+                                ctx.params, saved)
         return g[:, :6], g[:, 6:], None, None, None, None
 
 

@@ -335,15 +335,42 @@ ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t) {
 
 ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
                         const ccm_params* prm, float* y, ccm_stream stream) {
-  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr,
+  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr, nullptr,
                      static_cast<cudaStream_t>(stream));
 }
 
 ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, const float* pose_b,
                                  const ccm_params* prm, const float* ybar, const float* dir,
                                  float* grad, float* hvp, float* jvp, ccm_stream stream) {
-  return run_backward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, ybar, dir, grad, hvp,
-                      jvp, static_cast<cudaStream_t>(stream));
+  return run_backward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, nullptr, ybar, dir, grad, hvp,
+                      jvp, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+ccm_status ccm_contacts_save(ccm_batch batch, const float* pose_a, const float* pose_b,
+                             const ccm_params* prm, float* y, float* saved, ccm_stream stream) {
+  if (!saved) return fail(CCM_ERR_INVALID, "saved is NULL");
+  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, saved, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                       const ccm_params* prm, const float* saved,
+                                       const float* ybar, const float* dir, float* grad,
+                                       float* hvp, float* jvp, ccm_stream stream) {
+  if (!saved) return fail(CCM_ERR_INVALID, "saved is NULL");
+  return run_backward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, saved, ybar, dir,
+                      grad, hvp, jvp, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+ccm_status ccm_contacts_backward_counted(ccm_batch batch, const float* pose_a,
+                                         const float* pose_b, const ccm_params* prm,
+                                         const float* saved, const float* ybar, const float* dir,
+                                         float* grad, float* hvp, float* jvp, int64_t* counters,
+                                         ccm_stream stream) {
+  if (!counters) return fail(CCM_ERR_INVALID, "counters is NULL");
+  return run_backward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, saved, ybar, dir,
+                      grad, hvp, jvp, reinterpret_cast<unsigned long long*>(counters),
+                      static_cast<cudaStream_t>(stream));
 }
 
 ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
@@ -377,6 +404,8 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   L.pose_b = pose_b;
   L.ybar = ybar;
   L.dir = dir;
+  L.saved = nullptr;
+  L.counters = nullptr;
   L.kp = kp;
   L.us = b->us;
   L.part = nullptr;
@@ -395,7 +424,7 @@ ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const floa
                                 const ccm_params* prm, float* y, int64_t* counters,
                                 ccm_stream stream) {
   if (!counters) return fail(CCM_ERR_INVALID, "counters is NULL");
-  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y,
+  return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr,
                      reinterpret_cast<unsigned long long*>(counters),
                      static_cast<cudaStream_t>(stream));
 }
@@ -403,6 +432,8 @@ ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, const floa
 }  // extern "C"
 
 namespace ccm {
+
+static_assert(kSavedFloats == CCM_SAVED_FLOATS, "saved record layout");
 
 BatchMaxima body_maxima(const Context& c, int32_t body) {
   BatchMaxima m;
@@ -581,7 +612,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
 }
 
 ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
-                        const float* ybar, const float* dir, float* grad, float* hvp, float* jvp,
+                        const float* saved, const float* ybar, const float* dir, float* grad,
+                        float* hvp, float* jvp, unsigned long long* counters,
                         cudaStream_t stream) {
   if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
   if (b->n == 0) return CCM_OK;
@@ -605,6 +637,8 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.pose_b = pose_b;
   L.ybar = ybar;
   L.dir = dir;
+  L.saved = saved;
+  L.counters = counters;
   L.kp = kp;
   L.us = b->us;
   L.part = static_cast<float*>(b->d_part.ptr);
@@ -627,7 +661,7 @@ void Batch::release() {
 }
 
 ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
-                       float* y, unsigned long long* counters, cudaStream_t stream) {
+                       float* y, float* saved, unsigned long long* counters, cudaStream_t stream) {
   if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
   if (b->n == 0) return CCM_OK;
   if (!pose_a || !pose_b || !y) return fail(CCM_ERR_INVALID, "NULL pose or output pointer");
@@ -647,6 +681,7 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   L.kp = kp;
   L.us = b->us;
   L.y = y;
+  L.saved = saved;
   L.counters = counters;
   L.grid = b->grid;
   cudaError_t e = launch_forward(L, stream);

@@ -20,7 +20,7 @@
 #include <algorithm>
 #include <mutex>
 
-#include "ccm_dual.cuh"
+#include "ccm_blend.cuh"
 #include "ccm_unit.cuh"
 #include "ccm_bwd.h"
 
@@ -185,121 +185,6 @@ __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float 
   return r;
 }
 
-// ---------------------------------------------------------------------------
-// Sec. 4.4 blend partials on T (online softmax).  Besides the normaliser U a
-// partial keeps a reference contact r -- the one with the largest logit -- and
-// the weighted differences sum_j u_j (x_j - x_r) of every blended quantity
-// x = (d_c, f, p, grad phi), rather than the plain sums.  The adjoint needs
-// g_c - gbar for g = ybar . (contact values); formed from differences to r it
-// carries no cancellation, and it is exactly 0 for a group whose only active
-// contact is r (there 1/U = 1/f can be huge near the gate edge).
-// ---------------------------------------------------------------------------
-template <class T> struct PartT {
-  T M, U;
-  T rd, rf;          // reference contact: mollified depth, transition weight
-  V3T<T> rp, rn;     // reference point, gradient
-  T Dd, Da;          // sum u (d_c - rd), sum u (f - rf)
-  V3T<T> Dp, Dn;     // sum u (p - rp), sum u (grad phi - rn)
-};
-
-template <class T> __device__ __forceinline__ V3T<T> zero3t() { return v3(T(0.f), T(0.f), T(0.f)); }
-
-template <class T> __device__ __forceinline__ void part_zero(PartT<T>& c) {
-  c.M = T(-INFINITY);
-  c.U = c.rd = c.rf = c.Dd = c.Da = T(0.f);
-  c.rp = c.rn = c.Dp = c.Dn = zero3t<T>();
-}
-
-template <class T>
-__device__ __forceinline__ void part_from_contact(PartT<T>& c, T f, T dc, V3T<T> p, V3T<T> g,
-                                                  float c_blend) {
-  if (val(f) > 0.f) {
-    c.M = dc * (-c_blend);
-    c.U = f;
-    c.rd = dc;
-    c.rf = f;
-    c.rp = p;
-    c.rn = g;
-    c.Dd = c.Da = T(0.f);
-    c.Dp = c.Dn = zero3t<T>();
-  } else {
-    part_zero(c);
-  }
-}
-
-template <class T> __device__ __forceinline__ V3T<T> axpy3(T a, V3T<T> x, V3T<T> y) {
-  return v3(fma_t(a, x.x, y.x), fma_t(a, x.y, y.y), fma_t(a, x.z, y.z));
-}
-template <class T> __device__ __forceinline__ V3T<T> sub3(V3T<T> a, V3T<T> b) {
-  return v3(a.x - b.x, a.y - b.y, a.z - b.z);
-}
-template <class T> __device__ __forceinline__ V3T<T> scale3(T a, V3T<T> x) {
-  return v3(a * x.x, a * x.y, a * x.z);
-}
-
-// a <- a (+) b; the reference of the partial with the larger logit is kept
-// (a's on ties), the other's differences are re-based onto it
-template <class T> __device__ __forceinline__ void part_combine(PartT<T>& a, const PartT<T>& b) {
-  if (val(b.M) == -INFINITY) return;
-  if (val(a.M) == -INFINITY) { a = b; return; }
-  const bool keep_a = val(a.M) >= val(b.M);
-  const PartT<T>& H = keep_a ? a : b;   // keeps its reference
-  const PartT<T>& O = keep_a ? b : a;   // re-based
-  const T rO = ex2_t(O.M - H.M);
-  const T uO = O.U * rO;
-  PartT<T> r;
-  r.M = H.M;
-  r.rd = H.rd; r.rf = H.rf; r.rp = H.rp; r.rn = H.rn;
-  r.U = H.U + uO;
-  r.Dd = fma_t(rO, O.Dd, fma_t(uO, O.rd - H.rd, H.Dd));
-  r.Da = fma_t(rO, O.Da, fma_t(uO, O.rf - H.rf, H.Da));
-  r.Dp = axpy3(rO, O.Dp, axpy3(uO, sub3(O.rp, H.rp), H.Dp));
-  r.Dn = axpy3(rO, O.Dn, axpy3(uO, sub3(O.rn, H.rn), H.Dn));
-  a = r;
-}
-
-__device__ __forceinline__ float shfl_down_t(float v, int o) { return __shfl_down_sync(kFull, v, o); }
-__device__ __forceinline__ Dual shfl_down_t(Dual v, int o) {
-  return Dual(__shfl_down_sync(kFull, v.v, o), __shfl_down_sync(kFull, v.d, o));
-}
-__device__ __forceinline__ float shfl_xor_t(float v, int o) { return __shfl_xor_sync(kFull, v, o); }
-__device__ __forceinline__ Dual shfl_xor_t(Dual v, int o) {
-  return Dual(__shfl_xor_sync(kFull, v.v, o), __shfl_xor_sync(kFull, v.d, o));
-}
-template <class T> __device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_t(v, o);
-  return v;
-}
-
-template <class T> __device__ __forceinline__ V3T<T> shfl_down3(V3T<T> x, int o) {
-  return v3(shfl_down_t(x.x, o), shfl_down_t(x.y, o), shfl_down_t(x.z, o));
-}
-template <class T> __device__ __forceinline__ PartT<T> part_shfl_down(const PartT<T>& c, int o) {
-  PartT<T> r;
-  r.M = shfl_down_t(c.M, o); r.U = shfl_down_t(c.U, o);
-  r.rd = shfl_down_t(c.rd, o); r.rf = shfl_down_t(c.rf, o);
-  r.rp = shfl_down3(c.rp, o); r.rn = shfl_down3(c.rn, o);
-  r.Dd = shfl_down_t(c.Dd, o); r.Da = shfl_down_t(c.Da, o);
-  r.Dp = shfl_down3(c.Dp, o); r.Dn = shfl_down3(c.Dn, o);
-  return r;
-}
-
-// segmented fold of lane contacts sorted by key into the group table
-template <class T>
-__device__ void fold_t(PartT<T> c, int key, PartT<T>* acc, int lane) {
-  const unsigned seg = __match_any_sync(kFull, key);
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const PartT<T> b = part_shfl_down(c, o);
-    if (lane + o < 32 && ((seg >> (lane + o)) & 1u)) part_combine(c, b);
-  }
-  if ((__ffs(seg) - 1) == lane && key != 0xffff && val(c.M) != -INFINITY) {
-    PartT<T> g = acc[key];
-    part_combine(g, c);
-    acc[key] = g;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // per-group adjoint coefficients and the contact adjoint
@@ -361,10 +246,14 @@ template <class T> struct BwdSlice {
   uint16_t* vlist;    // [item_v]
   uint16_t* elist;    // [item_e]
   uint8_t* need;      // [item_v]
+  uint16_t* am;       // [item_v] a plane attaining the max-plane value
+  uint32_t* hit;      // [groups * kHitWords] directions that gave a contact in pass 1
 };
+
 
 template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShape& u) {
   int b = 0;
+  b += align16i(4 * kHitWords * u.groups);
   b += 16 * u.plane_budget;
   b += align16i(8 * u.spiece_budget);
   b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
@@ -380,11 +269,13 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
   b += align16i(2 * u.item_vb);
   b += align16i(2 * u.item_eb);
   b += align16i(u.item_vb);
+  b += align16i(2 * u.item_vb);
   return b;
 }
 
 template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, const UnitShape& u) {
   BwdSlice<T> s;
+  s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * kHitWords * u.groups);
   s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
   s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * u.spiece_budget);
   s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
@@ -402,7 +293,8 @@ template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, con
   s.grad = reinterpret_cast<V3T<T>*>(p);       p += align16i((int)sizeof(V3T<T>) * u.item_vb);
   s.vlist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_vb);
   s.elist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_eb);
-  s.need = reinterpret_cast<uint8_t*>(p);
+  s.need = reinterpret_cast<uint8_t*>(p);      p += align16i(u.item_vb);
+  s.am = reinterpret_cast<uint16_t*>(p);
   return s;
 }
 
@@ -508,9 +400,15 @@ template <class T> struct Accum {
   V3T<T> X1, X2;   // sum x_bar, sum x cross x_bar (S frame)
 };
 
-template <class T, int kPass, int kK>
-__device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, const KParams& kp,
-                             int lane, Accum<T>& ac) {
+// Work counters of a counted reverse pass (CCM_BWD_CNT_* of ccm.h): plane
+// evaluations by kind and pass, per lane, summed at the end of the kernel.
+struct BwdCounts {
+  unsigned long long dirs = 0, live = 0, maxp = 0, gate = 0, g1 = 0, v1 = 0, h2 = 0, g2 = 0;
+};
+
+template <class T, int kPass, int kK, bool kCount>
+__device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int sc0,
+                             const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt) {
   const int* dsub = sl.dsub;
   for (int t = lane; t < TV; t += 32) {
     const int r = find_dir(sl.pv, nd, t);
@@ -518,8 +416,11 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
     const int4 f = sl.fp[code >> 16];
     const int2 s = sl.sp[code & 0xffff];
     const V3T<T> x = sl.xs[f.x + t - sl.pv[r]];
-    sl.m[t] = max_plane(sl.planes + s.x, s.y, val(x.x), val(x.y), val(x.z));
+    int arg;
+    sl.m[t] = max_plane_arg(sl.planes + s.x, s.y, val(x.x), val(x.y), val(x.z), arg);
+    sl.am[t] = (uint16_t)arg;
     sl.need[t] = 0;
+    if (kCount) cnt.maxp += s.y;
   }
   __syncwarp();
   int n_e = 0;
@@ -529,13 +430,15 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
     if (t < TE) {
       const int r = find_dir(sl.pe, nd, t);
       const int4 f = sl.fp[dsub[r] >> 16];
+      const int2 s = sl.sp[dsub[r] & 0xffff];
       const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
       const int i0 = e & 0xffff, i1 = e >> 16;
       const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
       const V3T<T> a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
-      const float dx = val(b.x) - val(a.x), dy = val(b.y) - val(a.y), dz = val(b.z) - val(a.z);
-      const float L = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-      live = 0.5f * (sl.m[t0v] + sl.m[t1v] - L) < kp.d_max;
+      const float lb = edge_plane_bound(sl.planes[s.x + sl.am[t0v]], sl.planes[s.x + sl.am[t1v]],
+                                        val(b.x) - val(a.x), val(b.y) - val(a.y),
+                                        val(b.z) - val(a.z), sl.m[t0v], sl.m[t1v]);
+      live = lb - kEdgeTol < kp.d_max;
       if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
     }
     const unsigned bal = __ballot_sync(kFull, live);
@@ -568,6 +471,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
       const V3T<T> x = sl.xs[f.x + t - sl.pv[r]];
       const float m = sl.m[t];
       key = g;
+      if (kCount) { if (kPass == 1) cnt.g1 += s.y; else cnt.h2 += s.y; }
       if (kPass == 1) {
         const SdfT<T> e = sdf_t<T, 1>(sl.planes + s.x, s.y, x, m, x, kp);
         sl.phi[t] = e.phi;
@@ -576,6 +480,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
           transition_t(e.phi, kp, w, wp);
           const T dc = fma_t(w, e.phi - kp.d_max, T(kp.d_max));
           part_from_contact(c, w, dc, x, e.g, kp.c_blend);
+          mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
         }
       } else {
         const Coef<T>& cf = sl.coef[g];
@@ -614,7 +519,9 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
       SdfT<T> sc;
       V3T<T> pe, xbI, xbII;
       const Coef<T>& cf = sl.coef[g];
+      const int steps = 2 * ((kK > 0 ? kK : kp.trace_iters) - 1);
       if (kPass == 1) {
+        if (kCount) { cnt.g1 += s.y; cnt.v1 += (unsigned long long)steps * s.y; }
         const V3T<T> z = v3(T(0.f), T(0.f), T(0.f));
         edge_t<T, false, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
                          sl.phi[t1v], z, z, cf, kp, sc, pe, xbI, xbII);
@@ -622,7 +529,9 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
         transition_t(sc.phi, kp, w, wp);
         const T dc = fma_t(w, sc.phi - kp.d_max, T(kp.d_max));
         part_from_contact(c, w, dc, pe, sc.g, kp.c_blend);
+        mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
       } else if (cf.live) {
+        if (kCount) { cnt.h2 += s.y; cnt.g2 += (unsigned long long)steps * s.y; }
         edge_t<T, true, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
                         sl.phi[t1v], sl.grad[t0v], sl.grad[t1v], cf, kp, sc, pe, xbI, xbII);
         ac.X1 = v3(ac.X1.x + xbI.x + xbII.x, ac.X1.y + xbI.y + xbII.y, ac.X1.z + xbI.z + xbII.z);
@@ -636,9 +545,9 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, cons
   __syncwarp();
 }
 
-template <class T, int kPass, int kK>
-__device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& us,
-                                const KParams& kp, int lane, Accum<T>& ac) {
+template <class T, int kPass, int kK, bool kCount>
+__device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, int sc0, const UnitShape& us,
+                                const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt) {
   int start = 0;
   while (start < np) {
     const int r = start + lane;
@@ -664,16 +573,17 @@ __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, const UnitShape& 
     }
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
-    bwd_run_list<T, kPass, kK>(sl, nd, TV, TE, kp, lane, ac);
+    if (kCount && lane == 0) cnt.live += nd;
+    bwd_run_list<T, kPass, kK, kCount>(sl, nd, TV, TE, sc0, kp, lane, ac, cnt);
     start += nd;
   }
 }
 
 // all live directions of the staged F chunk against S, chunk by chunk
-template <class T, int kPass, int kK>
+template <class T, int kPass, int kK, bool kCount>
 __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec& S, int nfc,
-                          float margin, const UnitShape& us, const KParams& kp, int lane,
-                          Accum<T>& ac) {
+                          float margin, bool by_hits, const UnitShape& us, const KParams& kp,
+                          int lane, Accum<T>& ac, BwdCounts& cnt) {
   for (int sc0 = 0; sc0 < S.np;) {
     int sc1 = sc0, P = 0;
     while (sc1 < S.np && sc1 - sc0 < us.spiece_budget) {
@@ -700,23 +610,30 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
       int code = 0;
       if (d < ndir) {
         const int fcd = d / nsc, scd = d - fcd * nsc;
-        const float4 c = sl.fs[fcd];
-        const int2 s = sl.sp[scd];
-        const float mc = max_plane(sl.planes + s.x, s.y, c.x, c.y, c.z);
-        live = mc - c.w - margin < kp.d_max;
+        const int sg = sc0 + scd;
+        if (by_hits && sg < kHitS) {
+          live = (sl.hit[fcd * kHitWords + (sg >> 5)] >> (sg & 31)) & 1u;
+        } else {
+          const float4 c = sl.fs[fcd];
+          const int2 s = sl.sp[scd];
+          const float mc = max_plane(sl.planes + s.x, s.y, c.x, c.y, c.z);
+          live = mc - c.w - margin < kp.d_max;
+          if (kCount) cnt.gate += s.y;
+        }
+        if (kCount) cnt.dirs += 1;
         code = (fcd << 16) | scd;
       }
       const unsigned bal = __ballot_sync(kFull, live);
       const int nl = __popc(bal);
       if (np + nl > kPending) {
-        bwd_run_pending<T, kPass, kK>(sl, np, us, kp, lane, ac);
+        bwd_run_pending<T, kPass, kK, kCount>(sl, np, sc0, us, kp, lane, ac, cnt);
         np = 0;
       }
       if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
       np += nl;
       __syncwarp();
     }
-    if (np > 0) bwd_run_pending<T, kPass, kK>(sl, np, us, kp, lane, ac);
+    if (np > 0) bwd_run_pending<T, kPass, kK, kCount>(sl, np, sc0, us, kp, lane, ac, cnt);
     sc0 = sc1;
   }
 }
@@ -767,16 +684,19 @@ __device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <class T, int kK>
+template <class T, int kK, bool kCount>
 __global__ void __launch_bounds__(32, 1)
 bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 const WorkItem* __restrict__ items, const int32_t* __restrict__ order,
                 int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b,
-                const float* __restrict__ ybar, const float* __restrict__ dir, KParams kp,
-                UnitShape us, float* __restrict__ part, float* __restrict__ jvp) {
+                const float* __restrict__ ybar, const float* __restrict__ dir,
+                const float* __restrict__ saved, KParams kp, UnitShape us,
+                float* __restrict__ part, float* __restrict__ jvp,
+                unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
+  BwdCounts cnt;
   const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
   const int64_t n_run = dev_items ? *dev_items : n_items;
   for (int64_t k = blockIdx.x; k < n_run; k += gridDim.x) {
@@ -836,6 +756,13 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         PartT<T> z;
         part_zero(z);
         sl.acc[lane] = z;
+        if (saved) {   // the forward's hits: pass 1 visits only those directions
+          const uint32_t* h =
+              reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * (row0 + fc0 + lane) + 18);
+          for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = h[q];
+        } else {
+          for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
+        }
       }
       for (int i = lane; i < V; i += 32) {
         const float4 v = g.verts[pfirst.v0 + i];
@@ -846,7 +773,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
       for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
       __syncwarp();
 
-      bwd_sweep<T, 1, kK>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      bwd_sweep<T, 1, kK, kCount>(g, sl, S, nfc, margin, saved != nullptr, us, kp, lane, ac, cnt);
       __syncwarp();
 
       // group outputs, adjoint coefficients and output-transform terms
@@ -905,7 +832,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         sl.coef[lane] = cf;
       }
       __syncwarp();
-      bwd_sweep<T, 2, kK>(g, sl, S, nfc, margin, us, kp, lane, ac);
+      bwd_sweep<T, 2, kK, kCount>(g, sl, S, nfc, margin, true, us, kp, lane, ac, cnt);
       fc0 = fc1;
     }
 
@@ -951,6 +878,17 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
     }
     __syncwarp();
   }
+  if (kCount) {
+    const unsigned long long v[8] = {cnt.dirs, cnt.live, cnt.maxp, cnt.gate,
+                                     cnt.g1, cnt.v1, cnt.h2, cnt.g2};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      unsigned long long x = v[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0) atomicAdd(counters + q, x);
+    }
+  }
 }
 
 // grad / hvp of pair i = the two units' slots, side 0 then side 1
@@ -979,9 +917,14 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part,
 template <class T, int kK>
 static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
-  bwd_unit_kernel<T, kK><<<L.grid, 32, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b,
-                                                       L.ybar, L.dir, L.kp, L.us, L.part,
-                                                       L.jvp);
+  if (L.counters)
+    bwd_unit_kernel<T, kK, true><<<L.grid, 32, smem, stream>>>(
+        L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b, L.ybar, L.dir,
+        L.saved, L.kp, L.us, L.part, L.jvp, L.counters);
+  else
+    bwd_unit_kernel<T, kK, false><<<L.grid, 32, smem, stream>>>(
+        L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b, L.ybar, L.dir,
+        L.saved, L.kp, L.us, L.part, L.jvp, nullptr);
 }
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
@@ -1009,10 +952,14 @@ template <class T, int kK>
 static cudaError_t configure_unit(int bytes, int smem_limit, int* per_sm) {
   cudaError_t e = cudaSuccess;
   if (bytes > 48 * 1024)
-    e = cudaFuncSetAttribute(bwd_unit_kernel<T, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_limit);
+    e = cudaFuncSetAttribute(bwd_unit_kernel<T, kK, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  if (e == cudaSuccess && bytes > 48 * 1024)
+    e = cudaFuncSetAttribute(bwd_unit_kernel<T, kK, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bwd_unit_kernel<T, kK>, 32, bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bwd_unit_kernel<T, kK, false>, 32,
+                                                       bytes);
 }
 
 cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_f, int* per_sm_d) {

@@ -33,12 +33,14 @@ struct BwdLaunch {
   const float* pose_b;
   const float* ybar;    // [G, 8]
   const float* dir;     // [n, 12] or NULL
+  const float* saved;   // [G, kSavedFloats] from the forward with these poses, or NULL
   KParams kp;
   UnitShape us;
   float* part;          // [n_items, 24] per-item slots (workspace)
   float* grad;          // [n, 12]
   float* hvp;           // [n, 12] or NULL
   float* jvp;           // [G, 8] or NULL
+  unsigned long long* counters;   // optional work counters (CCM_BWD_CNT_*)
   int grid;
 };
 

@@ -183,41 +183,39 @@ __device__ __forceinline__ float max_plane(const float4* __restrict__ pl, int nf
   return mx;
 }
 
-// ---------------------------------------------------------------------------
-// Sec. 4.4 blend accumulator of one lane: running maximum logit M (log2
-// units) and the sums U, D, A, P, N of u = f 2^{l - M} times 1, d_c, f, p_c, n_c.
-// ---------------------------------------------------------------------------
-struct BlendAcc {
-  float M, U, D, A, px, py, pz, nx, ny, nz;
-  __device__ __forceinline__ void init() {
-    M = -INFINITY; U = D = A = px = py = pz = nx = ny = nz = 0.f;
+// largest plane value at x and the index of a plane attaining it
+__device__ __forceinline__ float max_plane_arg(const float4* __restrict__ pl, int nf, float x,
+                                               float y, float z, int& arg) {
+  float mx = -INFINITY;
+  int am = 0;
+#pragma unroll 4
+  for (int k = 0; k < nf; ++k) {
+    const float4 p = pl[k];
+    const float v = fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w)));
+    if (v > mx) { mx = v; am = k; }
   }
-  __device__ __forceinline__ void add(float f, float dc, float qx, float qy, float qz, float mx_,
-                                      float my_, float mz_, float c_blend) {
-    if (!(f > 0.f)) return;
-    const float l = -dc * c_blend;
-    if (l > M) {
-      const float r = ex2(M - l);   // 0 when M = -inf
-      U *= r; D *= r; A *= r; px *= r; py *= r; pz *= r; nx *= r; ny *= r; nz *= r;
-      M = l;
-    }
-    const float u = f * ex2(l - M);
-    U += u;
-    D = fmaf(u, dc, D);
-    A = fmaf(u, f, A);
-    px = fmaf(u, qx, px); py = fmaf(u, qy, py); pz = fmaf(u, qz, pz);
-    nx = fmaf(u, mx_, nx); ny = fmaf(u, my_, ny); nz = fmaf(u, mz_, nz);
+  arg = am;
+  return mx;
+}
+
+// Lower bound of the max-plane value over the edge x(t) = xI + t (xII - xI),
+// t in [0, 1], from the planes a and b that attain it at the two corners
+// (values mI and mII): max_k phi_k(x(t)) >= max(phi_a(x(t)), phi_b(x(t))),
+// two linear functions whose maximum is convex in t, so its minimum is at a
+// corner or where they cross.  Every unit-normal plane changes by at most the
+// edge length L along it, so the bound is never below (mI + mII - L) / 2.
+__device__ __forceinline__ float edge_plane_bound(float4 pa, float4 pb, float dx, float dy,
+                                                  float dz, float mI, float mII) {
+  const float A0 = mI, A1 = fmaf(pa.x, dx, fmaf(pa.y, dy, fmaf(pa.z, dz, mI)));
+  const float B1 = mII, B0 = mII - fmaf(pb.x, dx, fmaf(pb.y, dy, pb.z * dz));
+  float lb = fminf(fmaxf(A0, B0), fmaxf(A1, B1));
+  const float g0 = A0 - B0, g1 = A1 - B1;
+  if ((g0 < 0.f) != (g1 < 0.f)) {   // the lines cross inside the edge
+    const float t = g0 / (g0 - g1);
+    lb = fminf(lb, fmaf(t, A1 - A0, A0));
   }
-  // merge across the warp (fixed butterfly order: deterministic)
-  __device__ __forceinline__ void warp_merge() {
-    const float Mw = warp_max(M);
-    const float r = (Mw == -INFINITY) ? 0.f : ex2(M - Mw);
-    U = warp_sum(U * r); D = warp_sum(D * r); A = warp_sum(A * r);
-    px = warp_sum(px * r); py = warp_sum(py * r); pz = warp_sum(pz * r);
-    nx = warp_sum(nx * r); ny = warp_sum(ny * r); nz = warp_sum(nz * r);
-    M = Mw;
-  }
-};
+  return lb;
+}
 
 __device__ __forceinline__ void write_empty(float* out, const KParams& kp) {
   out[0] = kp.d_max;

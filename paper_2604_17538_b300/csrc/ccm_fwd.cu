@@ -9,8 +9,8 @@
 //   * piece pair: max_k phi_k(c_f) - r_f >= d_max proves phi_s >= d_max on
 //     all of f (phi >= max-plane and both are 1-Lipschitz);
 //   * vertex: max-plane value m >= d_max;
-//   * edge: (m_I + m_II - L) / 2 >= d_max, a lower bound of the max-plane
-//     value along the edge.
+//   * edge: a lower bound of the max-plane value along the edge >= d_max,
+//     from the planes attaining it at the two corners (edge_plane_bound).
 // A pair's outputs depend only on that pair: bit-identical in any batch.
 #include "ccm_narrow.cuh"
 #include "ccm_unit.cuh"
@@ -54,7 +54,7 @@ struct FwdCounts {
 // Narrow phase of the live directions sl.dsub[0..nd) whose vertex / edge items
 // are numbered by the exclusive prefixes sl.pv / sl.pe (totals TV, TE).
 template <bool kCount>
-__device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE,
+__device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE, int sc0,
                          const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
   // exact max-plane value of every (direction, vertex) item
   for (int t = lane; t < TV; t += 32) {
@@ -63,13 +63,15 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
     const int4 f = sl.fp[code >> 16];
     const int2 s = sl.sp[code & 0xffff];
     const float4 x = sl.xs[f.x + t - sl.pv[r]];
-    sl.m[t] = max_plane(sl.planes + s.x, s.y, x.x, x.y, x.z);
+    int arg;
+    sl.m[t] = max_plane_arg(sl.planes + s.x, s.y, x.x, x.y, x.z, arg);
+    sl.am[t] = (uint16_t)arg;
     sl.need[t] = 0;
     if (kCount) cnt.maxp += s.y;
   }
   __syncwarp();
-  // edge cull: every point of an edge is at distance a from v_I and L - a
-  // from v_II, so its max-plane value is >= (m_I + m_II - L) / 2
+  // edge cull: the max-plane value along the edge is bounded below by the
+  // two planes that attain it at the corners (edge_plane_bound)
   int n_e = 0;
   for (int t0 = 0; t0 < TE; t0 += 32) {
     const int t = t0 + lane;
@@ -78,13 +80,14 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       const int r = find_dir(sl.pe, nd, t);
       const int code = dsub[r];
       const int4 f = sl.fp[code >> 16];
+      const int2 s = sl.sp[code & 0xffff];
       const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
       const int i0 = e & 0xffff, i1 = e >> 16;
       const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
       const float4 a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
-      const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-      const float L = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-      live = no_cull || 0.5f * (sl.m[t0v] + sl.m[t1v] - L) < kp.d_max;
+      const float lb = edge_plane_bound(sl.planes[s.x + sl.am[t0v]], sl.planes[s.x + sl.am[t1v]],
+                                        b.x - a.x, b.y - a.y, b.z - a.z, sl.m[t0v], sl.m[t1v]);
+      live = no_cull || lb - kEdgeTol < kp.d_max;
       if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
     }
     const unsigned bal = __ballot_sync(kFull, live);
@@ -104,8 +107,8 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
   // V-SDF contacts (and the SDF at vertices that start a sphere trace)
   for (int k0 = 0; k0 < n_v; k0 += 32) {
     const int k = k0 + lane;
-    LaneContact c;
-    contact_to_partial(c, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kp.c_blend);
+    PartT<float> c;
+    part_zero(c);
     int key = 0xffff;
     if (k < n_v) {
       const int t = sl.vlist[k];
@@ -121,19 +124,20 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       if (no_cull || m < kp.d_max) {
         const float w = transition(g.phi, kp);
         const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
-        contact_to_partial(c, w, dc, x.x, x.y, x.z, g.gx, g.gy, g.gz, kp.c_blend);
+        part_from_contact(c, w, dc, v3(x.x, x.y, x.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
+        mark_hit(sl.hit, code >> 16, sc0 + (code & 0xffff), w);
         if (kCount) cnt.con += w > 0.f;
       }
       if (kCount) cnt.eg += s.y;
     }
-    fold_contacts(c, key, sl.acc, lane);
+    fold_t(c, key, sl.acc, lane);
   }
   __syncwarp();
   // E-SDF contacts: sphere trace from both corners, soft clip, midpoint
   for (int k0 = 0; k0 < n_e; k0 += 32) {
     const int k = k0 + lane;
-    LaneContact c;
-    contact_to_partial(c, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kp.c_blend);
+    PartT<float> c;
+    part_zero(c);
     int key = 0xffff;
     if (k < n_e) {
       const int t = sl.elist[k];
@@ -148,7 +152,8 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
                                           sl.m[t0v], sl.m[t1v], sl.phi[t0v], sl.phi[t1v], kp);
       const float w = transition(ec.phi, kp);
       const float dc = fmaf(w, ec.phi - kp.d_max, kp.d_max);
-      contact_to_partial(c, w, dc, ec.px, ec.py, ec.pz, ec.gx, ec.gy, ec.gz, kp.c_blend);
+      part_from_contact(c, w, dc, v3(ec.px, ec.py, ec.pz), v3(ec.gx, ec.gy, ec.gz), kp.c_blend);
+      mark_hit(sl.hit, code >> 16, sc0 + (code & 0xffff), w);
       key = code >> 16;
       if (kCount) {
         cnt.con += w > 0.f;
@@ -156,7 +161,7 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
         cnt.ev += (unsigned long long)s.y * 2 * (kp.trace_iters > 0 ? kp.trace_iters - 1 : 0);
       }
     }
-    fold_contacts(c, key, sl.acc, lane);
+    fold_t(c, key, sl.acc, lane);
   }
   __syncwarp();
 }
@@ -164,7 +169,7 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
 // Splits the pending directions sl.dir[0..np) into lists that fit the item
 // budgets and runs each.
 template <bool kCount>
-__device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitShape& us,
+__device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, const UnitShape& us,
                            const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
   int start = 0;
   while (start < np) {
@@ -192,7 +197,7 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, const UnitSh
     }
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
-    run_list<kCount>(sl, dsub, nd, TV, TE, kp, no_cull, lane, cnt);
+    run_list<kCount>(sl, dsub, nd, TV, TE, sc0, kp, no_cull, lane, cnt);
     start += nd;
   }
 }
@@ -203,7 +208,8 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 const WorkItem* __restrict__ items, const int32_t* __restrict__ order,
                 int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
-                UnitShape us, float* __restrict__ y, unsigned long long* __restrict__ counters) {
+                UnitShape us, float* __restrict__ y, float* __restrict__ saved,
+                unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -250,10 +256,8 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         sl.fp[lane] = make_int4(p.v0 - pfirst.v0, p.nv, p.e0 - pfirst.e0, p.ne);
         const float3 c = xform(Rr, tr, p.sphere);
         sl.fs[lane] = make_float4(c.x, c.y, c.z, p.sphere.w);
-        float* a = sl.acc + 10 * lane;
-        a[0] = -INFINITY;
-#pragma unroll
-        for (int q = 1; q < 10; ++q) a[q] = 0.f;
+        part_zero(sl.acc[lane]);
+        for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
       }
       for (int i = lane; i < V; i += 32) {
         const float3 x = xform(Rr, tr, g.verts[pfirst.v0 + i]);
@@ -300,25 +304,25 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           const unsigned bal = __ballot_sync(kFull, live);
           const int nl = __popc(bal);
           if (np + nl > kPending) {
-            run_pending<kCount>(sl, dsub, np, us, kp, no_cull, lane, cnt);
+            run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt);
             np = 0;
           }
           if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
           np += nl;
           __syncwarp();
         }
-        if (np > 0) run_pending<kCount>(sl, dsub, np, us, kp, no_cull, lane, cnt);
+        if (np > 0) run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt);
         sc0 = sc1;
       }
       __syncwarp();
       if (lane < nfc) {
-        const float* a = sl.acc + 10 * lane;
-        BlendAcc acc;
-        acc.M = a[0]; acc.U = a[1]; acc.D = a[2]; acc.A = a[3];
-        acc.px = a[4]; acc.py = a[5]; acc.pz = a[6]; acc.nx = a[7]; acc.ny = a[8]; acc.nz = a[9];
+        const PartT<float> acc = sl.acc[lane];
         float RS[9], tS[3];
         load_pose(pS, RS, tS);
         write_group(y + 8 * (row0 + fc0 + lane), acc, RS, tS, kp);
+        if (saved)
+          save_group(saved + (int64_t)kSavedFloats * (row0 + fc0 + lane), acc,
+                     sl.hit + lane * kHitWords);
       }
       fc0 = fc1;
     }
@@ -342,10 +346,10 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   const int threads = 32 * L.us.warps;
   if (L.counters)
     unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.counters);
+                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters);
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.counters);
+                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ struct FwdLaunch {
   KParams kp;
   UnitShape us;
   float* y;
+  float* saved;                   // optional [G, kSavedFloats] for the reverse pass
   unsigned long long* counters;   // optional work counters (CCM_CNT_*)
   int grid;
 };

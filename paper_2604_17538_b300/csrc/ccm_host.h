@@ -91,9 +91,10 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
 void default_tuning(ccm_tuning* t);
 ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t);
 ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
-                       float* y, unsigned long long* counters, cudaStream_t stream);
+                       float* y, float* saved, unsigned long long* counters, cudaStream_t stream);
 ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
-                        const float* ybar, const float* dir, float* grad, float* hvp, float* jvp,
+                        const float* saved, const float* ybar, const float* dir, float* grad,
+                        float* hvp, float* jvp, unsigned long long* counters,
                         cudaStream_t stream);
 
 }  // namespace ccm

@@ -1,7 +1,7 @@
 // Narrow-phase pieces shared by the kernels: the E-SDF contact of one edge
 // (Sec. 4.2) and the normalised, world-frame output of a blend (Sec. 4.4).
 #pragma once
-#include "ccm_device.cuh"
+#include "ccm_blend.cuh"
 
 namespace ccm {
 
@@ -51,20 +51,24 @@ __device__ inline EdgeContact edge_contact(const float4* __restrict__ pl, int nf
   return c;
 }
 
-// Normalised blend of a merged accumulator, rotated into world frame.
-__device__ inline void write_group(float* out, const BlendAcc& acc, const float* RS,
+// Normalised blend of a group's partial (Sec. 4.4), rotated into world frame:
+// d = rd + Dd / U, a = rf + Da / U, q = rp + Dp / U, n = R_S nu / |R_S nu| with
+// nu = rn + Dn / U; an empty group is (d_max, 0, 0, 0).
+__device__ inline void write_group(float* out, const PartT<float>& acc, const float* RS,
                                    const float* tS, const KParams& kp) {
   if (acc.U > 0.f) {
-    const float iU = 1.0f / acc.U;
-    const float qx = acc.px * iU, qy = acc.py * iU, qz = acc.pz * iU;
-    const float mx = acc.nx * iU, my = acc.ny * iU, mz = acc.nz * iU;
+    const float iU = __frcp_rn(acc.U);
+    const float qx = fmaf(acc.Dp.x, iU, acc.rp.x), qy = fmaf(acc.Dp.y, iU, acc.rp.y),
+                qz = fmaf(acc.Dp.z, iU, acc.rp.z);
+    const float mx = fmaf(acc.Dn.x, iU, acc.rn.x), my = fmaf(acc.Dn.y, iU, acc.rn.y),
+                mz = fmaf(acc.Dn.z, iU, acc.rn.z);
     const float wx = RS[0] * mx + RS[1] * my + RS[2] * mz;
     const float wy = RS[3] * mx + RS[4] * my + RS[5] * mz;
     const float wz = RS[6] * mx + RS[7] * my + RS[8] * mz;
     const float nn = sqrtf(wx * wx + wy * wy + wz * wz);
     const float in = nn > 0.f ? 1.0f / nn : 0.f;
-    out[0] = acc.D * iU;
-    out[1] = acc.A * iU;
+    out[0] = fmaf(acc.Dd, iU, acc.rd);
+    out[1] = fmaf(acc.Da, iU, acc.rf);
     out[2] = RS[0] * qx + RS[1] * qy + RS[2] * qz + tS[0];
     out[3] = RS[3] * qx + RS[4] * qy + RS[5] * qz + tS[1];
     out[4] = RS[6] * qx + RS[7] * qy + RS[8] * qz + tS[2];

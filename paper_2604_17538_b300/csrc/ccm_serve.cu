@@ -78,7 +78,7 @@ struct WaveSet {
   cudaGraphExec_t graph_f = nullptr;    // gather, forward, scatter
   cudaGraphExec_t graph_fb = nullptr;   // gather, forward, reverse pass, scatter
   DevBuf d_pairs, d_items, d_order_f, d_order_b, d_item_off, d_reqs, d_counts, d_pose_a,
-      d_pose_b, d_y, d_ybar, d_part, d_grad;
+      d_pose_b, d_y, d_ybar, d_part, d_grad, d_saved;
   PairRec* h_pairs = nullptr;
   WorkItem* h_items = nullptr;
   int32_t* h_order_f = nullptr;
@@ -196,7 +196,7 @@ static ccm_status alloc_buf(DevBuf& b, int64_t count, const char* what) {
 // outputs and cotangents.
 constexpr int64_t kBytesPerPair = (int64_t)sizeof(PairRec) + 8 + 2 * 12 * 4 + 12 * 4;
 constexpr int64_t kBytesPerItem = (int64_t)sizeof(WorkItem) + 2 * 4 + 24 * 4;
-constexpr int64_t kBytesPerGroup = 2 * 8 * 4;
+constexpr int64_t kBytesPerGroup = 2 * 8 * 4 + CCM_SAVED_FLOATS * 4;
 
 static int64_t set_bytes(int64_t P, int64_t G, int64_t R, int64_t I) {
   return P * kBytesPerPair + 8 + I * kBytesPerItem + G * kBytesPerGroup +
@@ -221,6 +221,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   F.kp = sv->kp;
   F.us = sv->us;
   F.y = static_cast<float*>(s.d_y.ptr);
+  F.saved = reverse ? static_cast<float*>(s.d_saved.ptr) : nullptr;
   F.counters = nullptr;
   F.grid = sv->fwd_grid;
   launch_forward(F, s.stream);
@@ -238,12 +239,14 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   B.pose_b = F.pose_b;
   B.ybar = static_cast<const float*>(s.d_ybar.ptr);
   B.dir = nullptr;
+  B.saved = static_cast<const float*>(s.d_saved.ptr);
   B.kp = sv->kp;
   B.us = sv->us;
   B.part = static_cast<float*>(s.d_part.ptr);
   B.grad = static_cast<float*>(s.d_grad.ptr);
   B.hvp = nullptr;
   B.jvp = nullptr;
+  B.counters = nullptr;
   B.grid = sv->bwd_grid;
   if (reverse) launch_backward(B, s.stream);
   serve_scatter<<<sv->ctx->n_sm * 4, 256, 0, s.stream>>>(
@@ -264,6 +267,7 @@ static ccm_status setup_set(Serving* sv, WaveSet& s) {
   if ((st = alloc_buf<float>(s.d_pose_b, 12 * P, "wave poses")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_y, 8 * G, "wave outputs")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_ybar, 8 * G, "wave cotangents")) != CCM_OK) return st;
+  if ((st = alloc_buf<float>(s.d_saved, CCM_SAVED_FLOATS * G, "wave records")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_part, 24 * I, "wave slots")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_grad, 12 * P, "wave gradients")) != CCM_OK) return st;
   if (cudaMallocHost(&s.h_pairs, sizeof(PairRec) * P) != cudaSuccess ||
@@ -301,7 +305,7 @@ static void release_set(WaveSet& s) {
   if (s.stream) cudaStreamDestroy(s.stream);
   for (DevBuf* b : {&s.d_pairs, &s.d_items, &s.d_order_f, &s.d_order_b, &s.d_item_off,
                     &s.d_reqs, &s.d_counts, &s.d_pose_a, &s.d_pose_b, &s.d_y, &s.d_ybar,
-                    &s.d_part, &s.d_grad})
+                    &s.d_part, &s.d_grad, &s.d_saved})
     b->release();
   for (void* p : {(void*)s.h_pairs, (void*)s.h_items, (void*)s.h_order_f, (void*)s.h_order_b,
                   (void*)s.h_item_off, (void*)s.h_reqs, (void*)s.h_counts})

@@ -15,7 +15,7 @@
 //     accumulators kept in shared memory -- one head lane per group, in a
 //     fixed order, so the result is deterministic.
 #pragma once
-#include "ccm_device.cuh"
+#include "ccm_blend.cuh"
 
 namespace ccm {
 
@@ -44,7 +44,8 @@ struct UnitSlice {
   uint32_t* edges;    // [edge_budget]
   int4* fp;           // [groups] (first vertex, nv, first edge, ne) per F piece
   float4* fs;         // [groups] bounding sphere (S frame) per F piece
-  float* acc;         // [groups * 10] group accumulators (M, U, D, A, P, N)
+  PartT<float>* acc;  // [groups] group blend partials (ccm_blend.cuh)
+  uint32_t* hit;      // [groups * kHitWords] directions that gave a contact
   int* dir;           // [32] pending live directions: fc << 16 | sc
   int* dsub;          // [32] directions of the list being run
   int* pv;            // [33] prefix of vertex items per pending direction
@@ -54,7 +55,12 @@ struct UnitSlice {
   uint16_t* vlist;    // [item_v] surviving vertex items
   uint16_t* elist;    // [item_e] surviving edge items
   uint8_t* need;      // [item_v]
+  uint16_t* am;       // [item_v] a plane attaining the max-plane value
 };
+
+// Rounding allowance of the edge cull's plane bound (coordinates are O(1) in
+// the SDF frame, so float rounding of the bound is ~1e-7).
+constexpr float kEdgeTol = 1e-5f;
 
 __host__ __device__ inline int align16i(int b) { return (b + 15) & ~15; }
 
@@ -66,13 +72,15 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += align16i(4 * u.edge_budget);
   b += 16 * u.groups;                        // fp
   b += 16 * u.groups;                        // fs
-  b += align16i(4 * 10 * u.groups);          // acc
+  b += align16i((int)sizeof(PartT<float>) * u.groups);   // acc
+  b += align16i(4 * kHitWords * u.groups);   // hit
   b += align16i(4 * kPending) * 2;           // dir, dsub
   b += align16i(4 * (kPending + 1)) * 2;     // pv, pe
   b += align16i(4 * u.item_v) * 2;           // m, phi
   b += align16i(2 * u.item_v);               // vlist
   b += align16i(2 * u.item_e);               // elist
   b += align16i(u.item_v);                   // need
+  b += align16i(2 * u.item_v);               // am
   return b;
 }
 
@@ -84,7 +92,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.edges = reinterpret_cast<uint32_t*>(p);          p += align16i(4 * u.edge_budget);
   s.fp = reinterpret_cast<int4*>(p);                 p += 16 * u.groups;
   s.fs = reinterpret_cast<float4*>(p);               p += 16 * u.groups;
-  s.acc = reinterpret_cast<float*>(p);               p += align16i(4 * 10 * u.groups);
+  s.acc = reinterpret_cast<PartT<float>*>(p);        p += align16i((int)sizeof(PartT<float>) * u.groups);
+  s.hit = reinterpret_cast<uint32_t*>(p);            p += align16i(4 * kHitWords * u.groups);
   s.dir = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);                p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));
@@ -93,81 +102,9 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.phi = reinterpret_cast<float*>(p);               p += align16i(4 * u.item_v);
   s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
   s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
-  s.need = reinterpret_cast<uint8_t*>(p);
+  s.need = reinterpret_cast<uint8_t*>(p);          p += align16i(u.item_v);
+  s.am = reinterpret_cast<uint16_t*>(p);
   return s;
-}
-
-// ---------------------------------------------------------------------------
-// one contact in a lane, and the segmented online-softmax fold into groups
-// ---------------------------------------------------------------------------
-struct LaneContact {
-  float M, U, D, A, px, py, pz, nx, ny, nz;   // partial blend of this lane
-};
-
-__device__ __forceinline__ void contact_to_partial(LaneContact& c, float f, float dc, float qx,
-                                                   float qy, float qz, float gx, float gy,
-                                                   float gz, float c_blend) {
-  if (f > 0.f) {
-    c.M = -dc * c_blend;   // logit in log2 units; the lane's only term has weight 2^0
-    c.U = f;
-    c.D = f * dc;
-    c.A = f * f;
-    c.px = f * qx; c.py = f * qy; c.pz = f * qz;
-    c.nx = f * gx; c.ny = f * gy; c.nz = f * gz;
-  } else {
-    c.M = -INFINITY;
-    c.U = c.D = c.A = c.px = c.py = c.pz = c.nx = c.ny = c.nz = 0.f;
-  }
-}
-
-// a <- a (+) b for online-softmax partials
-__device__ __forceinline__ void combine(LaneContact& a, const LaneContact& b) {
-  const float M = fmaxf(a.M, b.M);
-  if (M == -INFINITY) return;
-  const float ra = ex2(a.M - M), rb = ex2(b.M - M);
-  a.U = a.U * ra + b.U * rb;
-  a.D = a.D * ra + b.D * rb;
-  a.A = a.A * ra + b.A * rb;
-  a.px = a.px * ra + b.px * rb; a.py = a.py * ra + b.py * rb; a.pz = a.pz * ra + b.pz * rb;
-  a.nx = a.nx * ra + b.nx * rb; a.ny = a.ny * ra + b.ny * rb; a.nz = a.nz * ra + b.nz * rb;
-  a.M = M;
-}
-
-__device__ __forceinline__ LaneContact shfl_down_contact(const LaneContact& c, int o) {
-  LaneContact r;
-  r.M = __shfl_down_sync(kFull, c.M, o);
-  r.U = __shfl_down_sync(kFull, c.U, o);
-  r.D = __shfl_down_sync(kFull, c.D, o);
-  r.A = __shfl_down_sync(kFull, c.A, o);
-  r.px = __shfl_down_sync(kFull, c.px, o);
-  r.py = __shfl_down_sync(kFull, c.py, o);
-  r.pz = __shfl_down_sync(kFull, c.pz, o);
-  r.nx = __shfl_down_sync(kFull, c.nx, o);
-  r.ny = __shfl_down_sync(kFull, c.ny, o);
-  r.nz = __shfl_down_sync(kFull, c.nz, o);
-  return r;
-}
-
-// Lanes hold contacts sorted by `key` (group in the F chunk; 0xffff for an
-// idle lane, always after the others).  The first lane of each key's run
-// folds the run's total into that group's accumulator.
-__device__ inline void fold_contacts(LaneContact c, int key, float* acc, int lane) {
-  const unsigned seg = __match_any_sync(kFull, key);
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const LaneContact b = shfl_down_contact(c, o);
-    if (lane + o < 32 && ((seg >> (lane + o)) & 1u)) combine(c, b);
-  }
-  const bool head = (__ffs(seg) - 1) == lane;
-  if (head && key != 0xffff && c.M != -INFINITY) {
-    float* a = acc + 10 * key;
-    LaneContact g;
-    g.M = a[0]; g.U = a[1]; g.D = a[2]; g.A = a[3];
-    g.px = a[4]; g.py = a[5]; g.pz = a[6]; g.nx = a[7]; g.ny = a[8]; g.nz = a[9];
-    combine(g, c);
-    a[0] = g.M; a[1] = g.U; a[2] = g.D; a[3] = g.A;
-    a[4] = g.px; a[5] = g.py; a[6] = g.pz; a[7] = g.nx; a[8] = g.ny; a[9] = g.nz;
-  }
 }
 
 // largest r in [0, n) with pre[r] <= t (pre is an exclusive prefix, pre[0] = 0)

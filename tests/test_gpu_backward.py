@@ -81,6 +81,46 @@ def test_gradient_hvp_jvp_match_oracle(oracle_lib, ctx, cases, name):
     assert np.all(jmax <= GRAD_RTOL * jsc + 1e-6), (jmax / (jsc + 1e-30)).max()
     print(f"{name}: max rel err grad {rg:.2e} hvp {rh:.2e}")
     assert np.abs(go).max() > 0 and np.abs(hvo).max() > 0
+    # the same through the forward's saved record (ccm_contacts_save +
+    # ccm_contacts_backward_saved): the passes visit only the directions the
+    # forward found contacts in, against the same bars
+    saved = batch.saved_buffer()
+    y = batch.contacts(pa, pb, saved=saved)
+    gs, _, _ = batch.backward(pa, pb, yb, saved=saved)
+    gs2, hvs, jvs = batch.backward(pa, pb, yb, ut, want_jvp=True, saved=saved)
+    torch.cuda.synchronize()
+    _per_pair_check(gs.double().cpu().numpy(), go, f"{name} gradient (saved)", tol_g)
+    _per_pair_check(gs2.double().cpu().numpy(), go, f"{name} gradient (dual, saved)", tol_g)
+    _per_pair_check(hvs.double().cpu().numpy(), hvo, f"{name} H u (saved)", tol_h)
+    jvs = jvs.double().cpu().numpy()
+    jmax = np.array([np.abs(jvs[off[i]:off[i + 1]] - jvo[off[i]:off[i + 1]]).max()
+                     for i in range(sc.n_pairs)])
+    assert np.all(jmax <= GRAD_RTOL * jsc + 1e-6), (jmax / (jsc + 1e-30)).max()
+    # record layout: U > 0 exactly for groups with a contact (a > 0), and such
+    # a group has at least one hit bit (every SDF body here has < 256 pieces)
+    rec = saved.cpu().numpy()
+    yh = y.cpu().numpy()
+    assert np.array_equal(rec[:, 1] > 0, yh[:, 1] > 0)
+    hits = rec[:, 18:].copy().view(np.uint32)
+    assert np.all((hits != 0).any(1) == (yh[:, 1] > 0))
+    # counted reverse passes give the same results, and the saved record
+    # restricts them to fewer directions than a full re-gating
+    for direction in (None, ut):
+        c_full = torch.zeros(8, dtype=torch.int64, device="cuda")
+        c_saved = torch.zeros(8, dtype=torch.int64, device="cuda")
+        r_full = batch.backward(pa, pb, yb, direction, want_jvp=direction is not None,
+                                counters=c_full)
+        r_saved = batch.backward(pa, pb, yb, direction, want_jvp=direction is not None,
+                                 saved=saved, counters=c_saved)
+        torch.cuda.synchronize()
+        ref_full = g if direction is None else hv
+        ref_saved = gs if direction is None else hvs
+        got_full = r_full[0] if direction is None else r_full[1]
+        got_saved = r_saved[0] if direction is None else r_saved[1]
+        assert torch.equal(got_full, ref_full) and torch.equal(got_saved, ref_saved)
+        cf, cs = c_full.cpu().numpy(), c_saved.cpu().numpy()
+        assert cf[3] > 0 and cs[3] == 0        # no piece-pair gate with the record
+        assert 0 < cs[1] <= cf[1] and 0 < cs[4] <= cf[4] and cs[6] > 0
     batch.close()
 
 
