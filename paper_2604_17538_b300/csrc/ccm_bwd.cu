@@ -186,6 +186,125 @@ __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float 
 }
 
 
+// Two points at once (the two sphere-trace chains of an edge), kMode 0 or 1:
+// one loop over the planes for both, so the two independent dependency
+// chains overlap.  Each point's arithmetic is exactly that of sdf_t /
+// sdf_dual (same operations in the same order), so its results are bitwise
+// those of a single-point call with the same shift.
+template <int kMode>
+__device__ void sdf_dual2(const float4* __restrict__ pl, int nf, V3T<Dual> xa, float sa,
+                          V3T<Dual> xb, float sb, const KParams& kp, SdfT<Dual>& ra,
+                          SdfT<Dual>& rb) {
+  static_assert(kMode <= 1, "two-point evaluation has no Hessian-vector product");
+  const float xav = xa.x.v, yav = xa.y.v, zav = xa.z.v, xad = xa.x.d, yad = xa.y.d, zad = xa.z.d;
+  const float xbv = xb.x.v, ybv = xb.y.v, zbv = xb.z.v, xbd = xb.x.d, ybd = xb.y.d, zbd = xb.z.d;
+  float Sa, Gxa, Gya, Gza, Pda, Sb, Gxb, Gyb, Gzb, Pdb;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
+    Sa = Gxa = Gya = Gza = Pda = 0.f;
+    Sb = Gxb = Gyb = Gzb = Pdb = 0.f;
+    float mxa = -INFINITY, mxb = -INFINITY;
+#pragma unroll 2
+    for (int k = 0; k < nf; ++k) {
+      const float4 p = pl[k];
+      const float pha = fmaf(p.x, xav, fmaf(p.y, yav, fmaf(p.z, zav, p.w)));
+      const float phb = fmaf(p.x, xbv, fmaf(p.y, ybv, fmaf(p.z, zbv, p.w)));
+      mxa = fmaxf(mxa, pha);
+      mxb = fmaxf(mxb, phb);
+      const float ea = ex2(fmaf(pha, kp.c_sdf, -sca));
+      const float eb = ex2(fmaf(phb, kp.c_sdf, -scb));
+      Sa += ea;
+      Sb += eb;
+      Gxa = fmaf(ea, p.x, Gxa); Gya = fmaf(ea, p.y, Gya); Gza = fmaf(ea, p.z, Gza);
+      Gxb = fmaf(eb, p.x, Gxb); Gyb = fmaf(eb, p.y, Gyb); Gzb = fmaf(eb, p.z, Gzb);
+      Pda = fmaf(ea, fmaf(p.x, xad, fmaf(p.y, yad, p.z * zad)), Pda);
+      Pdb = fmaf(eb, fmaf(p.x, xbd, fmaf(p.y, ybd, p.z * zbd)), Pdb);
+    }
+    const bool bada = (mxa - sa) * kp.c_sdf > 64.0f, badb = (mxb - sb) * kp.c_sdf > 64.0f;
+    if (pass == 0 && (bada || badb)) {
+      if (bada) sa = mxa;
+      if (badb) sb = mxb;
+      continue;
+    }
+    break;
+  }
+  const float iSa = __frcp_rn(Sa), iSb = __frcp_rn(Sb);
+  const float it = 1.0f / kp.tau_sdf;
+  ra.phi = Dual(fmaf(kp.ic_sdf, __log2f(Sa), sa), Pda * iSa);
+  rb.phi = Dual(fmaf(kp.ic_sdf, __log2f(Sb), sb), Pdb * iSb);
+  if (kMode == 0) return;
+  const float gxa = Gxa * iSa, gya = Gya * iSa, gza = Gza * iSa;
+  const float gxb = Gxb * iSb, gyb = Gyb * iSb, gzb = Gzb * iSb;
+  const float phda = ra.phi.d, phdb = rb.phi.d;
+  const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
+  float dgxa = 0.f, dgya = 0.f, dgza = 0.f, dgxb = 0.f, dgyb = 0.f, dgzb = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < nf; ++k) {
+    const float4 p = pl[k];
+    const float pha = fmaf(p.x, xav, fmaf(p.y, yav, fmaf(p.z, zav, p.w)));
+    const float phb = fmaf(p.x, xbv, fmaf(p.y, ybv, fmaf(p.z, zbv, p.w)));
+    const float wa = ex2(fmaf(pha, kp.c_sdf, -sca)) * iSa;
+    const float wb = ex2(fmaf(phb, kp.c_sdf, -scb)) * iSb;
+    const float dda = fmaf(p.x, xad, fmaf(p.y, yad, p.z * zad)) - phda;
+    const float ddb = fmaf(p.x, xbd, fmaf(p.y, ybd, p.z * zbd)) - phdb;
+    const float wda = wa * dda, wdb = wb * ddb;
+    dgxa = fmaf(wda, p.x - gxa, dgxa);
+    dgya = fmaf(wda, p.y - gya, dgya);
+    dgza = fmaf(wda, p.z - gza, dgza);
+    dgxb = fmaf(wdb, p.x - gxb, dgxb);
+    dgyb = fmaf(wdb, p.y - gyb, dgyb);
+    dgzb = fmaf(wdb, p.z - gzb, dgzb);
+  }
+  ra.g = v3(Dual(gxa, dgxa * it), Dual(gya, dgya * it), Dual(gza, dgza * it));
+  rb.g = v3(Dual(gxb, dgxb * it), Dual(gyb, dgyb * it), Dual(gzb, dgzb * it));
+}
+
+template <class T, int kMode>
+__device__ void sdf_t2(const float4* __restrict__ pl, int nf, V3T<T> xa, float sa, V3T<T> xb,
+                       float sb, const KParams& kp, SdfT<T>& ra, SdfT<T>& rb) {
+  if constexpr (sizeof(T) == sizeof(Dual)) {
+    sdf_dual2<kMode>(pl, nf, xa, sa, xb, sb, kp, ra, rb);
+  } else {
+    static_assert(kMode <= 1, "two-point evaluation has no Hessian-vector product");
+    constexpr bool kGrad = kMode >= 1;
+    for (int pass = 0; pass < 2; ++pass) {
+      const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
+      T Sa(0.f), gxa(0.f), gya(0.f), gza(0.f), Sb(0.f), gxb(0.f), gyb(0.f), gzb(0.f);
+      float mxa = -INFINITY, mxb = -INFINITY;
+#pragma unroll 2
+      for (int k = 0; k < nf; ++k) {
+        const float4 p = pl[k];
+        const T pha = fma_t(p.x, xa.x, fma_t(p.y, xa.y, fma_t(p.z, xa.z, T(p.w))));
+        const T phb = fma_t(p.x, xb.x, fma_t(p.y, xb.y, fma_t(p.z, xb.z, T(p.w))));
+        mxa = fmaxf(mxa, val(pha));
+        mxb = fmaxf(mxb, val(phb));
+        const T ea = ex2_t(fma_t(pha, kp.c_sdf, T(-sca)));
+        const T eb = ex2_t(fma_t(phb, kp.c_sdf, T(-scb)));
+        Sa += ea;
+        Sb += eb;
+        if (kGrad) {
+          gxa = fma_t(ea, p.x, gxa); gya = fma_t(ea, p.y, gya); gza = fma_t(ea, p.z, gza);
+          gxb = fma_t(eb, p.x, gxb); gyb = fma_t(eb, p.y, gyb); gzb = fma_t(eb, p.z, gzb);
+        }
+      }
+      const bool bada = (mxa - sa) * kp.c_sdf > 64.0f, badb = (mxb - sb) * kp.c_sdf > 64.0f;
+      if (pass == 0 && (bada || badb)) {
+        if (bada) sa = mxa;
+        if (badb) sb = mxb;
+        continue;
+      }
+      ra.phi = fma_t(T(kp.ic_sdf), log2_t(Sa), T(sa));
+      rb.phi = fma_t(T(kp.ic_sdf), log2_t(Sb), T(sb));
+      if (kGrad) {
+        const T ia = rcp_t(Sa), ib = rcp_t(Sb);
+        ra.g = v3(gxa * ia, gya * ia, gza * ia);
+        rb.g = v3(gxb * ib, gyb * ib, gzb * ib);
+      }
+      break;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-group adjoint coefficients and the contact adjoint
 // ---------------------------------------------------------------------------
@@ -339,8 +458,8 @@ __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> 
                          fma_t(a[s + 1], e.z, xI.z));
     const V3T<T> qb = v3(fma_t(b[s + 1], e.x, xI.x), fma_t(b[s + 1], e.y, xI.y),
                          fma_t(b[s + 1], e.z, xI.z));
-    const SdfT<T> ra = sdf_t<T, kAdj ? 1 : 0>(pl, nf, qa, ma - fabsf(val(sa)), qa, kp);
-    const SdfT<T> rb = sdf_t<T, kAdj ? 1 : 0>(pl, nf, qb, mb - fabsf(val(sb)), qb, kp);
+    SdfT<T> ra, rb;
+    sdf_t2<T, kAdj ? 1 : 0>(pl, nf, qa, ma - fabsf(val(sa)), qb, mb - fabsf(val(sb)), kp, ra, rb);
     pa[s + 1] = ra.phi;
     pb[s + 1] = rb.phi;
     if (kAdj) { ga[s + 1] = ra.g; gb[s + 1] = rb.g; }
@@ -594,14 +713,58 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
     }
     const int nsc = sc1 - sc0;
     if (nsc == 0) break;   // unreachable: budgets hold every piece
-    const int f_first = g.pieces[S.p0 + sc0].f0;
     __syncwarp();
-    for (int q = lane; q < nsc; q += 32) {
-      const PieceRec p = g.pieces[S.p0 + sc0 + q];
-      sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
+    if (by_hits && S.np <= kHitS) {
+      // only the pieces some direction of the chunk is marked with are
+      // visited: stage just their planes, packed
+      int base = 0;
+      for (int q0 = 0; q0 < nsc; q0 += 32) {
+        const int q = q0 + lane;
+        int nf = 0, f0 = 0;
+        bool need = false;
+        if (q < nsc) {
+          const int sg = sc0 + q;
+          uint32_t any = 0;
+          for (int f = 0; f < nfc; ++f) any |= sl.hit[f * kHitWords + (sg >> 5)];
+          need = (any >> (sg & 31)) & 1u;
+          if (need) {
+            const PieceRec p = g.pieces[S.p0 + sg];
+            nf = p.nf;
+            f0 = p.f0;
+          }
+        }
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int off = base + incl - nf;
+        if (q < nsc) sl.sp[q] = make_int2(off, nf);
+        unsigned m = __ballot_sync(kFull, need);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const int o_l = __shfl_sync(kFull, off, l), n_l = __shfl_sync(kFull, nf, l),
+                    f_l = __shfl_sync(kFull, f0, l);
+          for (int k = lane; k < n_l; k += 32) sl.planes[o_l + k] = g.planes[f_l + k];
+        }
+        base += __shfl_sync(kFull, incl, 31);
+      }
+      __syncwarp();
+      if (base == 0) {   // no marked direction in this chunk
+        sc0 = sc1;
+        continue;
+      }
+    } else {
+      const int f_first = g.pieces[S.p0 + sc0].f0;
+      for (int q = lane; q < nsc; q += 32) {
+        const PieceRec p = g.pieces[S.p0 + sc0 + q];
+        sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
+      }
+      for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
+      __syncwarp();
     }
-    for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
-    __syncwarp();
     int np = 0;
     const int ndir = nfc * nsc;
     for (int d0 = 0; d0 < ndir; d0 += 32) {
@@ -745,8 +908,9 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
       if (nfc == 0) break;   // unreachable: budgets hold every piece
       const PieceRec pfirst = g.pieces[F.p0 + fc0];
       __syncwarp();
+      PieceRec p{};
+      if (lane < nfc) p = g.pieces[F.p0 + fc0 + lane];
       if (lane < nfc) {
-        const PieceRec p = g.pieces[F.p0 + fc0 + lane];
         sl.fp[lane] = make_int4(p.v0 - pfirst.v0, p.nv, p.e0 - pfirst.e0, p.ne);
         const float4 c = p.sphere;
         const float cx = val(Rr[0]) * c.x + val(Rr[1]) * c.y + val(Rr[2]) * c.z + val(tr[0]);
@@ -764,13 +928,45 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
         }
       }
-      for (int i = lane; i < V; i += 32) {
-        const float4 v = g.verts[pfirst.v0 + i];
-        const V3T<T> vv = v3(T(v.x), T(v.y), T(v.z));
-        const V3T<T> x = rot(Rr, vv);
-        sl.xs[i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
+      if (saved && S.np <= kHitS) {
+        // with the forward's hits known, only the pieces with a marked
+        // direction are visited: stage just their vertices and edges, packed
+        __syncwarp();
+        bool need = false;
+        if (lane < nfc)
+          for (int q = 0; q < kHitWords; ++q) need |= sl.hit[lane * kHitWords + q] != 0u;
+        const int nv = need ? p.nv : 0, ne = need ? p.ne : 0;
+        int iv = nv, ie = ne;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
+          if (lane >= o) { iv += a; ie += b; }
+        }
+        if (lane < nfc) sl.fp[lane] = make_int4(iv - nv, p.nv, ie - ne, p.ne);
+        unsigned m = __ballot_sync(kFull, need);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const int vo = __shfl_sync(kFull, iv - nv, l), vn = __shfl_sync(kFull, nv, l),
+                    v0 = __shfl_sync(kFull, p.v0, l);
+          const int eo = __shfl_sync(kFull, ie - ne, l), en = __shfl_sync(kFull, ne, l),
+                    e0 = __shfl_sync(kFull, p.e0, l);
+          for (int i = lane; i < vn; i += 32) {
+            const float4 v = g.verts[v0 + i];
+            const V3T<T> x = rot(Rr, v3(T(v.x), T(v.y), T(v.z)));
+            sl.xs[vo + i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
+          }
+          for (int j = lane; j < en; j += 32) sl.edges[eo + j] = g.edges[e0 + j];
+        }
+      } else {
+        for (int i = lane; i < V; i += 32) {
+          const float4 v = g.verts[pfirst.v0 + i];
+          const V3T<T> vv = v3(T(v.x), T(v.y), T(v.z));
+          const V3T<T> x = rot(Rr, vv);
+          sl.xs[i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
+        }
+        for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
       }
-      for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
       __syncwarp();
 
       bwd_sweep<T, 1, kK, kCount>(g, sl, S, nfc, margin, saved != nullptr, us, kp, lane, ac, cnt);
