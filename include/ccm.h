@@ -202,13 +202,14 @@ CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pos
 /* Same as ccm_contacts_backward, for callers that cannot obtain device
  * memory for scratch -- e.g. code running while another framework owns the
  * whole device memory pool, or a real-time loop that forbids allocation after
- * start-up.  The per-unit slots of the reverse pass (24 floats per side of a
- * pair) live in one fixed 4 MiB array compiled into the library instead of
- * the batch's workspace, so the call allocates nothing and uses no workspace;
+ * start-up.  The per-work-item slots of the reverse pass (24 floats each)
+ * live in one fixed 4 MiB array compiled into the library instead of the
+ * batch's workspace, so the call allocates nothing and uses no workspace;
  * the caller still passes every input and output.  The paper has no
  * counterpart: this is a deployment variant of the same computation.
- *   - Limit: n <= 21845 pairs (2 n * 24 floats <= 2^20); larger batches are
- *     rejected with CCM_ERR_INVALID.
+ *   - Limit: 43690 work items (43690 * 24 floats <= 2^20), i.e. n <= 21845
+ *     pairs when no body has more pieces than one work item holds (the
+ *     tuning's `groups`); larger batches are rejected with CCM_ERR_INVALID.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  *   - Every call on a device shares the array and it keeps the last call's
