@@ -132,8 +132,8 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world):
-    from paper_2604_17538_b300 import scenes
-    seed = 2 + 1000 * rank
+    from paper_2604_17538_b300 import scenes, shard
+    seed = shard.shard_seed(2, rank)
     sc = scenes.hull_env_scene(seed=seed, n_envs=args.envs, workers=0)
 
     import torch
@@ -251,12 +251,10 @@ def run_ours(args, rank, world):
         a1.synchronize()
         t_e2e += a0.elapsed_time(a1) / 1e3
 
-    # max over ranks
-    times = torch.tensor([t_step, t_fwd, t_vjp, t_hvp, t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    t_step, t_fwd, t_vjp, t_hvp, t_e2e = times.tolist()
-    total_pp = piece_pairs * world
+    # max over ranks of the times, sum over ranks of the work
+    t_step, t_fwd, t_vjp, t_hvp, t_e2e = shard.reduce_max([t_step, t_fwd, t_vjp, t_hvp, t_e2e],
+                                                          "cuda")
+    (total_pp,) = shard.reduce_sum([piece_pairs], "cuda")
     K = args.steps
 
     out = None
@@ -393,7 +391,8 @@ def run_uneven(args, rank, world):
     captured once in a CUDA graph and replayed."""
     from paper_2604_17538_b300 import scenes
     t0 = time.perf_counter()
-    sc = scenes.uneven_scene(seed=4 + 1000 * rank, n_pairs=args.pairs, workers=0)
+    from paper_2604_17538_b300 import shard
+    sc = scenes.uneven_scene(seed=shard.shard_seed(4, rank), n_pairs=args.pairs, workers=0)
     t_gen = time.perf_counter() - t0
     import torch
     from paper_2604_17538_b300 import abi, api, build, tune
@@ -443,23 +442,18 @@ def run_uneven(args, rank, world):
         b.synchronize()
         t += a.elapsed_time(b) / 1e3
     clocks = sampler.stop()
-    tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t = tt.item()
-    pp = sc.piece_pairs()
+    pp_all, t, _ = shard.job_rate(sc.piece_pairs(), t, "cuda")
     if rank != 0:
         return None, sc
     npb = np.diff(sc.geom.body_piece_off)
     return {
-        "metric": METRIC, "value": pp * world * args.steps / t, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": pp_all * args.steps / t, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded convex-hull scenes)",
         "config": {"workload": f"uneven batch: {args.pairs} body pairs, pieces/body log-U[1,64] "
                                "(pool of 8192 bodies), hull points log-U[8,512]; fwd + grad in "
-                               "one CUDA graph", "piece_pairs_per_gpu": pp,
+                               "one CUDA graph", "piece_pairs_per_gpu": sc.piece_pairs(),
                    "pieces_per_body_mean": float(npb[sc.pair_a].mean()),
                    "l2": "flushed between timed steps (512 MiB write, untimed)",
                    "tuning": tuning, "generation_s": t_gen},
