@@ -126,7 +126,9 @@ CCM_API ccm_status ccm_output_size(ccm_ctx ctx, int64_t n, const ccm_geom* A, co
 /* Plans a batch of n body pairs (A[i], B[i]) (host arrays): uploads the pair
  * table and the group offsets and picks the launch shape.  The batch is the
  * unit that ccm_contacts and ccm_contacts_backward run on; poses change
- * between calls, pairs do not.  Synchronous; allocates.
+ * between calls, pairs do not.  Calls on one batch share its workspace
+ * (reverse-pass slots, work counters): issue them in order on one stream.
+ * Synchronous; allocates.
  * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_batch_create(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
                             ccm_batch* out);

@@ -405,7 +405,9 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   L.ybar = ybar;
   L.dir = dir;
   L.saved = nullptr;
+  L.pair_order = nullptr;
   L.counters = nullptr;
+  L.sched = nullptr;   // no workspace: units dealt round-robin
   L.kp = kp;
   L.us = b->us;
   L.part = nullptr;
@@ -595,6 +597,17 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   if ((st = upload(bt->d_items, items, "work items")) != CCM_OK) return st;
   if ((st = upload(bt->d_item_order, items_by_cost(cost), "item order")) != CCM_OK) return st;
   if ((st = upload(bt->d_item_off, item_off, "item offsets")) != CCM_OK) return st;
+  {   // pairs by decreasing cost (the sum of their items'), for the per-pair reverse pass
+    std::vector<int64_t> pcost(bt->pairs.size(), 0);
+    for (size_t i = 0; i < bt->pairs.size(); ++i)
+      for (int64_t j = item_off[i]; j < item_off[i + 1]; ++j) pcost[i] += cost[j];
+    if ((st = upload(bt->d_pair_order, items_by_cost(pcost), "pair order")) != CCM_OK) return st;
+  }
+  bt->per_pair = bt->mx.s_pieces <= kHitS;
+  if (!bt->d_sched.ptr) {
+    std::vector<int32_t> zeros(2, 0);
+    if ((st = upload(bt->d_sched, zeros, "work counters")) != CCM_OK) return st;
+  }
   if ((int64_t)items.size() != bt->n_items || !bt->d_part.ptr) {
     bt->d_part.release();
     std::vector<float> zeros((size_t)std::max<size_t>(1, items.size()) * 24, 0.f);
@@ -638,7 +651,9 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.ybar = ybar;
   L.dir = dir;
   L.saved = saved;
+  L.pair_order = saved && b->per_pair ? static_cast<const int32_t*>(b->d_pair_order.ptr) : nullptr;
   L.counters = counters;
+  L.sched = static_cast<int*>(b->d_sched.ptr) + 1;
   L.kp = kp;
   L.us = b->us;
   L.part = static_cast<float*>(b->d_part.ptr);
@@ -657,6 +672,8 @@ void Batch::release() {
   d_items.release();
   d_item_order.release();
   d_item_off.release();
+  d_pair_order.release();
+  d_sched.release();
   d_part.release();
 }
 
@@ -683,6 +700,7 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   L.y = y;
   L.saved = saved;
   L.counters = counters;
+  L.sched = static_cast<int*>(b->d_sched.ptr);
   L.grid = b->grid;
   cudaError_t e = launch_forward(L, stream);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");

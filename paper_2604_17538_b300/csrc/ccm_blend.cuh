@@ -129,8 +129,9 @@ __device__ void fold_t(PartT<T> c, int key, PartT<T>* acc, int lane) {
 constexpr int kHitS = 256;
 constexpr int kHitWords = kHitS / 32;
 
+// A negative sg (a caller that gates by hits it already has) marks nothing.
 __device__ __forceinline__ void mark_hit(uint32_t* hit, int g, int sg, float w) {
-  if (w > 0.f && sg < kHitS) atomicOr(hit + g * kHitWords + (sg >> 5), 1u << (sg & 31));
+  if (w > 0.f && sg >= 0 && sg < kHitS) atomicOr(hit + g * kHitWords + (sg >> 5), 1u << (sg & 31));
 }
 
 // What ccm_contacts_save keeps per output group for the reverse pass: the

@@ -344,6 +344,49 @@ __device__ __forceinline__ V3T<T> contact_adjoint(const SdfT<T>& c, V3T<T> p, co
 }
 
 // ---------------------------------------------------------------------------
+// poses on T: the tangent of R is [w]x R and of t is v when differentiating
+// along a twist direction (w, v)
+// ---------------------------------------------------------------------------
+template <class T> struct PoseT {
+  T R[9];
+  T t[3];
+};
+
+__device__ inline void load_pose_t(const float* p, const float* u, PoseT<float>& P) {
+  (void)u;
+  for (int i = 0; i < 9; ++i) P.R[i] = __ldg(p + i);
+  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(p + 9 + i);
+}
+__device__ inline void load_pose_t(const float* p, const float* u, PoseT<Dual>& P) {
+  float R[9];
+  for (int i = 0; i < 9; ++i) R[i] = __ldg(p + i);
+  const float w0 = __ldg(u + 0), w1 = __ldg(u + 1), w2 = __ldg(u + 2);
+  const float W[9] = {0.f, -w2, w1, w2, 0.f, -w0, -w1, w0, 0.f};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      P.R[3 * i + j] = Dual(R[3 * i + j], W[3 * i] * R[j] + W[3 * i + 1] * R[3 + j] +
+                                              W[3 * i + 2] * R[6 + j]);
+  for (int i = 0; i < 3; ++i) P.t[i] = Dual(__ldg(p + 9 + i), __ldg(u + 3 + i));
+}
+
+template <class T> __device__ __forceinline__ V3T<T> rot(const T R[9], V3T<T> x) {
+  return v3(fma_t(R[0], x.x, fma_t(R[1], x.y, R[2] * x.z)),
+            fma_t(R[3], x.x, fma_t(R[4], x.y, R[5] * x.z)),
+            fma_t(R[6], x.x, fma_t(R[7], x.y, R[8] * x.z)));
+}
+template <class T> __device__ __forceinline__ V3T<T> rotT(const T R[9], V3T<T> x) {
+  return v3(fma_t(R[0], x.x, fma_t(R[3], x.y, R[6] * x.z)),
+            fma_t(R[1], x.x, fma_t(R[4], x.y, R[7] * x.z)),
+            fma_t(R[2], x.x, fma_t(R[5], x.y, R[8] * x.z)));
+}
+template <class T> __device__ __forceinline__ V3T<T> cross3(V3T<T> a, V3T<T> b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float tan_of(float) { return 0.f; }
+__device__ __forceinline__ float tan_of(Dual a) { return a.d; }
+
+// ---------------------------------------------------------------------------
 // slice of the backward kernel (per warp)
 // ---------------------------------------------------------------------------
 template <class T> struct BwdSlice {
@@ -366,12 +409,22 @@ template <class T> struct BwdSlice {
   uint16_t* elist;    // [item_e]
   uint8_t* need;      // [item_v]
   uint16_t* am;       // [item_v] a plane attaining the max-plane value
+  int* gside;         // [groups] side of each group: 0 (F = A, S = B) or 1 (F = B, S = A)
+  PoseT<T>* spose;    // [2] pose of the SDF body of side 0 (B) and side 1 (A)
+  V3T<T>* tba;        // [1] t_B - t_A
+  T* pacc;            // [18] pair totals: F, M (about t_A), output terms of A and B
+  PoseT<T>* rel;      // [2] relative pose S <- F of side 0 and side 1
   uint32_t* hit;      // [groups * kHitWords] directions that gave a contact in pass 1
 };
 
 
 template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShape& u) {
   int b = 0;
+  b += align16i(4 * u.groups);
+  b += align16i((int)sizeof(PoseT<T>) * 2);
+  b += align16i((int)sizeof(V3T<T>));
+  b += align16i((int)sizeof(T) * 18);
+  b += align16i((int)sizeof(PoseT<T>) * 2);
   b += align16i(4 * kHitWords * u.groups);
   b += 16 * u.plane_budget;
   b += align16i(8 * u.spiece_budget);
@@ -394,6 +447,11 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
 
 template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, const UnitShape& u) {
   BwdSlice<T> s;
+  s.gside = reinterpret_cast<int*>(p);          p += align16i(4 * u.groups);
+  s.spose = reinterpret_cast<PoseT<T>*>(p);     p += align16i((int)sizeof(PoseT<T>) * 2);
+  s.tba = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>));
+  s.pacc = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * 18);
+  s.rel = reinterpret_cast<PoseT<T>*>(p);       p += align16i((int)sizeof(PoseT<T>) * 2);
   s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * kHitWords * u.groups);
   s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
   s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * u.spiece_budget);
@@ -515,9 +573,71 @@ __device__ void edge_t(const float4* __restrict__ pl, int nf, V3T<T> xI, V3T<T> 
 // ---------------------------------------------------------------------------
 // one list of live directions: pass 1 (fold) or pass 2 (adjoint)
 // ---------------------------------------------------------------------------
+// Per-lane sums of the contact-point adjoints as forces on the bodies:
+// F = sum sigma f and M = sum sigma (p - t_A) x f, where f = R_S x_bar is the
+// world-frame adjoint of a contact point p (world) of a group whose feature
+// body is A (sigma = +1, side 0) or B (sigma = -1, side 1).  Body A receives
+// the force F and the torque M about t_A; body B receives -F and
+// -M + (t_B - t_A) x F about t_B.
 template <class T> struct Accum {
-  V3T<T> X1, X2;   // sum x_bar, sum x cross x_bar (S frame)
+  V3T<T> F, M;
 };
+
+template <class T>
+__device__ __forceinline__ void add_force(Accum<T>& ac, const BwdSlice<T>& sl, int grp, V3T<T> x,
+                                          V3T<T> xb) {
+  const int side = sl.gside[grp];
+  const PoseT<T>& P = sl.spose[side];
+  const V3T<T> f = rot(P.R, xb);
+  V3T<T> p = rot(P.R, x);
+  if (side == 0) {
+    const V3T<T> t = sl.tba[0];
+    p = v3(p.x + t.x, p.y + t.y, p.z + t.z);
+  }
+  const V3T<T> m = cross3(p, f);
+  if (side == 0) {
+    ac.F = v3(ac.F.x + f.x, ac.F.y + f.y, ac.F.z + f.z);
+    ac.M = v3(ac.M.x + m.x, ac.M.y + m.y, ac.M.z + m.z);
+  } else {
+    ac.F = v3(ac.F.x - f.x, ac.F.y - f.y, ac.F.z - f.z);
+    ac.M = v3(ac.M.x - m.x, ac.M.y - m.y, ac.M.z - m.z);
+  }
+}
+
+// The 12 gradient components (w_A, v_A, w_B, v_B) of one pair's (or one
+// work item's) forces, plus the output-transform terms (w, v) of each body,
+// into g[12]; with h != NULL the tangents (H u) into h[12], each body's
+// twist gradient corrected by -1/2 u_w x grad_w (the chart's second-order
+// term).  uA / uB: the direction's twists of A and B (NULL for float).
+template <class T>
+__device__ void write_twists(V3T<T> F, V3T<T> M, V3T<T> oAw, V3T<T> oAv, V3T<T> oBw,
+                             V3T<T> oBv, V3T<T> tba, const float* uA, const float* uB, float* g,
+                             float* h) {
+  const V3T<T> c = cross3(tba, F);
+  const T gA[6] = {M.x + oAw.x, M.y + oAw.y, M.z + oAw.z, F.x + oAv.x, F.y + oAv.y, F.z + oAv.z};
+  const T gB[6] = {c.x - M.x + oBw.x, c.y - M.y + oBw.y, c.z - M.z + oBw.z,
+                   oBv.x - F.x, oBv.y - F.y, oBv.z - F.z};
+  for (int q = 0; q < 6; ++q) {
+    g[q] = val(gA[q]);
+    g[6 + q] = val(gB[q]);
+  }
+  if (h) {
+    float hA[6], hB[6];
+    for (int q = 0; q < 6; ++q) { hA[q] = tan_of(gA[q]); hB[q] = tan_of(gB[q]); }
+    const float wA[3] = {val(gA[0]), val(gA[1]), val(gA[2])};
+    const float wB[3] = {val(gB[0]), val(gB[1]), val(gB[2])};
+    hA[0] -= 0.5f * (uA[1] * wA[2] - uA[2] * wA[1]);
+    hA[1] -= 0.5f * (uA[2] * wA[0] - uA[0] * wA[2]);
+    hA[2] -= 0.5f * (uA[0] * wA[1] - uA[1] * wA[0]);
+    hB[0] -= 0.5f * (uB[1] * wB[2] - uB[2] * wB[1]);
+    hB[1] -= 0.5f * (uB[2] * wB[0] - uB[0] * wB[2]);
+    hB[2] -= 0.5f * (uB[0] * wB[1] - uB[1] * wB[0]);
+    for (int q = 0; q < 6; ++q) {
+      h[q] = hA[q];
+      h[6 + q] = hB[q];
+    }
+  }
+}
 
 // Work counters of a counted reverse pass (CCM_BWD_CNT_* of ccm.h): plane
 // evaluations by kind and pass, per lane, summed at the end of the kernel.
@@ -606,12 +726,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         const SdfT<T> e = sdf_t<T, 2>(sl.planes + s.x, s.y, x, m, cf.nb, kp);
         sl.phi[t] = e.phi;
         sl.grad[t] = e.g;
-        if (m < kp.d_max && cf.live) {
-          const V3T<T> xb = contact_adjoint(e, x, cf, kp);
-          ac.X1 = v3(ac.X1.x + xb.x, ac.X1.y + xb.y, ac.X1.z + xb.z);
-          ac.X2 = v3(ac.X2.x + (x.y * xb.z - x.z * xb.y), ac.X2.y + (x.z * xb.x - x.x * xb.z),
-                     ac.X2.z + (x.x * xb.y - x.y * xb.x));
-        }
+        if (m < kp.d_max && cf.live) add_force(ac, sl, g, x, contact_adjoint(e, x, cf, kp));
       }
     }
     if (kPass == 1) fold_t(c, key, sl.acc, lane);
@@ -653,10 +768,8 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         if (kCount) { cnt.h2 += s.y; cnt.g2 += (unsigned long long)steps * s.y; }
         edge_t<T, true, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
                         sl.phi[t1v], sl.grad[t0v], sl.grad[t1v], cf, kp, sc, pe, xbI, xbII);
-        ac.X1 = v3(ac.X1.x + xbI.x + xbII.x, ac.X1.y + xbI.y + xbII.y, ac.X1.z + xbI.z + xbII.z);
-        ac.X2 = v3(ac.X2.x + (a.y * xbI.z - a.z * xbI.y) + (b.y * xbII.z - b.z * xbII.y),
-                   ac.X2.y + (a.z * xbI.x - a.x * xbI.z) + (b.z * xbII.x - b.x * xbII.z),
-                   ac.X2.z + (a.x * xbI.y - a.y * xbI.x) + (b.x * xbII.y - b.y * xbII.x));
+        add_force(ac, sl, g, a, xbI);
+        add_force(ac, sl, g, b, xbII);
       }
     }
     if (kPass == 1) fold_t(c, key, sl.acc, lane);
@@ -801,48 +914,60 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
   }
 }
 
-// ---------------------------------------------------------------------------
-// poses on T: the tangent of R is [w]x R and of t is v when differentiating
-// along a twist direction (w, v)
-// ---------------------------------------------------------------------------
-template <class T> struct PoseT {
-  T R[9];
-  T t[3];
-};
 
-__device__ inline void load_pose_t(const float* p, const float* u, PoseT<float>& P) {
-  (void)u;
-  for (int i = 0; i < 9; ++i) P.R[i] = __ldg(p + i);
-  for (int i = 0; i < 3; ++i) P.t[i] = __ldg(p + 9 + i);
+// A group's adjoint coefficients (Coef) from its blend partial A and its
+// cotangent row yb, with PS the pose of its SDF body; with jrow the output
+// tangents (J u) of the group; ow, ov: the output-transform terms of the SDF
+// body's twist, d<ybar, y>/d(w_S, v_S) through p_w = R_S q + t_S and
+// n_w = R_S nu / |nu| (zero for a group without a contact).
+template <class T>
+__device__ void form_coef(const PartT<T>& A, const float* yb, const PoseT<T>& PS, float* jrow,
+                          Coef<T>& cf, V3T<T>& ow, V3T<T>& ov) {
+  cf.db = yb[0];
+  cf.ab = yb[1];
+  cf.live = val(A.U) > 0.f;
+  const V3T<T> pbw = v3(T(yb[2]), T(yb[3]), T(yb[4]));
+  const V3T<T> nbw = v3(T(yb[5]), T(yb[6]), T(yb[7]));
+  ow = ov = zero3t<T>();
+  if (cf.live) {
+    const T iU = rcp_t(A.U);
+    const T d = fma_t(A.Dd, iU, A.rd), a = fma_t(A.Da, iU, A.rf);
+    const V3T<T> q = axpy3(iU, A.Dp, A.rp);
+    const V3T<T> nu = axpy3(iU, A.Dn, A.rn);
+    const V3T<T> nuw = rot(PS.R, nu);
+    const T nn = sqrt_t(dot3(nuw, nuw));
+    const T inn = val(nn) > 0.f ? rcp_t(nn) : T(0.f);
+    const V3T<T> nw = v3(nuw.x * inn, nuw.y * inn, nuw.z * inn);
+    const V3T<T> qw = rot(PS.R, q);
+    if (jrow) {
+      jrow[0] = tan_of(d);
+      jrow[1] = tan_of(a);
+      jrow[2] = tan_of(qw.x) + tan_of(PS.t[0]);
+      jrow[3] = tan_of(qw.y) + tan_of(PS.t[1]);
+      jrow[4] = tan_of(qw.z) + tan_of(PS.t[2]);
+      jrow[5] = tan_of(nw.x);
+      jrow[6] = tan_of(nw.y);
+      jrow[7] = tan_of(nw.z);
+    }
+    cf.M = A.M;
+    cf.invU = iU;
+    cf.qb = rotT(PS.R, pbw);
+    const V3T<T> nbs = rotT(PS.R, nbw);
+    const V3T<T> ns = rotT(PS.R, nw);
+    const T nsn = dot3(ns, nbs);
+    cf.nb = v3((nbs.x - ns.x * nsn) * inn, (nbs.y - ns.y * nsn) * inn, (nbs.z - ns.z * nsn) * inn);
+    cf.rd = A.rd; cf.rf = A.rf; cf.rp = A.rp; cf.rn = A.rn;
+    cf.gdel = (cf.db * A.Dd + cf.ab * A.Da + dot3(cf.qb, A.Dp) + dot3(cf.nb, A.Dn)) * iU;
+    const V3T<T> c1 = cross3(qw, pbw), c2 = cross3(nw, nbw);
+    ow = v3(c1.x + c2.x, c1.y + c2.y, c1.z + c2.z);
+    ov = pbw;
+  } else {
+    cf.M = cf.invU = cf.gdel = cf.rd = cf.rf = T(0.f);
+    cf.qb = cf.nb = cf.rp = cf.rn = zero3t<T>();
+    if (jrow)
+      for (int q = 0; q < 8; ++q) jrow[q] = 0.f;
+  }
 }
-__device__ inline void load_pose_t(const float* p, const float* u, PoseT<Dual>& P) {
-  float R[9];
-  for (int i = 0; i < 9; ++i) R[i] = __ldg(p + i);
-  const float w0 = __ldg(u + 0), w1 = __ldg(u + 1), w2 = __ldg(u + 2);
-  const float W[9] = {0.f, -w2, w1, w2, 0.f, -w0, -w1, w0, 0.f};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      P.R[3 * i + j] = Dual(R[3 * i + j], W[3 * i] * R[j] + W[3 * i + 1] * R[3 + j] +
-                                              W[3 * i + 2] * R[6 + j]);
-  for (int i = 0; i < 3; ++i) P.t[i] = Dual(__ldg(p + 9 + i), __ldg(u + 3 + i));
-}
-
-template <class T> __device__ __forceinline__ V3T<T> rot(const T R[9], V3T<T> x) {
-  return v3(fma_t(R[0], x.x, fma_t(R[1], x.y, R[2] * x.z)),
-            fma_t(R[3], x.x, fma_t(R[4], x.y, R[5] * x.z)),
-            fma_t(R[6], x.x, fma_t(R[7], x.y, R[8] * x.z)));
-}
-template <class T> __device__ __forceinline__ V3T<T> rotT(const T R[9], V3T<T> x) {
-  return v3(fma_t(R[0], x.x, fma_t(R[3], x.y, R[6] * x.z)),
-            fma_t(R[1], x.x, fma_t(R[4], x.y, R[7] * x.z)),
-            fma_t(R[2], x.x, fma_t(R[5], x.y, R[8] * x.z)));
-}
-template <class T> __device__ __forceinline__ V3T<T> cross3(V3T<T> a, V3T<T> b) {
-  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-
-__device__ __forceinline__ float tan_of(float) { return 0.f; }
-__device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 
 // ---------------------------------------------------------------------------
 // the kernel
@@ -856,13 +981,14 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 const float* __restrict__ ybar, const float* __restrict__ dir,
                 const float* __restrict__ saved, KParams kp, UnitShape us,
                 float* __restrict__ part, float* __restrict__ jvp,
-                unsigned long long* __restrict__ counters) {
+                unsigned long long* __restrict__ counters, int* __restrict__ sched) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   BwdCounts cnt;
   const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
   const int64_t n_run = dev_items ? *dev_items : n_items;
-  for (int64_t k = blockIdx.x; k < n_run; k += gridDim.x) {
+  for (int64_t k = first_unit(sched, blockIdx.x); k < n_run;
+       k = next_unit(sched, k, gridDim.x)) {
     const int32_t item = order[k];   // heaviest items first, round-robin
     const WorkItem it = items[item];
     const int64_t u = it.unit;
@@ -891,9 +1017,14 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
     }
     const float margin = 1e-6f * (1.0f + fabsf(val(tr[0])) + fabsf(val(tr[1])) + fabsf(val(tr[2])));
     Accum<T> ac;
-    ac.X1 = v3(T(0.f), T(0.f), T(0.f));
-    ac.X2 = ac.X1;
-    V3T<T> gws = ac.X1, gvs = ac.X1;   // output-transform terms of this lane's groups
+    ac.F = v3(T(0.f), T(0.f), T(0.f));
+    ac.M = ac.F;
+    V3T<T> gws = ac.F, gvs = ac.F;   // output-transform terms of this lane's groups
+    if (lane == 0) {
+      sl.spose[side] = PS;
+      sl.tba[0] = side == 0 ? v3(PS.t[0] - PF.t[0], PS.t[1] - PF.t[1], PS.t[2] - PF.t[2])
+                            : v3(PF.t[0] - PS.t[0], PF.t[1] - PS.t[1], PF.t[2] - PS.t[2]);
+    }
 
     for (int fc0 = it.fc0; fc0 < it.fc1;) {
       int fc1 = fc0, V = 0, E = 0;
@@ -917,6 +1048,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         const float cy = val(Rr[3]) * c.x + val(Rr[4]) * c.y + val(Rr[5]) * c.z + val(tr[1]);
         const float cz = val(Rr[6]) * c.x + val(Rr[7]) * c.y + val(Rr[8]) * c.z + val(tr[2]);
         sl.fs[lane] = make_float4(cx, cy, cz, c.w);
+        sl.gside[lane] = side;
         PartT<T> z;
         part_zero(z);
         sl.acc[lane] = z;
@@ -974,57 +1106,12 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 
       // group outputs, adjoint coefficients and output-transform terms
       if (lane < nfc) {
-        const PartT<T> A = sl.acc[lane];
-        const float* yb = ybar + 8 * (row0 + fc0 + lane);
         Coef<T> cf;
-        cf.db = yb[0];
-        cf.ab = yb[1];
-        cf.live = val(A.U) > 0.f;
-        const V3T<T> pbw = v3(T(yb[2]), T(yb[3]), T(yb[4]));
-        const V3T<T> nbw = v3(T(yb[5]), T(yb[6]), T(yb[7]));
-        if (cf.live) {
-          const T iU = rcp_t(A.U);
-          const T d = fma_t(A.Dd, iU, A.rd), a = fma_t(A.Da, iU, A.rf);
-          const V3T<T> q = axpy3(iU, A.Dp, A.rp);
-          const V3T<T> nu = axpy3(iU, A.Dn, A.rn);
-          const V3T<T> nuw = rot(PS.R, nu);
-          const T nn = sqrt_t(dot3(nuw, nuw));
-          const T inn = val(nn) > 0.f ? rcp_t(nn) : T(0.f);
-          const V3T<T> nw = v3(nuw.x * inn, nuw.y * inn, nuw.z * inn);
-          const V3T<T> qw = rot(PS.R, q);
-          if (jvp) {
-            float* o = jvp + 8 * (row0 + fc0 + lane);
-            o[0] = tan_of(d);
-            o[1] = tan_of(a);
-            o[2] = tan_of(qw.x) + tan_of(PS.t[0]);
-            o[3] = tan_of(qw.y) + tan_of(PS.t[1]);
-            o[4] = tan_of(qw.z) + tan_of(PS.t[2]);
-            o[5] = tan_of(nw.x);
-            o[6] = tan_of(nw.y);
-            o[7] = tan_of(nw.z);
-          }
-          cf.M = A.M;
-          cf.invU = iU;
-          cf.qb = rotT(PS.R, pbw);
-          const V3T<T> nbs = rotT(PS.R, nbw);
-          const V3T<T> ns = rotT(PS.R, nw);
-          const T nsn = dot3(ns, nbs);
-          cf.nb = v3((nbs.x - ns.x * nsn) * inn, (nbs.y - ns.y * nsn) * inn,
-                     (nbs.z - ns.z * nsn) * inn);
-          cf.rd = A.rd; cf.rf = A.rf; cf.rp = A.rp; cf.rn = A.rn;
-          cf.gdel = (cf.db * A.Dd + cf.ab * A.Da + dot3(cf.qb, A.Dp) + dot3(cf.nb, A.Dn)) * iU;
-          // p_w = R_S q + t_S and n_w = R_S nu / |nu| under the twist of S
-          const V3T<T> c1 = cross3(qw, pbw), c2 = cross3(nw, nbw);
-          gws = v3(gws.x + c1.x + c2.x, gws.y + c1.y + c2.y, gws.z + c1.z + c2.z);
-          gvs = v3(gvs.x + pbw.x, gvs.y + pbw.y, gvs.z + pbw.z);
-        } else {
-          cf.M = cf.invU = cf.gdel = cf.rd = cf.rf = T(0.f);
-          cf.qb = cf.nb = cf.rp = cf.rn = zero3t<T>();
-          if (jvp) {
-            float* o = jvp + 8 * (row0 + fc0 + lane);
-            for (int q = 0; q < 8; ++q) o[q] = 0.f;
-          }
-        }
+        V3T<T> ow, ov;
+        form_coef(sl.acc[lane], ybar + 8 * (row0 + fc0 + lane), PS,
+                  jvp ? jvp + 8 * (row0 + fc0 + lane) : nullptr, cf, ow, ov);
+        gws = v3(gws.x + ow.x, gws.y + ow.y, gws.z + ow.z);
+        gvs = v3(gvs.x + ov.x, gvs.y + ov.y, gvs.z + ov.z);
         sl.coef[lane] = cf;
       }
       __syncwarp();
@@ -1032,45 +1119,19 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
       fc0 = fc1;
     }
 
-    // reduce the lanes and form the 12 twist components of this side
-    V3T<T> X1 = ac.X1, X2 = ac.X2;
-    X1 = v3(warp_sum_t(X1.x), warp_sum_t(X1.y), warp_sum_t(X1.z));
-    X2 = v3(warp_sum_t(X2.x), warp_sum_t(X2.y), warp_sum_t(X2.z));
+    // reduce the lanes; the item's forces and its groups' output terms (on
+    // the SDF body) give its share of the pair's 12 twist components
+    const V3T<T> Fs = v3(warp_sum_t(ac.F.x), warp_sum_t(ac.F.y), warp_sum_t(ac.F.z));
+    const V3T<T> Ms = v3(warp_sum_t(ac.M.x), warp_sum_t(ac.M.y), warp_sum_t(ac.M.z));
     gws = v3(warp_sum_t(gws.x), warp_sum_t(gws.y), warp_sum_t(gws.z));
     gvs = v3(warp_sum_t(gvs.x), warp_sum_t(gvs.y), warp_sum_t(gvs.z));
     if (lane == 0) {
-      const V3T<T> X1w = rot(PS.R, X1), X2w = rot(PS.R, X2);
-      const V3T<T> dts = v3(PS.t[0] - PF.t[0], PS.t[1] - PF.t[1], PS.t[2] - PF.t[2]);
-      const V3T<T> cx = cross3(dts, X1w);
-      // F: w_F = R_S X2 + (t_S - t_F) x R_S X1, v_F = R_S X1
-      // S: w_S = -R_S X2 + output terms,       v_S = -R_S X1 + output terms
-      T gF[6] = {X2w.x + cx.x, X2w.y + cx.y, X2w.z + cx.z, X1w.x, X1w.y, X1w.z};
-      T gS[6] = {gws.x - X2w.x, gws.y - X2w.y, gws.z - X2w.z,
-                 gvs.x - X1w.x, gvs.y - X1w.y, gvs.z - X1w.z};
-      // slot layout per unit: [grad (w_A, v_A, w_B, v_B) | H u (same layout)]
+      const V3T<T> z = zero3t<T>();
+      // slot layout per item: [grad (w_A, v_A, w_B, v_B) | H u (same layout)]
       float* o = part + 24 * (int64_t)item;
-      const int offF = side == 0 ? 0 : 6, offS = side == 0 ? 6 : 0;
-      for (int q = 0; q < 6; ++q) {
-        o[offF + q] = val(gF[q]);
-        o[offS + q] = val(gS[q]);
-      }
-      if (uF) {
-        // H u = d/de grad(Exp(e u) T) - 1/2 u_w x grad_w (per body)
-        float hF[6], hS[6], vF[6], vS[6];
-        for (int q = 0; q < 6; ++q) {
-          hF[q] = tan_of(gF[q]); hS[q] = tan_of(gS[q]);
-          vF[q] = val(gF[q]); vS[q] = val(gS[q]);
-        }
-        const float cF[3] = {uF[1] * vF[2] - uF[2] * vF[1], uF[2] * vF[0] - uF[0] * vF[2],
-                             uF[0] * vF[1] - uF[1] * vF[0]};
-        const float cS[3] = {uS[1] * vS[2] - uS[2] * vS[1], uS[2] * vS[0] - uS[0] * vS[2],
-                             uS[0] * vS[1] - uS[1] * vS[0]};
-        for (int q = 0; q < 3; ++q) { hF[q] -= 0.5f * cF[q]; hS[q] -= 0.5f * cS[q]; }
-        for (int q = 0; q < 6; ++q) {
-          o[12 + offF + q] = hF[q];
-          o[12 + offS + q] = hS[q];
-        }
-      }
+      write_twists(Fs, Ms, side == 1 ? gws : z, side == 1 ? gvs : z, side == 0 ? gws : z,
+                   side == 0 ? gvs : z, sl.tba[0], dir ? dir + 12 * pi : nullptr,
+                   dir ? dir + 12 * pi + 6 : nullptr, o, dir ? o + 12 : nullptr);
     }
     __syncwarp();
   }
@@ -1088,6 +1149,303 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 }
 
 // grad / hvp of pair i = the two units' slots, side 0 then side 1
+// ---------------------------------------------------------------------------
+// Reverse pass per body pair, given the forward's saved record.  Only the
+// groups the forward found contacts in (a non-zero hit word) are visited,
+// those of both sides of the pair in the same lists: every group carries its
+// side, so the contacts of A's vertices and edges in B's frame and of B's in
+// A's frame share a warp's lanes.  The SDF pieces of the marked directions of
+// both bodies are staged packed in one index space, [0, npB) for B's pieces
+// and [npB, npB + npA) for A's.  The pair's 12 gradient (and H u) components
+// are written directly; a pair without marked groups gets zeros.  Every SDF
+// body must have at most kHitS pieces (the host checks).
+// ---------------------------------------------------------------------------
+constexpr int kNoMark = -(1 << 30);   // run_list offset that disables hit marks
+
+template <class T, int kPass, int kK, bool kCount>
+__device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec& bA,
+                           const BodyRec& bB, int nfc, const UnitShape& us, const KParams& kp,
+                           int lane, Accum<T>& ac, BwdCounts& cnt) {
+  const int npB = bB.np, nS = bA.np + bB.np;
+  // does some group of the matching side mark S index si?
+  auto needed = [&](int si) {
+    const int side = si < npB ? 0 : 1;
+    const int b = side == 0 ? si : si - npB;
+    uint32_t any = 0;
+    for (int f = 0; f < nfc; ++f)
+      if (sl.gside[f] == side) any |= sl.hit[f * kHitWords + (b >> 5)];
+    return ((any >> (b & 31)) & 1u) != 0u;
+  };
+  for (int sc0 = 0; sc0 < nS;) {
+    // the chunk [sc0, sc1): at most spiece_budget indices whose needed
+    // pieces' planes fit plane_budget; stage those planes, packed
+    int sc1 = sc0, P = 0;
+    __syncwarp();
+    while (sc1 < nS && sc1 - sc0 < us.spiece_budget) {
+      const int si = sc1 + lane;
+      const bool valid = si < nS && si - sc0 < us.spiece_budget;
+      int nf = 0, f0 = 0;
+      if (valid && needed(si)) {
+        const PieceRec p = g.pieces[si < npB ? bB.p0 + si : bA.p0 + (si - npB)];
+        nf = p.nf;
+        f0 = p.f0;
+      }
+      int incl = nf;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const bool fits = valid && P + incl <= us.plane_budget;
+      const unsigned fb = __ballot_sync(kFull, fits);
+      const int take = __popc(fb);   // a prefix of the lanes: incl grows with the lane
+      if (valid && fits) sl.sp[si - sc0] = make_int2(P + incl - nf, nf);
+      unsigned m = __ballot_sync(kFull, fits && nf > 0);
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        const int o_l = P + __shfl_sync(kFull, incl - nf, l), n_l = __shfl_sync(kFull, nf, l),
+                  f_l = __shfl_sync(kFull, f0, l);
+        for (int k = lane; k < n_l; k += 32) sl.planes[o_l + k] = g.planes[f_l + k];
+      }
+      if (take > 0) P += __shfl_sync(kFull, incl, take - 1);
+      sc1 += take;
+      if (take < 32) break;
+    }
+    __syncwarp();
+    if (sc1 == sc0) break;   // unreachable: every piece fits the plane budget
+    if (P == 0) {            // no marked direction in this chunk
+      sc0 = sc1;
+      continue;
+    }
+    const int nsc = sc1 - sc0;
+    int np = 0;
+    const int ndir = nfc * nsc;
+    for (int d0 = 0; d0 < ndir; d0 += 32) {
+      const int d = d0 + lane;
+      bool live = false;
+      int code = 0;
+      if (d < ndir) {
+        const int fcd = d / nsc, scd = d - fcd * nsc;
+        const int si = sc0 + scd;
+        const int side = si < npB ? 0 : 1;
+        if (sl.gside[fcd] == side) {
+          const int b = side == 0 ? si : si - npB;
+          live = (sl.hit[fcd * kHitWords + (b >> 5)] >> (b & 31)) & 1u;
+        }
+        code = (fcd << 16) | scd;
+        if (kCount) cnt.dirs += 1;
+      }
+      const unsigned bal = __ballot_sync(kFull, live);
+      const int nl = __popc(bal);
+      if (np + nl > kPending) {
+        bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt);
+        np = 0;
+      }
+      if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
+      np += nl;
+      __syncwarp();
+    }
+    if (np > 0) bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt);
+    sc0 = sc1;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ bool any_hit(const float* saved, int64_t row) {
+  const uint32_t* h = reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * row + 18);
+  uint32_t a = 0;
+  for (int q = 0; q < kHitWords; ++q) a |= h[q];
+  return a != 0u;
+}
+
+template <class T, int kK, bool kCount>
+__global__ void __launch_bounds__(32, 1)
+bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __restrict__ porder,
+                int64_t n_pairs, const int64_t* __restrict__ dev_pairs,
+                const float* __restrict__ pose_a, const float* __restrict__ pose_b,
+                const float* __restrict__ ybar, const float* __restrict__ dir,
+                const float* __restrict__ saved, KParams kp, UnitShape us,
+                float* __restrict__ grad, float* __restrict__ hvp, float* __restrict__ jvp,
+                unsigned long long* __restrict__ counters, int* __restrict__ sched) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  BwdCounts cnt;
+  const BwdSlice<T> sl = bwd_slice<T>(smem_raw, us);
+  PoseT<T>* rel = sl.rel;
+  const int64_t n_run = dev_pairs ? *dev_pairs : n_pairs;
+  for (int64_t k = first_unit(sched, blockIdx.x); k < n_run;
+       k = next_unit(sched, k, gridDim.x)) {
+    const int64_t pi = porder[k];   // heaviest pairs first, round-robin
+    const PairRec pr = pairs[pi];
+    const BodyRec bA = g.bodies[pr.bodyA], bB = g.bodies[pr.bodyB];
+    const float* uA = dir ? dir + 12 * pi : nullptr;
+    const float* uB = dir ? dir + 12 * pi + 6 : nullptr;
+    __syncwarp();
+    if (lane == 0) {
+      PoseT<T> PA, PB;
+      load_pose_t(pose_a + 12 * pi, uA, PA);
+      load_pose_t(pose_b + 12 * pi, uB, PB);
+      sl.spose[0] = PB;
+      sl.spose[1] = PA;
+      sl.tba[0] = v3(PB.t[0] - PA.t[0], PB.t[1] - PA.t[1], PB.t[2] - PA.t[2]);
+      for (int side = 0; side < 2; ++side) {   // relative pose S <- F
+        const PoseT<T>& F = side == 0 ? PA : PB;
+        const PoseT<T>& S = side == 0 ? PB : PA;
+        PoseT<T> r;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            r.R[3 * i + j] = fma_t(S.R[i], F.R[j], fma_t(S.R[3 + i], F.R[3 + j], S.R[6 + i] * F.R[6 + j]));
+        const V3T<T> q = rotT(S.R, v3(F.t[0] - S.t[0], F.t[1] - S.t[1], F.t[2] - S.t[2]));
+        r.t[0] = q.x; r.t[1] = q.y; r.t[2] = q.z;
+        rel[side] = r;
+      }
+      for (int q = 0; q < 18; ++q) sl.pacc[q] = T(0.f);
+    }
+    __syncwarp();
+    Accum<T> ac;
+    ac.F = v3(T(0.f), T(0.f), T(0.f));
+    ac.M = ac.F;
+    const int ncand = bA.np + bB.np;   // group rows goff + c; c < npA: A's pieces (side 0)
+    int cand = 0;
+    for (;;) {
+      // the next chunk: up to us.groups marked groups within the budgets
+      int nfc = 0, V = 0, E = 0;
+      while (cand < ncand && nfc < us.groups) {
+        const int c = cand + lane;
+        bool live = false;
+        int nv = 0, ne = 0;
+        if (c < ncand) {
+          live = any_hit<T>(saved, pr.goff + c);
+          if (live) {
+            const PieceRec p = g.pieces[c < bA.np ? bA.p0 + c : bB.p0 + (c - bA.np)];
+            nv = p.nv;
+            ne = p.ne;
+          }
+        }
+        unsigned m = __ballot_sync(kFull, live);
+        int next = min(ncand, cand + 32);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          const int nv_l = __shfl_sync(kFull, nv, l), ne_l = __shfl_sync(kFull, ne, l);
+          if (nfc == us.groups || V + nv_l > us.vert_budget || E + ne_l > us.edge_budget) {
+            next = cand + l;   // starts the next chunk
+            break;
+          }
+          if (lane == 0) sl.gside[nfc] = cand + l;   // candidate index for now
+          V += nv_l;
+          E += ne_l;
+          ++nfc;
+          m &= m - 1;
+        }
+        cand = next;
+        if (m) break;
+      }
+      if (nfc == 0) break;
+      __syncwarp();
+      // stage the chunk's groups: side, packed vertices (moved into the SDF
+      // frame of their side) and edges, hits, zero partials
+      int c = 0, side = 0;
+      PieceRec p{};
+      if (lane < nfc) {
+        c = sl.gside[lane];
+        side = c < bA.np ? 0 : 1;
+        p = g.pieces[side == 0 ? bA.p0 + c : bB.p0 + (c - bA.np)];
+      }
+      const int nv = lane < nfc ? p.nv : 0, ne = lane < nfc ? p.ne : 0;
+      int iv = nv, ie = ne;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
+        if (lane >= o) { iv += a; ie += b; }
+      }
+      __syncwarp();
+      if (lane < nfc) {
+        sl.gside[lane] = side;
+        sl.fp[lane] = make_int4(iv - nv, p.nv, ie - ne, p.ne);
+        const PoseT<T>& r = rel[side];
+        const float4 s4 = p.sphere;
+        const float cx = val(r.R[0]) * s4.x + val(r.R[1]) * s4.y + val(r.R[2]) * s4.z + val(r.t[0]);
+        const float cy = val(r.R[3]) * s4.x + val(r.R[4]) * s4.y + val(r.R[5]) * s4.z + val(r.t[1]);
+        const float cz = val(r.R[6]) * s4.x + val(r.R[7]) * s4.y + val(r.R[8]) * s4.z + val(r.t[2]);
+        sl.fs[lane] = make_float4(cx, cy, cz, s4.w);
+        PartT<T> z;
+        part_zero(z);
+        sl.acc[lane] = z;
+        const uint32_t* h =
+            reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * (pr.goff + c) + 18);
+        for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = h[q];
+      }
+      for (int l = 0; l < nfc; ++l) {
+        const int vo = __shfl_sync(kFull, iv - nv, l), vn = __shfl_sync(kFull, nv, l),
+                  v0 = __shfl_sync(kFull, p.v0, l), sd = __shfl_sync(kFull, side, l);
+        const int eo = __shfl_sync(kFull, ie - ne, l), en = __shfl_sync(kFull, ne, l),
+                  e0 = __shfl_sync(kFull, p.e0, l);
+        const PoseT<T>& r = rel[sd];
+        for (int i = lane; i < vn; i += 32) {
+          const float4 v = g.verts[v0 + i];
+          const V3T<T> x = rot(r.R, v3(T(v.x), T(v.y), T(v.z)));
+          sl.xs[vo + i] = v3(x.x + r.t[0], x.y + r.t[1], x.z + r.t[2]);
+        }
+        for (int j = lane; j < en; j += 32) sl.edges[eo + j] = g.edges[e0 + j];
+      }
+      __syncwarp();
+
+      pair_sweep<T, 1, kK, kCount>(g, sl, bA, bB, nfc, us, kp, lane, ac, cnt);
+      __syncwarp();
+
+      // coefficients; the output terms go to the SDF body of each group
+      V3T<T> oAw = zero3t<T>(), oAv = oAw, oBw = oAw, oBv = oAw;
+      if (lane < nfc) {
+        Coef<T> cf;
+        V3T<T> ow, ov;
+        const int64_t row = pr.goff + c;
+        form_coef(sl.acc[lane], ybar + 8 * row, sl.spose[side], jvp ? jvp + 8 * row : nullptr, cf,
+                  ow, ov);
+        if (side == 0) { oBw = ow; oBv = ov; } else { oAw = ow; oAv = ov; }
+        sl.coef[lane] = cf;
+      }
+      __syncwarp();
+      pair_sweep<T, 2, kK, kCount>(g, sl, bA, bB, nfc, us, kp, lane, ac, cnt);
+
+      // chunk totals into the pair's accumulators
+      const T s[12] = {oAw.x, oAw.y, oAw.z, oAv.x, oAv.y, oAv.z,
+                       oBw.x, oBw.y, oBw.z, oBv.x, oBv.y, oBv.z};
+      for (int q = 0; q < 12; ++q) {
+        const T t = warp_sum_t(s[q]);
+        if (lane == 0) sl.pacc[6 + q] += t;
+      }
+      __syncwarp();
+    }
+    const V3T<T> Fs = v3(warp_sum_t(ac.F.x), warp_sum_t(ac.F.y), warp_sum_t(ac.F.z));
+    const V3T<T> Ms = v3(warp_sum_t(ac.M.x), warp_sum_t(ac.M.y), warp_sum_t(ac.M.z));
+    // groups without marks: zero output tangents
+    if (jvp)
+      for (int c0 = lane; c0 < ncand; c0 += 32)
+        if (!any_hit<T>(saved, pr.goff + c0)) {
+          float* o = jvp + 8 * (pr.goff + c0);
+          for (int q = 0; q < 8; ++q) o[q] = 0.f;
+        }
+    if (lane == 0) {
+      const T* a = sl.pacc;
+      write_twists(Fs, Ms, v3(a[6], a[7], a[8]), v3(a[9], a[10], a[11]), v3(a[12], a[13], a[14]),
+                   v3(a[15], a[16], a[17]), sl.tba[0], uA, uB, grad + 12 * pi,
+                   hvp ? hvp + 12 * pi : nullptr);
+    }
+  }
+  if (kCount) {
+    const unsigned long long v[8] = {cnt.dirs, cnt.live, cnt.maxp, cnt.gate,
+                                     cnt.g1, cnt.v1, cnt.h2, cnt.g2};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      unsigned long long x = v[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0) atomicAdd(counters + q, x);
+    }
+  }
+}
+
 // grad / hvp of pair p: the sum of its items' slots [item_off[p], item_off[p+1])
 // in index order.
 __global__ void bwd_reduce_kernel(const float* __restrict__ part,
@@ -1111,20 +1469,48 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part,
 }
 
 template <class T, int kK>
+static void launch_pair(const BwdLaunch& L, cudaStream_t stream) {
+  const int smem = bwd_slice_bytes<T>(L.us);
+  if (L.counters)
+    bwd_pair_kernel<T, kK, true><<<L.grid, 32, smem, stream>>>(
+        L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
+        L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, L.counters, L.sched);
+  else
+    bwd_pair_kernel<T, kK, false><<<L.grid, 32, smem, stream>>>(
+        L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
+        L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, nullptr, L.sched);
+}
+
+template <class T, int kK>
 static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
   if (L.counters)
     bwd_unit_kernel<T, kK, true><<<L.grid, 32, smem, stream>>>(
         L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b, L.ybar, L.dir,
-        L.saved, L.kp, L.us, L.part, L.jvp, L.counters);
+        L.saved, L.kp, L.us, L.part, L.jvp, L.counters, L.sched);
   else
     bwd_unit_kernel<T, kK, false><<<L.grid, 32, smem, stream>>>(
         L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b, L.ybar, L.dir,
-        L.saved, L.kp, L.us, L.part, L.jvp, nullptr);
+        L.saved, L.kp, L.us, L.part, L.jvp, nullptr, L.sched);
 }
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   const bool small_k = L.kp.trace_iters == 3;   // the paper's three steps: unrolled
+  if (L.sched) {
+    const cudaError_t e = cudaMemsetAsync(L.sched, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (L.saved && L.pair_order) {   // per pair, from the forward's record
+    if (L.dir) {
+      if (small_k) launch_pair<Dual, 3>(L, stream); else launch_pair<Dual, 0>(L, stream);
+    } else {
+      BwdLaunch M = L;
+      M.hvp = nullptr;
+      M.jvp = nullptr;
+      if (small_k) launch_pair<float, 3>(M, stream); else launch_pair<float, 0>(M, stream);
+    }
+    return cudaGetLastError();
+  }
   if (L.dir) {
     if (small_k) launch_unit<Dual, 3>(L, stream); else launch_unit<Dual, 0>(L, stream);
   } else {
@@ -1144,6 +1530,21 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
 
 // The limit is raised to the device's opt-in maximum, not to this shape's size:
 // the attribute is shared by every batch and captured graph of the process.
+template <class T, int kK>
+static cudaError_t configure_pair(int bytes, int smem_limit, int* per_sm) {
+  cudaError_t e = cudaSuccess;
+  if (bytes > 48 * 1024) {
+    e = cudaFuncSetAttribute(bwd_pair_kernel<T, kK, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bwd_pair_kernel<T, kK, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bwd_pair_kernel<T, kK, false>, 32,
+                                                       bytes);
+}
+
 template <class T, int kK>
 static cudaError_t configure_unit(int bytes, int smem_limit, int* per_sm) {
   cudaError_t e = cudaSuccess;
@@ -1165,7 +1566,16 @@ cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_
   if ((e = configure_unit<float, 0>(sf, smem_limit, &tmp)) != cudaSuccess) return e;
   if ((e = configure_unit<Dual, 0>(sd, smem_limit, &tmp)) != cudaSuccess) return e;
   if ((e = configure_unit<float, 3>(sf, smem_limit, per_sm_f)) != cudaSuccess) return e;
-  return configure_unit<Dual, 3>(sd, smem_limit, per_sm_d);
+  if ((e = configure_unit<Dual, 3>(sd, smem_limit, per_sm_d)) != cudaSuccess) return e;
+  // the per-pair kernels share the slices; their occupancy is no higher
+  int pf = 1, pd = 1;
+  if ((e = configure_pair<float, 0>(sf, smem_limit, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_pair<Dual, 0>(sd, smem_limit, &tmp)) != cudaSuccess) return e;
+  if ((e = configure_pair<float, 3>(sf, smem_limit, &pf)) != cudaSuccess) return e;
+  if ((e = configure_pair<Dual, 3>(sd, smem_limit, &pd)) != cudaSuccess) return e;
+  *per_sm_f = std::min(*per_sm_f, pf);
+  *per_sm_d = std::min(*per_sm_d, pd);
+  return cudaSuccess;
 }
 
 int backward_slice_bytes(const UnitShape& us, bool dual) {

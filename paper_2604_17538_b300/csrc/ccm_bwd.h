@@ -34,6 +34,8 @@ struct BwdLaunch {
   const float* ybar;    // [G, 8]
   const float* dir;     // [n, 12] or NULL
   const float* saved;   // [G, kSavedFloats] from the forward with these poses, or NULL
+  const int32_t* pair_order;   // pairs by decreasing cost: with `saved`, run per pair
+                               // (every SDF body <= kHitS pieces), else NULL
   KParams kp;
   UnitShape us;
   float* part;          // [n_items, 24] per-item slots (workspace)
@@ -41,6 +43,7 @@ struct BwdLaunch {
   float* hvp;           // [n, 12] or NULL
   float* jvp;           // [G, 8] or NULL
   unsigned long long* counters;   // optional work counters (CCM_BWD_CNT_*)
+  int* sched;                     // optional work counter (device int), zeroed by the launch
   int grid;
 };
 

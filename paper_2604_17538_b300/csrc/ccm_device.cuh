@@ -60,6 +60,23 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr unsigned kFull = 0xffffffffu;
 
+// Next work unit of a warp: a shared counter (zeroed before the launch) hands
+// out units in order, so warps that drew light units take more of them and
+// the heaviest-first order finishes together; without a counter the units are
+// dealt round-robin from `first` in steps of `stride`.
+__device__ __forceinline__ int64_t next_unit(int* sched, int64_t prev, int64_t stride) {
+  if (!sched) return prev + stride;
+  int v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(sched, 1);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ int64_t first_unit(int* sched, int64_t first) {
+  if (!sched) return first;
+  int v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(sched, 1);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
 // 2^x on the SFU (hand-written PTX; flushes denormal results to zero).
 __device__ __forceinline__ float ex2(float x) {
   float y;

@@ -209,7 +209,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, float* __restrict__ saved,
-                unsigned long long* __restrict__ counters) {
+                unsigned long long* __restrict__ counters, int* __restrict__ sched) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -221,7 +221,8 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
   FwdCounts cnt;
 
   // heaviest items first, dealt round-robin to the warps (balanced, no atomics)
-  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < n_run; k += nwarps) {
+  for (int64_t k = first_unit(sched, (int64_t)blockIdx.x * (blockDim.x >> 5) + warp); k < n_run;
+       k = next_unit(sched, k, nwarps)) {
     const WorkItem it = items[order[k]];
     const int64_t u = it.unit;
     const int64_t pi = u >> 1;
@@ -342,14 +343,18 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 }
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
+  if (L.sched) {
+    const cudaError_t e = cudaMemsetAsync(L.sched, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = (size_t)L.us.warps * L.us.slice_bytes;
   const int threads = 32 * L.us.warps;
   if (L.counters)
     unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters);
+                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched);
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters);
+                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ struct FwdLaunch {
   float* y;
   float* saved;                   // optional [G, kSavedFloats] for the reverse pass
   unsigned long long* counters;   // optional work counters (CCM_CNT_*)
+  int* sched;                     // optional work counter (device int), zeroed by the launch
   int grid;
 };
 

@@ -60,6 +60,9 @@ struct Batch {
   DevBuf d_item_order;           // item indices by decreasing estimated cost
   DevBuf d_item_off;             // [n + 1] items of each pair
   DevBuf d_part;                 // [n_items, 24] per-item slots of the reverse pass
+  DevBuf d_pair_order;           // pairs by decreasing cost (per-pair reverse pass)
+  bool per_pair = false;         // every body has <= kHitS pieces
+  DevBuf d_sched;                // [2] work counters of the forward and reverse launches
   BatchMaxima mx;
   ccm_tuning tuning{};
   UnitShape us{};

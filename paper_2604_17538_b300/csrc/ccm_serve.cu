@@ -41,6 +41,7 @@ struct ReqDesc {
 struct WaveCounts {
   int64_t n_pairs, n_items_f, n_items_b, n_req;
   int64_t e_in, e_out;   // elements gathered / scattered in total
+  int64_t n_pairs_b;     // pairs of the gradient requests (per-pair reverse pass)
 };
 
 // Cost class of a work item: four classes per octave of its estimated cost.
@@ -57,6 +58,7 @@ struct Pending {
   std::vector<PairRec> pairs;     // goff relative to the request
   std::vector<WorkItem> items;    // units relative to the request's first pair
   std::vector<uint8_t> cls;       // cost class per item (see cost_class)
+  std::vector<uint8_t> pcls;      // cost class per pair (sum of its items' costs)
   std::vector<int64_t> item_off;  // [n + 1], from 0
   ReqDesc d;
 };
@@ -77,13 +79,14 @@ struct WaveSet {
   cudaEvent_t t0 = nullptr;              // start of the wave's graph
   cudaGraphExec_t graph_f = nullptr;    // gather, forward, scatter
   cudaGraphExec_t graph_fb = nullptr;   // gather, forward, reverse pass, scatter
-  DevBuf d_pairs, d_items, d_order_f, d_order_b, d_item_off, d_reqs, d_counts, d_pose_a,
-      d_pose_b, d_y, d_ybar, d_part, d_grad, d_saved;
+  DevBuf d_pairs, d_items, d_order_f, d_order_b, d_item_off, d_porder, d_reqs, d_counts, d_pose_a,
+      d_pose_b, d_y, d_ybar, d_part, d_grad, d_saved, d_sched;
   PairRec* h_pairs = nullptr;
   WorkItem* h_items = nullptr;
   int32_t* h_order_f = nullptr;
   int32_t* h_order_b = nullptr;
   int64_t* h_item_off = nullptr;
+  int32_t* h_porder = nullptr;
   ReqDesc* h_reqs = nullptr;
   WaveCounts* h_counts = nullptr;
   std::vector<uint64_t> tickets;
@@ -99,6 +102,7 @@ struct Serving {
   int fwd_grid = 1, bwd_grid = 1;
   int64_t cap_pairs = 0, cap_groups = 0, cap_req = 0, cap_items = 0;
   BatchMaxima mx;                  // largest pieces the launch shape holds
+  bool per_pair = false;           // per-pair reverse pass (every body <= kHitS pieces)
   std::vector<int8_t> fit_cache;   // per body: -1 unknown, 0 no, 1 yes (ctx->mu held)
   WaveSet sets[2];
   std::thread worker;
@@ -119,7 +123,8 @@ struct Serving {
     if ((size_t)b >= fit_cache.size()) fit_cache.resize(c.bodies.size(), -1);
     if (fit_cache[b] < 0) {
       const BatchMaxima m = body_maxima(c, b);
-      fit_cache[b] = m.vmax <= mx.vmax && m.fmax <= mx.fmax && m.emax <= mx.emax;
+      fit_cache[b] = m.vmax <= mx.vmax && m.fmax <= mx.fmax && m.emax <= mx.emax &&
+                     (!per_pair || m.s_pieces <= kHitS);
     }
     return fit_cache[b] == 1;
   }
@@ -194,7 +199,7 @@ static ccm_status alloc_buf(DevBuf& b, int64_t count, const char* what) {
 // per pair the pair record, item offset, two poses and the gradient; per work
 // item its record, two order entries and its reverse-pass slot; per group the
 // outputs and cotangents.
-constexpr int64_t kBytesPerPair = (int64_t)sizeof(PairRec) + 8 + 2 * 12 * 4 + 12 * 4;
+constexpr int64_t kBytesPerPair = (int64_t)sizeof(PairRec) + 8 + 4 + 2 * 12 * 4 + 12 * 4;
 constexpr int64_t kBytesPerItem = (int64_t)sizeof(WorkItem) + 2 * 4 + 24 * 4;
 constexpr int64_t kBytesPerGroup = 2 * 8 * 4 + CCM_SAVED_FLOATS * 4;
 
@@ -223,6 +228,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   F.y = static_cast<float*>(s.d_y.ptr);
   F.saved = reverse ? static_cast<float*>(s.d_saved.ptr) : nullptr;
   F.counters = nullptr;
+  F.sched = static_cast<int*>(s.d_sched.ptr);
   F.grid = sv->fwd_grid;
   launch_forward(F, s.stream);
   BwdLaunch B;
@@ -234,7 +240,8 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   B.item_off = static_cast<const int64_t*>(s.d_item_off.ptr);
   B.n_pairs = sv->cap_pairs;
   B.dev_items = &static_cast<const int64_t*>(s.d_counts.ptr)[2];
-  B.dev_pairs = &static_cast<const int64_t*>(s.d_counts.ptr)[0];
+  B.dev_pairs = &static_cast<const int64_t*>(s.d_counts.ptr)[sv->per_pair ? 6 : 0];
+  B.pair_order = sv->per_pair ? static_cast<const int32_t*>(s.d_porder.ptr) : nullptr;
   B.pose_a = F.pose_a;
   B.pose_b = F.pose_b;
   B.ybar = static_cast<const float*>(s.d_ybar.ptr);
@@ -247,6 +254,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   B.hvp = nullptr;
   B.jvp = nullptr;
   B.counters = nullptr;
+  B.sched = static_cast<int*>(s.d_sched.ptr) + 1;
   B.grid = sv->bwd_grid;
   if (reverse) launch_backward(B, s.stream);
   serve_scatter<<<sv->ctx->n_sm * 4, 256, 0, s.stream>>>(
@@ -261,6 +269,7 @@ static ccm_status setup_set(Serving* sv, WaveSet& s) {
   if ((st = alloc_buf<int32_t>(s.d_order_f, I, "wave order")) != CCM_OK) return st;
   if ((st = alloc_buf<int32_t>(s.d_order_b, I, "wave order")) != CCM_OK) return st;
   if ((st = alloc_buf<int64_t>(s.d_item_off, P + 1, "wave item offsets")) != CCM_OK) return st;
+  if ((st = alloc_buf<int32_t>(s.d_porder, P, "wave pair order")) != CCM_OK) return st;
   if ((st = alloc_buf<ReqDesc>(s.d_reqs, R, "wave requests")) != CCM_OK) return st;
   if ((st = alloc_buf<WaveCounts>(s.d_counts, 1, "wave counts")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_pose_a, 12 * P, "wave poses")) != CCM_OK) return st;
@@ -268,6 +277,7 @@ static ccm_status setup_set(Serving* sv, WaveSet& s) {
   if ((st = alloc_buf<float>(s.d_y, 8 * G, "wave outputs")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_ybar, 8 * G, "wave cotangents")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_saved, CCM_SAVED_FLOATS * G, "wave records")) != CCM_OK) return st;
+  if ((st = alloc_buf<int32_t>(s.d_sched, 2, "wave work counters")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_part, 24 * I, "wave slots")) != CCM_OK) return st;
   if ((st = alloc_buf<float>(s.d_grad, 12 * P, "wave gradients")) != CCM_OK) return st;
   if (cudaMallocHost(&s.h_pairs, sizeof(PairRec) * P) != cudaSuccess ||
@@ -275,6 +285,7 @@ static ccm_status setup_set(Serving* sv, WaveSet& s) {
       cudaMallocHost(&s.h_order_f, 4 * I) != cudaSuccess ||
       cudaMallocHost(&s.h_order_b, 4 * I) != cudaSuccess ||
       cudaMallocHost(&s.h_item_off, 8 * (P + 1)) != cudaSuccess ||
+      cudaMallocHost(&s.h_porder, 4 * P) != cudaSuccess ||
       cudaMallocHost(&s.h_reqs, sizeof(ReqDesc) * R) != cudaSuccess ||
       cudaMallocHost(&s.h_counts, sizeof(WaveCounts)) != cudaSuccess)
     return fail(CCM_ERR_OOM, "pinned staging buffers");
@@ -303,12 +314,12 @@ static void release_set(WaveSet& s) {
   if (s.done) cudaEventDestroy(s.done);
   if (s.t0) cudaEventDestroy(s.t0);
   if (s.stream) cudaStreamDestroy(s.stream);
-  for (DevBuf* b : {&s.d_pairs, &s.d_items, &s.d_order_f, &s.d_order_b, &s.d_item_off,
+  for (DevBuf* b : {&s.d_pairs, &s.d_items, &s.d_order_f, &s.d_order_b, &s.d_item_off, &s.d_porder,
                     &s.d_reqs, &s.d_counts, &s.d_pose_a, &s.d_pose_b, &s.d_y, &s.d_ybar,
-                    &s.d_part, &s.d_grad, &s.d_saved})
+                    &s.d_part, &s.d_grad, &s.d_saved, &s.d_sched})
     b->release();
   for (void* p : {(void*)s.h_pairs, (void*)s.h_items, (void*)s.h_order_f, (void*)s.h_order_b,
-                  (void*)s.h_item_off, (void*)s.h_reqs, (void*)s.h_counts})
+                  (void*)s.h_item_off, (void*)s.h_porder, (void*)s.h_reqs, (void*)s.h_counts})
     if (p) cudaFreeHost(p);
   s = WaveSet();
 }
@@ -411,7 +422,26 @@ static void launch_wave(Serving* sv, WaveSet& s, std::unique_lock<std::mutex>& l
       base += ni;
     }
   }
-  *s.h_counts = WaveCounts{P, nf, nb, R, EI, EO};
+  // the gradient requests' pairs by cost class, heaviest first
+  int64_t npb = 0;
+  {
+    int64_t cnt_p[kCostClasses] = {0};
+    for (const Pending& q : take)
+      if (q.d.ybar)
+        for (uint8_t c : q.pcls) ++cnt_p[c];
+    for (int c = kCostClasses - 1; c >= 0; --c) {
+      const int64_t a = cnt_p[c];
+      cnt_p[c] = npb;
+      npb += a;
+    }
+    int64_t base = 0;
+    for (const Pending& q : take) {
+      if (q.d.ybar)
+        for (int64_t i = 0; i < q.d.n; ++i) s.h_porder[cnt_p[q.pcls[i]]++] = (int32_t)(base + i);
+      base += q.d.n;
+    }
+  }
+  *s.h_counts = WaveCounts{P, nf, nb, R, EI, EO, npb};
   cudaError_t e = cudaSuccess;
   auto copy = [&](void* dst, const void* src, size_t bytes) {
     if (bytes && e == cudaSuccess)
@@ -420,6 +450,7 @@ static void launch_wave(Serving* sv, WaveSet& s, std::unique_lock<std::mutex>& l
   copy(s.d_pairs.ptr, s.h_pairs, sizeof(PairRec) * P);
   copy(s.d_items.ptr, s.h_items, sizeof(WorkItem) * I);
   copy(s.d_item_off.ptr, s.h_item_off, 8 * (P + 1));
+  copy(s.d_porder.ptr, s.h_porder, 4 * npb);
   copy(s.d_order_f.ptr, s.h_order_f, 4 * nf);
   copy(s.d_order_b.ptr, s.h_order_b, 4 * nb);
   copy(s.d_reqs.ptr, s.h_reqs, sizeof(ReqDesc) * R);
@@ -552,6 +583,7 @@ ccm_status ccm_serve_start(ccm_ctx ctx, const ccm_serve_config* cfg) {
     }
     sv->mx = probe.mx;
     sv->us = probe.us;
+    sv->per_pair = probe.mx.s_pieces <= kHitS;
     std::vector<WorkItem> items;
     std::vector<int64_t> cost, off(1, 0);
     {
@@ -641,6 +673,12 @@ ccm_status ccm_submit(ccm_ctx ctx, const ccm_request* req, ccm_ticket* out) {
     p.item_off.assign(1, 0);
     std::vector<int64_t> cost;
     make_items(*c, p.pairs.data(), req->n_pairs, 0, sv->us, &p.items, &cost, &p.item_off);
+    p.pcls.resize(req->n_pairs);
+    for (int64_t i = 0; i < req->n_pairs; ++i) {
+      int64_t pc = 0;
+      for (int64_t j = p.item_off[i]; j < p.item_off[i + 1]; ++j) pc += cost[j];
+      p.pcls[i] = cost_class(pc);
+    }
     p.cls.resize(cost.size());
     for (size_t j = 0; j < cost.size(); ++j) p.cls[j] = cost_class(cost[j]);
   }
