@@ -386,12 +386,21 @@ template <class T> __device__ __forceinline__ V3T<T> cross3(V3T<T> a, V3T<T> b) 
 __device__ __forceinline__ float tan_of(float) { return 0.f; }
 __device__ __forceinline__ float tan_of(Dual a) { return a.d; }
 
+// List memo of the per-pair reverse pass: when a chunk of groups fits one
+// S chunk and one list, the adjoint sweep reuses the recompute sweep's lists
+// (same directions, same budgets, so the same lists) instead of rebuilding
+// them, and visits only the vertices and edges whose contact had f > 0 (plus
+// the corners such edges start their traces from): the others have a zero
+// adjoint.  Layout (ints): S chunks, lists, nd, TV, TE, n_v, n_e, unused,
+// then the vertex-item bits, then the edge-item bits.
+constexpr int kMemoHead = 8;
+
 // ---------------------------------------------------------------------------
 // slice of the backward kernel (per warp)
 // ---------------------------------------------------------------------------
 template <class T> struct BwdSlice {
   float4* planes;     // [plane_budget]
-  int2* sp;           // [spiece_budget]
+  int2* sp;           // [2 spiece_budget] (both bodies in the per-pair pass)
   V3T<T>* xs;         // [vert_budget] F vertices in the S frame
   uint32_t* edges;    // [edge_budget]
   int4* fp;           // [32]
@@ -414,6 +423,7 @@ template <class T> struct BwdSlice {
   V3T<T>* tba;        // [1] t_B - t_A
   T* pacc;            // [18] pair totals: F, M (about t_A), output terms of A and B
   PoseT<T>* rel;      // [2] relative pose S <- F of side 0 and side 1
+  int* memo;          // list memo of the per-pair pass (see ListMemo)
   uint32_t* hit;      // [groups * kHitWords] directions that gave a contact in pass 1
 };
 
@@ -422,12 +432,14 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
   int b = 0;
   b += align16i(4 * u.groups);
   b += align16i((int)sizeof(PoseT<T>) * 2);
+  b += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
   b += align16i((int)sizeof(V3T<T>));
   b += align16i((int)sizeof(T) * 18);
   b += align16i((int)sizeof(PoseT<T>) * 2);
+  b += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
   b += align16i(4 * kHitWords * u.groups);
   b += 16 * u.plane_budget;
-  b += align16i(8 * u.spiece_budget);
+  b += align16i(8 * 2 * u.spiece_budget);
   b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   b += align16i(4 * u.edge_budget);
   b += 16 * u.groups * 2;
@@ -452,9 +464,11 @@ template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, con
   s.tba = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>));
   s.pacc = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * 18);
   s.rel = reinterpret_cast<PoseT<T>*>(p);       p += align16i((int)sizeof(PoseT<T>) * 2);
+  s.memo = reinterpret_cast<int*>(p);
+  p += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
   s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * kHitWords * u.groups);
   s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
-  s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * u.spiece_budget);
+  s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * 2 * u.spiece_budget);
   s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   s.edges = reinterpret_cast<uint32_t*>(p);    p += align16i(4 * u.edge_budget);
   s.fp = reinterpret_cast<int4*>(p);           p += 16 * u.groups;
@@ -647,8 +661,58 @@ struct BwdCounts {
 
 template <class T, int kPass, int kK, bool kCount>
 __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int sc0,
-                             const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt) {
+                             const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt,
+                             int* memo, bool reuse) {
   const int* dsub = sl.dsub;
+  uint32_t* vbits = memo ? reinterpret_cast<uint32_t*>(memo + kMemoHead) : nullptr;
+  uint32_t* ebits = nullptr;
+  int n_e = 0, n_v = 0;
+  const uint16_t* vl = sl.vlist;
+  if (memo) ebits = vbits + memo[7];
+  if (reuse) {
+    // the recompute sweep's single list: keep the contributing edges (in
+    // place, in order) and the vertices that contributed or start a kept trace
+    nd = memo[2];
+    TV = memo[3];
+    TE = memo[4];
+    const int nv0 = memo[5], ne0 = memo[6];
+    for (int t = lane; t < TV; t += 32) sl.need[t] = 0;
+    __syncwarp();
+    for (int k0 = 0; k0 < ne0; k0 += 32) {
+      const int k = k0 + lane;
+      bool keep = false;
+      int t = 0;
+      if (k < ne0) {
+        t = sl.elist[k];
+        keep = (ebits[k >> 5] >> (k & 31)) & 1u;
+        if (keep) {
+          const int r = find_dir(sl.pe, nd, t);
+          const int4 f = sl.fp[dsub[r] >> 16];
+          const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+          sl.need[sl.pv[r] + (e & 0xffff)] = 1;
+          sl.need[sl.pv[r] + (e >> 16)] = 1;
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) sl.elist[n_e + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+      n_e += __popc(bal);
+    }
+    __syncwarp();
+    for (int k0 = 0; k0 < nv0; k0 += 32) {
+      const int k = k0 + lane;
+      bool keep = false;
+      int t = 0;
+      if (k < nv0) {
+        t = sl.vlist[k];
+        keep = ((vbits[k >> 5] >> (k & 31)) & 1u) || sl.need[t];
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) sl.am[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+      n_v += __popc(bal);
+    }
+    vl = sl.am;
+    __syncwarp();
+  } else {
   for (int t = lane; t < TV; t += 32) {
     const int r = find_dir(sl.pv, nd, t);
     const int code = dsub[r];
@@ -662,7 +726,6 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
     if (kCount) cnt.maxp += s.y;
   }
   __syncwarp();
-  int n_e = 0;
   for (int t0 = 0; t0 < TE; t0 += 32) {
     const int t = t0 + lane;
     bool live = false;
@@ -685,7 +748,6 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
     n_e += __popc(bal);
   }
   __syncwarp();
-  int n_v = 0;
   for (int t0 = 0; t0 < TV; t0 += 32) {
     const int t = t0 + lane;
     const bool live = t < TV && (sl.m[t] < kp.d_max || sl.need[t]);
@@ -694,14 +756,20 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
     n_v += __popc(bal);
   }
   __syncwarp();
+  if (memo && kPass == 1 && lane == 0) {
+    memo[1] += 1;
+    memo[2] = nd; memo[3] = TV; memo[4] = TE; memo[5] = n_v; memo[6] = n_e;
+  }
+  }
   // vertices
   for (int k0 = 0; k0 < n_v; k0 += 32) {
     const int k = k0 + lane;
     PartT<T> c;
     part_zero(c);
     int key = 0xffff;
+    bool contrib = false;
     if (k < n_v) {
-      const int t = sl.vlist[k];
+      const int t = vl[k];
       const int r = find_dir(sl.pv, nd, t);
       const int code = dsub[r];
       const int g = code >> 16;
@@ -720,6 +788,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
           const T dc = fma_t(w, e.phi - kp.d_max, T(kp.d_max));
           part_from_contact(c, w, dc, x, e.g, kp.c_blend);
           mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
+          contrib = val(w) > 0.f;
         }
       } else {
         const Coef<T>& cf = sl.coef[g];
@@ -729,7 +798,13 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         if (m < kp.d_max && cf.live) add_force(ac, sl, g, x, contact_adjoint(e, x, cf, kp));
       }
     }
-    if (kPass == 1) fold_t(c, key, sl.acc, lane);
+    if (kPass == 1) {
+      if (memo) {
+        const unsigned cb = __ballot_sync(kFull, contrib);
+        if (lane == 0) vbits[k0 >> 5] = cb;
+      }
+      fold_t(c, key, sl.acc, lane);
+    }
   }
   __syncwarp();
   // edges
@@ -738,6 +813,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
     PartT<T> c;
     part_zero(c);
     int key = 0xffff;
+    bool contrib = false;
     if (k < n_e) {
       const int t = sl.elist[k];
       const int r = find_dir(sl.pe, nd, t);
@@ -764,6 +840,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         const T dc = fma_t(w, sc.phi - kp.d_max, T(kp.d_max));
         part_from_contact(c, w, dc, pe, sc.g, kp.c_blend);
         mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
+        contrib = val(w) > 0.f;
       } else if (cf.live) {
         if (kCount) { cnt.h2 += s.y; cnt.g2 += (unsigned long long)steps * s.y; }
         edge_t<T, true, kK>(sl.planes + s.x, s.y, a, b, sl.m[t0v], sl.m[t1v], sl.phi[t0v],
@@ -772,14 +849,21 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         add_force(ac, sl, g, b, xbII);
       }
     }
-    if (kPass == 1) fold_t(c, key, sl.acc, lane);
+    if (kPass == 1) {
+      if (memo) {
+        const unsigned cb = __ballot_sync(kFull, contrib);
+        if (lane == 0) ebits[k0 >> 5] = cb;
+      }
+      fold_t(c, key, sl.acc, lane);
+    }
   }
   __syncwarp();
 }
 
 template <class T, int kPass, int kK, bool kCount>
 __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, int sc0, const UnitShape& us,
-                                const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt) {
+                                const KParams& kp, int lane, Accum<T>& ac, BwdCounts& cnt,
+                                int* memo = nullptr) {
   int start = 0;
   while (start < np) {
     const int r = start + lane;
@@ -806,7 +890,7 @@ __device__ void bwd_run_pending(const BwdSlice<T>& sl, int np, int sc0, const Un
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
     if (kCount && lane == 0) cnt.live += nd;
-    bwd_run_list<T, kPass, kK, kCount>(sl, nd, TV, TE, sc0, kp, lane, ac, cnt);
+    bwd_run_list<T, kPass, kK, kCount>(sl, nd, TV, TE, sc0, kp, lane, ac, cnt, memo, false);
     start += nd;
   }
 }
@@ -1167,6 +1251,17 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
                            const BodyRec& bB, int nfc, const UnitShape& us, const KParams& kp,
                            int lane, Accum<T>& ac, BwdCounts& cnt) {
   const int npB = bB.np, nS = bA.np + bB.np;
+  int* memo = sl.memo;
+  if (kPass == 2 && memo[0] == 1 && memo[1] == 1) {
+    // one S chunk and one list in the recompute sweep: its planes and its
+    // list are still staged; visit only the contributing contacts
+    bwd_run_list<T, 2, kK, kCount>(sl, 0, 0, 0, kNoMark, kp, lane, ac, cnt, memo, true);
+    return;
+  }
+  if (kPass == 1) {
+    if (lane == 0) { memo[0] = 0; memo[1] = 0; memo[7] = (us.item_vb + 31) / 32; }
+    __syncwarp();
+  }
   // does some group of the matching side mark S index si?
   auto needed = [&](int si) {
     const int side = si < npB ? 0 : 1;
@@ -1177,13 +1272,14 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
     return ((any >> (b & 31)) & 1u) != 0u;
   };
   for (int sc0 = 0; sc0 < nS;) {
-    // the chunk [sc0, sc1): at most spiece_budget indices whose needed
-    // pieces' planes fit plane_budget; stage those planes, packed
+    // the chunk [sc0, sc1): at most 2 spiece_budget indices (a piece budget
+    // for each body) whose needed pieces' planes fit plane_budget; stage
+    // those planes, packed
     int sc1 = sc0, P = 0;
     __syncwarp();
-    while (sc1 < nS && sc1 - sc0 < us.spiece_budget) {
+    while (sc1 < nS && sc1 - sc0 < 2 * us.spiece_budget) {
       const int si = sc1 + lane;
-      const bool valid = si < nS && si - sc0 < us.spiece_budget;
+      const bool valid = si < nS && si - sc0 < 2 * us.spiece_budget;
       int nf = 0, f0 = 0;
       if (valid && needed(si)) {
         const PieceRec p = g.pieces[si < npB ? bB.p0 + si : bA.p0 + (si - npB)];
@@ -1213,6 +1309,7 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
       if (take < 32) break;
     }
     __syncwarp();
+    if (kPass == 1 && lane == 0) memo[0] += 1;
     if (sc1 == sc0) break;   // unreachable: every piece fits the plane budget
     if (P == 0) {            // no marked direction in this chunk
       sc0 = sc1;
@@ -1239,14 +1336,14 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
       const unsigned bal = __ballot_sync(kFull, live);
       const int nl = __popc(bal);
       if (np + nl > kPending) {
-        bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt);
+        bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt, memo);
         np = 0;
       }
       if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
       np += nl;
       __syncwarp();
     }
-    if (np > 0) bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt);
+    if (np > 0) bwd_run_pending<T, kPass, kK, kCount>(sl, np, kNoMark, us, kp, lane, ac, cnt, memo);
     sc0 = sc1;
   }
 }
