@@ -56,8 +56,41 @@ struct FwdCounts {
 template <bool kCount>
 __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE, int sc0,
                          const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
-  // exact max-plane value of every (direction, vertex) item
-  for (int t = lane; t < TV; t += 32) {
+  // max-plane value of every (direction, vertex) item.  First one plane: the
+  // plane attaining the max at the feature piece's centre (from the gate) is
+  // far above d_max at the vertices on the far side of the piece, and its
+  // value is a lower bound of the max-plane value, so those vertices are
+  // culled exactly; the others (packed into vlist, used here as scratch) get
+  // the exact max over all planes
+  int nfull = 0;
+  for (int t0 = 0; t0 < TV; t0 += 32) {
+    const int t = t0 + lane;
+    bool full = false;
+    if (t < TV) {
+      const int r = find_dir(sl.pv, nd, t);
+      const int code = dsub[r];
+      const int4 f = sl.fp[code >> 16];
+      const int2 s = sl.sp[code & 0xffff];
+      const float4 x = sl.xs[f.x + t - sl.pv[r]];
+      const int j = sl.dsubpl[r];
+      const float4 pj = sl.planes[s.x + j];
+      const float vj = fmaf(pj.x, x.x, fmaf(pj.y, x.y, fmaf(pj.z, x.z, pj.w)));
+      sl.need[t] = 0;
+      if (!no_cull && vj >= kp.d_max) {
+        sl.m[t] = vj;
+        sl.am[t] = (uint16_t)j;
+        if (kCount) cnt.maxp += 1;
+      } else {
+        full = true;
+      }
+    }
+    const unsigned bal = __ballot_sync(kFull, full);
+    if (full) sl.vlist[nfull + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+    nfull += __popc(bal);
+  }
+  __syncwarp();
+  for (int k = lane; k < nfull; k += 32) {
+    const int t = sl.vlist[k];
     const int r = find_dir(sl.pv, nd, t);
     const int code = dsub[r];
     const int4 f = sl.fp[code >> 16];
@@ -66,7 +99,6 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
     int arg;
     sl.m[t] = max_plane_arg(sl.planes + s.x, s.y, x.x, x.y, x.z, arg);
     sl.am[t] = (uint16_t)arg;
-    sl.need[t] = 0;
     if (kCount) cnt.maxp += s.y;
   }
   __syncwarp();
@@ -174,9 +206,10 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, con
   int start = 0;
   while (start < np) {
     const int r = start + lane;
-    int nvr = 0, ner = 0, code = 0;
+    int nvr = 0, ner = 0, code = 0, pl = 0;
     if (r < np) {
       code = sl.dir[r];
+      pl = sl.dpl[r];
       const int4 f = sl.fp[code >> 16];
       nvr = f.y;
       ner = f.w;
@@ -191,6 +224,7 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, con
     const int nd = __popc(__ballot_sync(kFull, fits));   // >= 1: budgets hold any one piece
     if (lane < nd) {
       dsub[lane] = code;
+      sl.dsubpl[lane] = pl;
       sl.pv[lane] = iv - nvr;
       sl.pe[lane] = ie - ner;
       if (kCount) { cnt.live += 1; cnt.feat += nvr + ner; }
@@ -292,12 +326,12 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         for (int d0 = 0; d0 < ndir; d0 += 32) {
           const int d = d0 + lane;
           bool live = false;
-          int code = 0;
+          int code = 0, pl = 0;
           if (d < ndir) {
             const int fcd = d / nsc, scd = d - fcd * nsc;
             const float4 c = sl.fs[fcd];
             const int2 s = sl.sp[scd];
-            const float mc = max_plane(sl.planes + s.x, s.y, c.x, c.y, c.z);
+            const float mc = max_plane_arg(sl.planes + s.x, s.y, c.x, c.y, c.z, pl);
             live = no_cull || mc - c.w - margin < kp.d_max;
             code = (fcd << 16) | scd;
             if (kCount) { cnt.dirs += 1; cnt.gate += s.y; }
@@ -308,7 +342,11 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
             run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt);
             np = 0;
           }
-          if (live) sl.dir[np + __popc(bal & ((1u << lane) - 1u))] = code;
+          if (live) {
+            const int at = np + __popc(bal & ((1u << lane) - 1u));
+            sl.dir[at] = code;
+            sl.dpl[at] = pl;
+          }
           np += nl;
           __syncwarp();
         }

@@ -48,6 +48,8 @@ struct UnitSlice {
   uint32_t* hit;      // [groups * kHitWords] directions that gave a contact
   int* dir;           // [32] pending live directions: fc << 16 | sc
   int* dsub;          // [32] directions of the list being run
+  int* dpl;           // [32] per pending direction: a plane attaining the gate's max
+  int* dsubpl;        // [32] the same for the list being run
   int* pv;            // [33] prefix of vertex items per pending direction
   int* pe;            // [33] prefix of edge items
   float* m;           // [item_v] max-plane value per (direction, vertex)
@@ -74,7 +76,7 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += 16 * u.groups;                        // fs
   b += align16i((int)sizeof(PartT<float>) * u.groups);   // acc
   b += align16i(4 * kHitWords * u.groups);   // hit
-  b += align16i(4 * kPending) * 2;           // dir, dsub
+  b += align16i(4 * kPending) * 4;           // dir, dsub, dpl, dsubpl
   b += align16i(4 * (kPending + 1)) * 2;     // pv, pe
   b += align16i(4 * u.item_v) * 2;           // m, phi
   b += align16i(2 * u.item_v);               // vlist
@@ -96,6 +98,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.hit = reinterpret_cast<uint32_t*>(p);            p += align16i(4 * kHitWords * u.groups);
   s.dir = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);                p += align16i(4 * kPending);
+  s.dpl = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
+  s.dsubpl = reinterpret_cast<int*>(p);              p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));
   s.pe = reinterpret_cast<int*>(p);                  p += align16i(4 * (kPending + 1));
   s.m = reinterpret_cast<float*>(p);                 p += align16i(4 * u.item_v);
