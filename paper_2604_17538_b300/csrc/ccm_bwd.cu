@@ -944,7 +944,7 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
           m &= m - 1;
           const int o_l = __shfl_sync(kFull, off, l), n_l = __shfl_sync(kFull, nf, l),
                     f_l = __shfl_sync(kFull, f0, l);
-          for (int k = lane; k < n_l; k += 32) sl.planes[o_l + k] = g.planes[f_l + k];
+          stage_copy(sl.planes + o_l, g.planes + f_l, n_l, lane);
         }
         base += __shfl_sync(kFull, incl, 31);
       }
@@ -959,7 +959,7 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
         const PieceRec p = g.pieces[S.p0 + sc0 + q];
         sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
       }
-      for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
+      stage_copy(sl.planes, g.planes + f_first, P, lane);
       __syncwarp();
     }
     int np = 0;
@@ -1172,7 +1172,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
             const V3T<T> x = rot(Rr, v3(T(v.x), T(v.y), T(v.z)));
             sl.xs[vo + i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
           }
-          for (int j = lane; j < en; j += 32) sl.edges[eo + j] = g.edges[e0 + j];
+          stage_copy(sl.edges + eo, g.edges + e0, en, lane);
         }
       } else {
         for (int i = lane; i < V; i += 32) {
@@ -1181,7 +1181,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           const V3T<T> x = rot(Rr, vv);
           sl.xs[i] = v3(x.x + tr[0], x.y + tr[1], x.z + tr[2]);
         }
-        for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
+        stage_copy(sl.edges, g.edges + pfirst.e0, E, lane);
       }
       __syncwarp();
 
@@ -1302,7 +1302,7 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
         m &= m - 1;
         const int o_l = P + __shfl_sync(kFull, incl - nf, l), n_l = __shfl_sync(kFull, nf, l),
                   f_l = __shfl_sync(kFull, f0, l);
-        for (int k = lane; k < n_l; k += 32) sl.planes[o_l + k] = g.planes[f_l + k];
+        stage_copy(sl.planes + o_l, g.planes + f_l, n_l, lane);
       }
       if (take > 0) P += __shfl_sync(kFull, incl, take - 1);
       sc1 += take;
@@ -1484,7 +1484,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
           const V3T<T> x = rot(r.R, v3(T(v.x), T(v.y), T(v.z)));
           sl.xs[vo + i] = v3(x.x + r.t[0], x.y + r.t[1], x.z + r.t[2]);
         }
-        for (int j = lane; j < en; j += 32) sl.edges[eo + j] = g.edges[e0 + j];
+        stage_copy(sl.edges + eo, g.edges + e0, en, lane);
       }
       __syncwarp();
 

@@ -191,28 +191,61 @@ __device__ __forceinline__ void sdf_val2(const float4* __restrict__ pl, int nf, 
 // exact largest plane value at x (the hard polytope "depth" max_k phi_k)
 __device__ __forceinline__ float max_plane(const float4* __restrict__ pl, int nf, float x, float y,
                                            float z) {
-  float mx = -INFINITY;
-#pragma unroll 4
-  for (int k = 0; k < nf; ++k) {
-    const float4 p = pl[k];
-    mx = fmaxf(mx, fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w))));
+  // two running maxima (even / odd planes) halve the dependency chain
+  float m0 = -INFINITY, m1 = -INFINITY;
+  int k = 0;
+#pragma unroll 2
+  for (; k + 1 < nf; k += 2) {
+    const float4 p = pl[k], q = pl[k + 1];
+    m0 = fmaxf(m0, fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w))));
+    m1 = fmaxf(m1, fmaf(q.x, x, fmaf(q.y, y, fmaf(q.z, z, q.w))));
   }
-  return mx;
+  if (k < nf) {
+    const float4 p = pl[k];
+    m0 = fmaxf(m0, fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w))));
+  }
+  return fmaxf(m0, m1);
 }
 
-// largest plane value at x and the index of a plane attaining it
+// largest plane value at x and the lowest index of a plane attaining it
 __device__ __forceinline__ float max_plane_arg(const float4* __restrict__ pl, int nf, float x,
                                                float y, float z, int& arg) {
-  float mx = -INFINITY;
-  int am = 0;
-#pragma unroll 4
-  for (int k = 0; k < nf; ++k) {
-    const float4 p = pl[k];
-    const float v = fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w)));
-    if (v > mx) { mx = v; am = k; }
+  float m0 = -INFINITY, m1 = -INFINITY;
+  int a0 = 0, a1 = 1;
+  int k = 0;
+#pragma unroll 2
+  for (; k + 1 < nf; k += 2) {
+    const float4 p = pl[k], q = pl[k + 1];
+    const float v0 = fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w)));
+    const float v1 = fmaf(q.x, x, fmaf(q.y, y, fmaf(q.z, z, q.w)));
+    if (v0 > m0) { m0 = v0; a0 = k; }
+    if (v1 > m1) { m1 = v1; a1 = k + 1; }
   }
-  arg = am;
-  return mx;
+  if (k < nf) {
+    const float4 p = pl[k];
+    const float v0 = fmaf(p.x, x, fmaf(p.y, y, fmaf(p.z, z, p.w)));
+    if (v0 > m0) { m0 = v0; a0 = k; }
+  }
+  const bool second = m1 > m0 || (m1 == m0 && a1 < a0);
+  arg = second ? a1 : a0;
+  return second ? m1 : m0;
+}
+
+// Copies n elements from global to shared memory, four loads in flight per
+// lane (the staging of a work item's geometry is latency-bound otherwise).
+template <class U>
+__device__ __forceinline__ void stage_copy(U* __restrict__ dst, const U* __restrict__ src, int n,
+                                           int lane) {
+  int k = lane;
+  for (; k + 96 < n; k += 128) {
+    const U a = __ldg(src + k), b = __ldg(src + k + 32), c = __ldg(src + k + 64),
+            d = __ldg(src + k + 96);
+    dst[k] = a;
+    dst[k + 32] = b;
+    dst[k + 64] = c;
+    dst[k + 96] = d;
+  }
+  for (; k < n; k += 32) dst[k] = __ldg(src + k);
 }
 
 // Lower bound of the max-plane value over the edge x(t) = xI + t (xII - xI),

@@ -294,11 +294,15 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         part_zero(sl.acc[lane]);
         for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
       }
-      for (int i = lane; i < V; i += 32) {
-        const float3 x = xform(Rr, tr, g.verts[pfirst.v0 + i]);
-        sl.xs[i] = make_float4(x.x, x.y, x.z, 0.f);
+      for (int i = lane; i < V; i += 64) {   // two loads in flight per lane
+        const bool two = i + 32 < V;
+        const float4 v0 = __ldg(g.verts + pfirst.v0 + i);
+        const float4 v1 = two ? __ldg(g.verts + pfirst.v0 + i + 32) : v0;
+        const float3 x0 = xform(Rr, tr, v0), x1 = xform(Rr, tr, v1);
+        sl.xs[i] = make_float4(x0.x, x0.y, x0.z, 0.f);
+        if (two) sl.xs[i + 32] = make_float4(x1.x, x1.y, x1.z, 0.f);
       }
-      for (int j = lane; j < E; j += 32) sl.edges[j] = g.edges[pfirst.e0 + j];
+      stage_copy(sl.edges, g.edges + pfirst.e0, E, lane);
 
       for (int sc0 = 0; sc0 < S.np;) {
         // S chunk [sc0, sc1) within the plane / piece budgets
@@ -317,7 +321,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           const PieceRec p = g.pieces[S.p0 + sc0 + q];
           sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
         }
-        for (int k = lane; k < P; k += 32) sl.planes[k] = g.planes[f_first + k];
+        stage_copy(sl.planes, g.planes + f_first, P, lane);
         __syncwarp();
 
         // gate the directions (fc, sc), 32 at a time, collecting live ones
