@@ -373,6 +373,17 @@ ccm_status ccm_contacts_backward_counted(ccm_batch batch, const float* pose_a,
                       static_cast<cudaStream_t>(stream));
 }
 
+// Blocks of the reverse kernels for a batch: one per unit of work (item or
+// pair) at most, and no more than stay resident.
+static void set_bwd_grids(const Batch& b, const KParams& kp, bool dual, BwdLaunch* L) {
+  const int d = dual ? 1 : 0, k = kp.trace_iters == 3 ? 1 : 0;
+  const int64_t n_sm = b.ctx->n_sm;
+  L->grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(b.n_items, n_sm * std::max(1, b.bwd_occ.unit[d][k])));
+  L->pair_grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(b.n, n_sm * std::max(1, b.bwd_occ.pair[d][k])));
+}
+
 ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
                                          const float* pose_b, const ccm_params* prm,
                                          const float* ybar, const float* dir, float* grad,
@@ -415,7 +426,7 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   L.dev_pairs = nullptr;
   L.hvp = hvp;
   L.jvp = dir ? jvp : nullptr;
-  L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
+  set_bwd_grids(*b, kp, dir != nullptr, &L);
   const cudaError_t e =
       launch_backward_noalloc(L, b->ctx->device, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "backward (no-alloc) launch");
@@ -571,6 +582,7 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   us.item_vb = std::max(mx.vmax, t.item_vb);
   us.item_eb = std::max(mx.emax, t.item_eb);
   us.groups = std::min(t.groups, mx.pieces_any);
+  us.hit_words = std::min(kHitWords, (mx.s_pieces + 31) / 32);
   us.slice_bytes = unit_slice_bytes(us);
   us.warps = t.fwd_warps;
   while (us.warps > 1 && us.warps * us.slice_bytes > c->smem_optin) --us.warps;
@@ -583,8 +595,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   int per_sm = 1;
   cudaError_t e = configure_forward(us, c->smem_optin, &per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "configure_forward");
-  int per_f = 1, per_d = 1;
-  e = configure_backward(us, c->smem_optin, &per_f, &per_d);
+  BwdOccupancy occ{};
+  e = configure_backward(us, c->smem_optin, &occ);
   if (e != cudaSuccess) return cuda_fail(e, "configure_backward");
   // work items of the pairs for this shape, heaviest first
   std::vector<WorkItem> items;
@@ -619,8 +631,7 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   bt->tuning = t;
   bt->grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((units + us.warps - 1) / us.warps, (int64_t)c->n_sm * std::max(1, per_sm)));
-  bt->bwd_grid_f = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_f)));
-  bt->bwd_grid_d = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->n_sm * std::max(1, per_d)));
+  bt->bwd_occ = occ;
   return CCM_OK;
 }
 
@@ -661,7 +672,7 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.dev_pairs = nullptr;
   L.hvp = hvp;
   L.jvp = dir ? jvp : nullptr;
-  L.grid = dir ? b->bwd_grid_d : b->bwd_grid_f;
+  set_bwd_grids(*b, kp, dir != nullptr, &L);
   cudaError_t e = launch_backward(L, stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return CCM_OK;

@@ -129,32 +129,27 @@ __device__ void fold_t(PartT<T> c, int key, PartT<T>* acc, int lane) {
 constexpr int kHitS = 256;
 constexpr int kHitWords = kHitS / 32;
 
-// A negative sg (a caller that gates by hits it already has) marks nothing.
-__device__ __forceinline__ void mark_hit(uint32_t* hit, int g, int sg, float w) {
-  if (w > 0.f && sg >= 0 && sg < kHitS) atomicOr(hit + g * kHitWords + (sg >> 5), 1u << (sg & 31));
+// The hit table in shared memory keeps hw <= kHitWords words per group (as
+// many as the largest SDF body needs).  A negative sg (a caller that gates by
+// hits it already has) marks nothing.
+__device__ __forceinline__ void mark_hit(uint32_t* hit, int hw, int g, int sg, float w) {
+  if (w > 0.f && sg >= 0 && sg < 32 * hw) atomicOr(hit + g * hw + (sg >> 5), 1u << (sg & 31));
 }
 
 // What ccm_contacts_save keeps per output group for the reverse pass: the
 // group's blend partial (18 floats: M, U, rd, rf, rp, rn, Dd, Da, Dp, Dn) and
-// its hit words (kHitWords uint32, stored bit for bit).
+// its hit words (kHitWords uint32, stored bit for bit; words past the
+// shared-memory table's hw are zero).
 constexpr int kSavedFloats = 18 + kHitWords;
 
-__device__ __forceinline__ void save_group(float* o, const PartT<float>& a, const uint32_t* hit) {
+__device__ __forceinline__ void save_group(float* o, const PartT<float>& a, const uint32_t* hit,
+                                           int hw) {
   o[0] = a.M; o[1] = a.U; o[2] = a.rd; o[3] = a.rf;
   o[4] = a.rp.x; o[5] = a.rp.y; o[6] = a.rp.z; o[7] = a.rn.x; o[8] = a.rn.y; o[9] = a.rn.z;
   o[10] = a.Dd; o[11] = a.Da;
   o[12] = a.Dp.x; o[13] = a.Dp.y; o[14] = a.Dp.z; o[15] = a.Dn.x; o[16] = a.Dn.y; o[17] = a.Dn.z;
   uint32_t* h = reinterpret_cast<uint32_t*>(o + 18);
-  for (int q = 0; q < kHitWords; ++q) h[q] = hit[q];
-}
-
-__device__ __forceinline__ void load_group(const float* o, PartT<float>& a, uint32_t* hit) {
-  a.M = o[0]; a.U = o[1]; a.rd = o[2]; a.rf = o[3];
-  a.rp = v3(o[4], o[5], o[6]); a.rn = v3(o[7], o[8], o[9]);
-  a.Dd = o[10]; a.Da = o[11];
-  a.Dp = v3(o[12], o[13], o[14]); a.Dn = v3(o[15], o[16], o[17]);
-  const uint32_t* h = reinterpret_cast<const uint32_t*>(o + 18);
-  for (int q = 0; q < kHitWords; ++q) hit[q] = h[q];
+  for (int q = 0; q < kHitWords; ++q) h[q] = q < hw ? hit[q] : 0u;
 }
 
 }  // namespace ccm

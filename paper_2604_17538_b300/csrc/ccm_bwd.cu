@@ -406,7 +406,7 @@ template <class T> struct BwdSlice {
   int4* fp;           // [32]
   float4* fs;         // [32]
   PartT<T>* acc;      // [32]
-  Coef<T>* coef;      // [32]
+  Coef<T>* coef;      // [32], the same slots as acc
   int* dir;           // [32]
   int* dsub;          // [32]
   int* pv;            // [33]
@@ -417,34 +417,37 @@ template <class T> struct BwdSlice {
   uint16_t* vlist;    // [item_v]
   uint16_t* elist;    // [item_e]
   uint8_t* need;      // [item_v]
-  uint16_t* am;       // [item_v] a plane attaining the max-plane value
+  uint16_t* am;       // [item_v] a plane attaining the max-plane value (in grad's space)
   int* gside;         // [groups] side of each group: 0 (F = A, S = B) or 1 (F = B, S = A)
   PoseT<T>* spose;    // [2] pose of the SDF body of side 0 (B) and side 1 (A)
   V3T<T>* tba;        // [1] t_B - t_A
   T* pacc;            // [18] pair totals: F, M (about t_A), output terms of A and B
   PoseT<T>* rel;      // [2] relative pose S <- F of side 0 and side 1
-  int* memo;          // list memo of the per-pair pass (see ListMemo)
-  uint32_t* hit;      // [groups * kHitWords] directions that gave a contact in pass 1
+  int* memo;          // list memo of the per-pair pass (see kMemoHead)
+  uint32_t* hit;      // [groups * hw] directions that gave a contact in pass 1
+  int hw;             // hit words per group (UnitShape::hit_words)
 };
 
+
+template <class T> __host__ __device__ constexpr int group_table_bytes() {
+  return (int)(sizeof(PartT<T>) > sizeof(Coef<T>) ? sizeof(PartT<T>) : sizeof(Coef<T>));
+}
 
 template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShape& u) {
   int b = 0;
   b += align16i(4 * u.groups);
   b += align16i((int)sizeof(PoseT<T>) * 2);
-  b += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
   b += align16i((int)sizeof(V3T<T>));
   b += align16i((int)sizeof(T) * 18);
   b += align16i((int)sizeof(PoseT<T>) * 2);
   b += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
-  b += align16i(4 * kHitWords * u.groups);
+  b += align16i(4 * u.hit_words * u.groups);
   b += 16 * u.plane_budget;
   b += align16i(8 * 2 * u.spiece_budget);
   b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   b += align16i(4 * u.edge_budget);
   b += 16 * u.groups * 2;
-  b += align16i((int)sizeof(PartT<T>) * u.groups);
-  b += align16i((int)sizeof(Coef<T>) * u.groups);
+  b += align16i(group_table_bytes<T>() * u.groups);
   b += align16i(4 * kPending) * 2;
   b += align16i(4 * (kPending + 1)) * 2;
   b += align16i(4 * u.item_vb);
@@ -453,7 +456,6 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
   b += align16i(2 * u.item_vb);
   b += align16i(2 * u.item_eb);
   b += align16i(u.item_vb);
-  b += align16i(2 * u.item_vb);
   return b;
 }
 
@@ -466,15 +468,18 @@ template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, con
   s.rel = reinterpret_cast<PoseT<T>*>(p);       p += align16i((int)sizeof(PoseT<T>) * 2);
   s.memo = reinterpret_cast<int*>(p);
   p += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
-  s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * kHitWords * u.groups);
+  s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * u.hit_words * u.groups);
+  s.hw = u.hit_words;
   s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
   s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * 2 * u.spiece_budget);
   s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   s.edges = reinterpret_cast<uint32_t*>(p);    p += align16i(4 * u.edge_budget);
   s.fp = reinterpret_cast<int4*>(p);           p += 16 * u.groups;
   s.fs = reinterpret_cast<float4*>(p);         p += 16 * u.groups;
-  s.acc = reinterpret_cast<PartT<T>*>(p);      p += align16i((int)sizeof(PartT<T>) * u.groups);
-  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i((int)sizeof(Coef<T>) * u.groups);
+  // a group's blend partial (sweep 1) and its adjoint coefficients (sweep 2)
+  // share one slot: the coefficients are formed from the partial in registers
+  s.acc = reinterpret_cast<PartT<T>*>(p);
+  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i(group_table_bytes<T>() * u.groups);
   s.dir = reinterpret_cast<int*>(p);           p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);          p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
@@ -484,8 +489,10 @@ template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, con
   s.grad = reinterpret_cast<V3T<T>*>(p);       p += align16i((int)sizeof(V3T<T>) * u.item_vb);
   s.vlist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_vb);
   s.elist = reinterpret_cast<uint16_t*>(p);    p += align16i(2 * u.item_eb);
-  s.need = reinterpret_cast<uint8_t*>(p);      p += align16i(u.item_vb);
-  s.am = reinterpret_cast<uint16_t*>(p);
+  s.need = reinterpret_cast<uint8_t*>(p);
+  // the attaining planes live only from the max-plane pass to the edge cull,
+  // before the vertex gradients of the same list are written
+  s.am = reinterpret_cast<uint16_t*>(s.grad);
   return s;
 }
 
@@ -707,10 +714,9 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         keep = ((vbits[k >> 5] >> (k & 31)) & 1u) || sl.need[t];
       }
       const unsigned bal = __ballot_sync(kFull, keep);
-      if (keep) sl.am[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+      if (keep) sl.vlist[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
       n_v += __popc(bal);
     }
-    vl = sl.am;
     __syncwarp();
   } else {
   for (int t = lane; t < TV; t += 32) {
@@ -787,7 +793,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
           transition_t(e.phi, kp, w, wp);
           const T dc = fma_t(w, e.phi - kp.d_max, T(kp.d_max));
           part_from_contact(c, w, dc, x, e.g, kp.c_blend);
-          mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
+          mark_hit(sl.hit, sl.hw, g, sc0 + (code & 0xffff), val(w));
           contrib = val(w) > 0.f;
         }
       } else {
@@ -839,7 +845,7 @@ __device__ void bwd_run_list(const BwdSlice<T>& sl, int nd, int TV, int TE, int 
         transition_t(sc.phi, kp, w, wp);
         const T dc = fma_t(w, sc.phi - kp.d_max, T(kp.d_max));
         part_from_contact(c, w, dc, pe, sc.g, kp.c_blend);
-        mark_hit(sl.hit, g, sc0 + (code & 0xffff), val(w));
+        mark_hit(sl.hit, sl.hw, g, sc0 + (code & 0xffff), val(w));
         contrib = val(w) > 0.f;
       } else if (cf.live) {
         if (kCount) { cnt.h2 += s.y; cnt.g2 += (unsigned long long)steps * s.y; }
@@ -922,7 +928,7 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
         if (q < nsc) {
           const int sg = sc0 + q;
           uint32_t any = 0;
-          for (int f = 0; f < nfc; ++f) any |= sl.hit[f * kHitWords + (sg >> 5)];
+          for (int f = 0; f < nfc; ++f) any |= sl.hit[f * sl.hw + (sg >> 5)];
           need = (any >> (sg & 31)) & 1u;
           if (need) {
             const PieceRec p = g.pieces[S.p0 + sg];
@@ -972,7 +978,7 @@ __device__ void bwd_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRec
         const int fcd = d / nsc, scd = d - fcd * nsc;
         const int sg = sc0 + scd;
         if (by_hits && sg < kHitS) {
-          live = (sl.hit[fcd * kHitWords + (sg >> 5)] >> (sg & 31)) & 1u;
+          live = (sl.hit[fcd * sl.hw + (sg >> 5)] >> (sg & 31)) & 1u;
         } else {
           const float4 c = sl.fs[fcd];
           const int2 s = sl.sp[scd];
@@ -1139,9 +1145,9 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         if (saved) {   // the forward's hits: pass 1 visits only those directions
           const uint32_t* h =
               reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * (row0 + fc0 + lane) + 18);
-          for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = h[q];
+          for (int q = 0; q < sl.hw; ++q) sl.hit[lane * sl.hw + q] = h[q];
         } else {
-          for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
+          for (int q = 0; q < sl.hw; ++q) sl.hit[lane * sl.hw + q] = 0u;
         }
       }
       if (saved && S.np <= kHitS) {
@@ -1150,7 +1156,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         __syncwarp();
         bool need = false;
         if (lane < nfc)
-          for (int q = 0; q < kHitWords; ++q) need |= sl.hit[lane * kHitWords + q] != 0u;
+          for (int q = 0; q < sl.hw; ++q) need |= sl.hit[lane * sl.hw + q] != 0u;
         const int nv = need ? p.nv : 0, ne = need ? p.ne : 0;
         int iv = nv, ie = ne;
 #pragma unroll
@@ -1268,7 +1274,7 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
     const int b = side == 0 ? si : si - npB;
     uint32_t any = 0;
     for (int f = 0; f < nfc; ++f)
-      if (sl.gside[f] == side) any |= sl.hit[f * kHitWords + (b >> 5)];
+      if (sl.gside[f] == side) any |= sl.hit[f * sl.hw + (b >> 5)];
     return ((any >> (b & 31)) & 1u) != 0u;
   };
   for (int sc0 = 0; sc0 < nS;) {
@@ -1328,7 +1334,7 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
         const int side = si < npB ? 0 : 1;
         if (sl.gside[fcd] == side) {
           const int b = side == 0 ? si : si - npB;
-          live = (sl.hit[fcd * kHitWords + (b >> 5)] >> (b & 31)) & 1u;
+          live = (sl.hit[fcd * sl.hw + (b >> 5)] >> (b & 31)) & 1u;
         }
         code = (fcd << 16) | scd;
         if (kCount) cnt.dirs += 1;
@@ -1349,10 +1355,10 @@ __device__ void pair_sweep(const DevGeom& g, const BwdSlice<T>& sl, const BodyRe
 }
 
 template <class T>
-__device__ __forceinline__ bool any_hit(const float* saved, int64_t row) {
+__device__ __forceinline__ bool any_hit(const float* saved, int64_t row, int hw) {
   const uint32_t* h = reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * row + 18);
   uint32_t a = 0;
-  for (int q = 0; q < kHitWords; ++q) a |= h[q];
+  for (int q = 0; q < hw; ++q) a |= h[q];   // the record's words past hw are zero
   return a != 0u;
 }
 
@@ -1413,7 +1419,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
         bool live = false;
         int nv = 0, ne = 0;
         if (c < ncand) {
-          live = any_hit<T>(saved, pr.goff + c);
+          live = any_hit<T>(saved, pr.goff + c, sl.hw);
           if (live) {
             const PieceRec p = g.pieces[c < bA.np ? bA.p0 + c : bB.p0 + (c - bA.np)];
             nv = p.nv;
@@ -1471,7 +1477,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
         sl.acc[lane] = z;
         const uint32_t* h =
             reinterpret_cast<const uint32_t*>(saved + (int64_t)kSavedFloats * (pr.goff + c) + 18);
-        for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = h[q];
+        for (int q = 0; q < sl.hw; ++q) sl.hit[lane * sl.hw + q] = h[q];
       }
       for (int l = 0; l < nfc; ++l) {
         const int vo = __shfl_sync(kFull, iv - nv, l), vn = __shfl_sync(kFull, nv, l),
@@ -1519,7 +1525,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
     // groups without marks: zero output tangents
     if (jvp)
       for (int c0 = lane; c0 < ncand; c0 += 32)
-        if (!any_hit<T>(saved, pr.goff + c0)) {
+        if (!any_hit<T>(saved, pr.goff + c0, sl.hw)) {
           float* o = jvp + 8 * (pr.goff + c0);
           for (int q = 0; q < 8; ++q) o[q] = 0.f;
         }
@@ -1565,15 +1571,19 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part,
   }
 }
 
+// The per-pair pass keeps the trace-step loop (kK = 0) for every step count:
+// its code is smaller and it needs fewer registers than the unrolled three
+// steps, so more warps stay resident without thrashing the instruction cache
+// (measured faster on both float and Dual).
 template <class T, int kK>
 static void launch_pair(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
   if (L.counters)
-    bwd_pair_kernel<T, kK, true><<<L.grid, 32, smem, stream>>>(
+    bwd_pair_kernel<T, kK, true><<<L.pair_grid, 32, smem, stream>>>(
         L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
         L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, L.counters, L.sched);
   else
-    bwd_pair_kernel<T, kK, false><<<L.grid, 32, smem, stream>>>(
+    bwd_pair_kernel<T, kK, false><<<L.pair_grid, 32, smem, stream>>>(
         L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
         L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, nullptr, L.sched);
 }
@@ -1599,12 +1609,12 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   }
   if (L.saved && L.pair_order) {   // per pair, from the forward's record
     if (L.dir) {
-      if (small_k) launch_pair<Dual, 3>(L, stream); else launch_pair<Dual, 0>(L, stream);
+      launch_pair<Dual, 0>(L, stream);
     } else {
       BwdLaunch M = L;
       M.hvp = nullptr;
       M.jvp = nullptr;
-      if (small_k) launch_pair<float, 3>(M, stream); else launch_pair<float, 0>(M, stream);
+      launch_pair<float, 0>(M, stream);
     }
     return cudaGetLastError();
   }
@@ -1656,22 +1666,18 @@ static cudaError_t configure_unit(int bytes, int smem_limit, int* per_sm) {
                                                        bytes);
 }
 
-cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_f, int* per_sm_d) {
+cudaError_t configure_backward(const UnitShape& us, int smem_limit, BwdOccupancy* occ) {
   const int sf = bwd_slice_bytes<float>(us), sd = bwd_slice_bytes<Dual>(us);
-  int tmp = 0;
-  cudaError_t e;
-  if ((e = configure_unit<float, 0>(sf, smem_limit, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_unit<Dual, 0>(sd, smem_limit, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_unit<float, 3>(sf, smem_limit, per_sm_f)) != cudaSuccess) return e;
-  if ((e = configure_unit<Dual, 3>(sd, smem_limit, per_sm_d)) != cudaSuccess) return e;
-  // the per-pair kernels share the slices; their occupancy is no higher
   int pf = 1, pd = 1;
-  if ((e = configure_pair<float, 0>(sf, smem_limit, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_pair<Dual, 0>(sd, smem_limit, &tmp)) != cudaSuccess) return e;
-  if ((e = configure_pair<float, 3>(sf, smem_limit, &pf)) != cudaSuccess) return e;
-  if ((e = configure_pair<Dual, 3>(sd, smem_limit, &pd)) != cudaSuccess) return e;
-  *per_sm_f = std::min(*per_sm_f, pf);
-  *per_sm_d = std::min(*per_sm_d, pd);
+  cudaError_t e;
+  if ((e = configure_unit<float, 0>(sf, smem_limit, &occ->unit[0][0])) != cudaSuccess) return e;
+  if ((e = configure_unit<Dual, 0>(sd, smem_limit, &occ->unit[1][0])) != cudaSuccess) return e;
+  if ((e = configure_unit<float, 3>(sf, smem_limit, &occ->unit[0][1])) != cudaSuccess) return e;
+  if ((e = configure_unit<Dual, 3>(sd, smem_limit, &occ->unit[1][1])) != cudaSuccess) return e;
+  if ((e = configure_pair<float, 0>(sf, smem_limit, &pf)) != cudaSuccess) return e;
+  if ((e = configure_pair<Dual, 0>(sd, smem_limit, &pd)) != cudaSuccess) return e;
+  occ->pair[0][0] = occ->pair[0][1] = pf;
+  occ->pair[1][0] = occ->pair[1][1] = pd;
   return cudaSuccess;
 }
 

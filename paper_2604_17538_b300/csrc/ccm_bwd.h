@@ -44,11 +44,19 @@ struct BwdLaunch {
   float* jvp;           // [G, 8] or NULL
   unsigned long long* counters;   // optional work counters (CCM_BWD_CNT_*)
   int* sched;                     // optional work counter (device int), zeroed by the launch
-  int grid;
+  int grid;        // one-warp blocks of the per-item kernel
+  int pair_grid;   // one-warp blocks of the per-pair kernel
+};
+
+// Resident one-warp blocks per SM of the reverse kernels that launch_backward
+// uses for a shape, indexed [T: 0 float, 1 Dual][trace steps: 0 any, 1 three].
+struct BwdOccupancy {
+  int unit[2][2];
+  int pair[2][2];
 };
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream);
-cudaError_t configure_backward(const UnitShape& us, int smem_limit, int* per_sm_f, int* per_sm_d);
+cudaError_t configure_backward(const UnitShape& us, int smem_limit, BwdOccupancy* occ);
 int backward_slice_bytes(const UnitShape& us, bool dual);
 
 // Variant with the per-item slots in a fixed device array (no workspace).

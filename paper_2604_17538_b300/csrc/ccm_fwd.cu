@@ -157,7 +157,7 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
         const float w = transition(g.phi, kp);
         const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
         part_from_contact(c, w, dc, v3(x.x, x.y, x.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
-        mark_hit(sl.hit, code >> 16, sc0 + (code & 0xffff), w);
+        mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
         if (kCount) cnt.con += w > 0.f;
       }
       if (kCount) cnt.eg += s.y;
@@ -185,7 +185,7 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       const float w = transition(ec.phi, kp);
       const float dc = fmaf(w, ec.phi - kp.d_max, kp.d_max);
       part_from_contact(c, w, dc, v3(ec.px, ec.py, ec.pz), v3(ec.gx, ec.gy, ec.gz), kp.c_blend);
-      mark_hit(sl.hit, code >> 16, sc0 + (code & 0xffff), w);
+      mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
       key = code >> 16;
       if (kCount) {
         cnt.con += w > 0.f;
@@ -292,7 +292,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         const float3 c = xform(Rr, tr, p.sphere);
         sl.fs[lane] = make_float4(c.x, c.y, c.z, p.sphere.w);
         part_zero(sl.acc[lane]);
-        for (int q = 0; q < kHitWords; ++q) sl.hit[lane * kHitWords + q] = 0u;
+        for (int q = 0; q < sl.hw; ++q) sl.hit[lane * sl.hw + q] = 0u;
       }
       for (int i = lane; i < V; i += 64) {   // two loads in flight per lane
         const bool two = i + 32 < V;
@@ -365,7 +365,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         write_group(y + 8 * (row0 + fc0 + lane), acc, RS, tS, kp);
         if (saved)
           save_group(saved + (int64_t)kSavedFloats * (row0 + fc0 + lane), acc,
-                     sl.hit + lane * kHitWords);
+                     sl.hit + lane * sl.hw, sl.hw);
       }
       fc0 = fc1;
     }

@@ -67,7 +67,7 @@ struct Batch {
   ccm_tuning tuning{};
   UnitShape us{};
   int grid = 1;
-  int bwd_grid_f = 1, bwd_grid_d = 1;
+  BwdOccupancy bwd_occ{};        // reverse kernels' resident blocks per SM
   void release();
 };
 

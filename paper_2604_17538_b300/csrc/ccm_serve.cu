@@ -99,7 +99,7 @@ struct Serving {
   ccm_serve_config cfg{};
   KParams kp{};
   UnitShape us{};
-  int fwd_grid = 1, bwd_grid = 1;
+  int fwd_grid = 1, bwd_grid = 1, bwd_pair_grid = 1;
   int64_t cap_pairs = 0, cap_groups = 0, cap_req = 0, cap_items = 0;
   BatchMaxima mx;                  // largest pieces the launch shape holds
   bool per_pair = false;           // per-pair reverse pass (every body <= kHitS pieces)
@@ -256,6 +256,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   B.counters = nullptr;
   B.sched = static_cast<int*>(s.d_sched.ptr) + 1;
   B.grid = sv->bwd_grid;
+  B.pair_grid = sv->bwd_pair_grid;
   if (reverse) launch_backward(B, s.stream);
   serve_scatter<<<sv->ctx->n_sm * 4, 256, 0, s.stream>>>(
       reqs, wc, static_cast<const float*>(s.d_y.ptr), static_cast<const float*>(s.d_grad.ptr));
@@ -593,15 +594,18 @@ ccm_status ccm_serve_start(ccm_ctx ctx, const ccm_serve_config* cfg) {
     for (int64_t k = 0; k < probe.n; ++k) max_items = std::max(max_items, off[k + 1] - off[k]);
     probe.release();
     // persistent grids: every resident warp slot of the device
-    int per_sm = 1, per_f = 1, per_d = 1;
+    int per_sm = 1;
+    BwdOccupancy occ{};
     cudaError_t e = configure_forward(sv->us, c->smem_optin, &per_sm);
-    if (e == cudaSuccess) e = configure_backward(sv->us, c->smem_optin, &per_f, &per_d);
+    if (e == cudaSuccess) e = configure_backward(sv->us, c->smem_optin, &occ);
     if (e != cudaSuccess) {
       delete sv;
       return cuda_fail(e, "configure serving kernels");
     }
     sv->fwd_grid = c->n_sm * std::max(1, per_sm);
-    sv->bwd_grid = c->n_sm * std::max(1, per_f);
+    const int k = sv->kp.trace_iters == 3 ? 1 : 0;   // waves run gradients only
+    sv->bwd_grid = c->n_sm * std::max(1, occ.unit[0][k]);
+    sv->bwd_pair_grid = c->n_sm * std::max(1, occ.pair[0][k]);
   }
   // per pair of the largest resident bodies: its record, items and groups
   const int64_t per_pair = kBytesPerPair + max_items * kBytesPerItem + 2 * max_np * kBytesPerGroup;

@@ -32,6 +32,8 @@ struct UnitShape {
   int32_t groups;         // feature pieces (groups) per chunk, <= kGroupsPerChunk
   int32_t item_vb;        // item budgets of the reverse pass
   int32_t item_eb;
+  int32_t hit_words;      // hit words per group kept in shared memory:
+                          // ceil(largest S body's pieces / 32) <= kHitWords
 };
 
 constexpr int kGroupsPerChunk = 32;   // most groups of one F chunk (lane-indexed)
@@ -45,7 +47,8 @@ struct UnitSlice {
   int4* fp;           // [groups] (first vertex, nv, first edge, ne) per F piece
   float4* fs;         // [groups] bounding sphere (S frame) per F piece
   PartT<float>* acc;  // [groups] group blend partials (ccm_blend.cuh)
-  uint32_t* hit;      // [groups * kHitWords] directions that gave a contact
+  uint32_t* hit;      // [groups * hw] directions that gave a contact
+  int hw;             // hit words per group (UnitShape::hit_words)
   int* dir;           // [32] pending live directions: fc << 16 | sc
   int* dsub;          // [32] directions of the list being run
   int* dpl;           // [32] per pending direction: a plane attaining the gate's max
@@ -53,11 +56,12 @@ struct UnitSlice {
   int* pv;            // [33] prefix of vertex items per pending direction
   int* pe;            // [33] prefix of edge items
   float* m;           // [item_v] max-plane value per (direction, vertex)
-  float* phi;         // [item_v] SDF per (direction, vertex)
+  float* phi;         // [item_v] SDF per (direction, vertex) (from the vertex contacts on)
   uint16_t* vlist;    // [item_v] surviving vertex items
   uint16_t* elist;    // [item_e] surviving edge items
   uint8_t* need;      // [item_v]
-  uint16_t* am;       // [item_v] a plane attaining the max-plane value
+  uint16_t* am;       // [item_v] a plane attaining the max-plane value (until the
+                      // edge cull, in phi's space)
 };
 
 // Rounding allowance of the edge cull's plane bound (coordinates are O(1) in
@@ -75,14 +79,13 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += 16 * u.groups;                        // fp
   b += 16 * u.groups;                        // fs
   b += align16i((int)sizeof(PartT<float>) * u.groups);   // acc
-  b += align16i(4 * kHitWords * u.groups);   // hit
+  b += align16i(4 * u.hit_words * u.groups);   // hit
   b += align16i(4 * kPending) * 4;           // dir, dsub, dpl, dsubpl
   b += align16i(4 * (kPending + 1)) * 2;     // pv, pe
   b += align16i(4 * u.item_v) * 2;           // m, phi
   b += align16i(2 * u.item_v);               // vlist
   b += align16i(2 * u.item_e);               // elist
   b += align16i(u.item_v);                   // need
-  b += align16i(2 * u.item_v);               // am
   return b;
 }
 
@@ -95,7 +98,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.fp = reinterpret_cast<int4*>(p);                 p += 16 * u.groups;
   s.fs = reinterpret_cast<float4*>(p);               p += 16 * u.groups;
   s.acc = reinterpret_cast<PartT<float>*>(p);        p += align16i((int)sizeof(PartT<float>) * u.groups);
-  s.hit = reinterpret_cast<uint32_t*>(p);            p += align16i(4 * kHitWords * u.groups);
+  s.hit = reinterpret_cast<uint32_t*>(p);            p += align16i(4 * u.hit_words * u.groups);
+  s.hw = u.hit_words;
   s.dir = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);                p += align16i(4 * kPending);
   s.dpl = reinterpret_cast<int*>(p);                 p += align16i(4 * kPending);
@@ -106,8 +110,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.phi = reinterpret_cast<float*>(p);               p += align16i(4 * u.item_v);
   s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
   s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
-  s.need = reinterpret_cast<uint8_t*>(p);          p += align16i(u.item_v);
-  s.am = reinterpret_cast<uint16_t*>(p);
+  s.need = reinterpret_cast<uint8_t*>(p);
+  s.am = reinterpret_cast<uint16_t*>(s.phi);
   return s;
 }
 
