@@ -200,6 +200,44 @@ class Batch:
                                                     ptr(jvp), abi.stream_of(pose_a)))
         return grad, hvp, jvp
 
+    def step_host(self, pose_a, pose_b, ybar=None, direction=None, params=None,
+                  want_jvp=False, out=None, stream=None):
+        """One step from host tensors (``ccm_contacts_step_host``): forward
+        (y), then with ``ybar`` the gradient and with ``direction`` H u and
+        (``want_jvp``) J u, with the host<->device copies overlapped with the
+        kernels.  Inputs are contiguous CPU float32 tensors (pinned for
+        asynchronous copies); returns CPU tensors (y, grad, hvp, jvp), None
+        where not asked, written once ``stream`` (default: the current cuda
+        stream) reaches this point -- synchronize before reading them.
+        ``out``: preallocated (y, grad, hvp, jvp) CPU tensors (any may be None)."""
+        import torch
+
+        def host(t, shape, name):
+            if t is None:
+                return None
+            if not (t.device.type == "cpu" and t.dtype == torch.float32 and t.is_contiguous()
+                    and tuple(t.shape) == shape):
+                raise ValueError(f"{name} must be a contiguous CPU float32 {list(shape)} tensor")
+            return t
+
+        P, G8 = (self.n_pairs, 12), (self.n_groups, 8)
+        pose_a, pose_b = host(pose_a, P, "pose_a"), host(pose_b, P, "pose_b")
+        ybar, direction = host(ybar, G8, "ybar"), host(direction, P, "direction")
+        o = list(out) if out is not None else [None] * 4
+
+        def new(i, shape):
+            return o[i] if o[i] is not None else torch.empty(shape, pin_memory=True)
+        y = host(new(0, G8), G8, "y")
+        grad = host(new(1, P), P, "grad") if ybar is not None else None
+        hvp = host(new(2, P), P, "hvp") if direction is not None else None
+        jvp = host(new(3, G8), G8, "jvp") if direction is not None and want_jvp else None
+        prm = _params(params)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        check(lib().ccm_contacts_step_host(self.handle, ptr(pose_a), ptr(pose_b), C.byref(prm),
+                                           ptr(ybar), ptr(direction), ptr(y), ptr(grad),
+                                           ptr(hvp), ptr(jvp), C.c_void_p(s.cuda_stream)))
+        return y, grad, hvp, jvp
+
 
 def scene_to_device(scene, ctx: Context, device="cuda"):
     """Loads a ``scenes.Scene`` (geometry, pairs, poses) into ``ctx``: returns

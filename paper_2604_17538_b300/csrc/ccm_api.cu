@@ -373,6 +373,100 @@ ccm_status ccm_contacts_backward_counted(ccm_batch batch, const float* pose_a,
                       static_cast<cudaStream_t>(stream));
 }
 
+static ccm_status reserve(DevBuf& b, size_t bytes, const char* what) {
+  if (bytes <= b.bytes) return CCM_OK;
+  b.release();
+  cudaError_t e = cudaMalloc(&b.ptr, std::max<size_t>(bytes, 256));
+  if (e != cudaSuccess)
+    return fail(CCM_ERR_OOM, "%s: cudaMalloc(%zu): %s", what, bytes, cudaGetErrorString(e));
+  b.bytes = std::max<size_t>(bytes, 256);
+  return CCM_OK;
+}
+
+static ccm_status host_step_state(Batch* b) {
+  if (!b->hs) b->hs = new HostStep();
+  HostStep& h = *b->hs;
+  const size_t P = sizeof(float) * 12 * (size_t)b->n, G = sizeof(float) * (size_t)b->G;
+  struct { DevBuf* buf; size_t bytes; const char* what; } bufs[] = {
+      {&h.pa, P, "step poses"}, {&h.pb, P, "step poses"}, {&h.y, 8 * G, "step outputs"},
+      {&h.saved, CCM_SAVED_FLOATS * G, "step record"}, {&h.ybar, 8 * G, "step cotangents"},
+      {&h.grad, P, "step gradient"}, {&h.grad2, P, "step gradient"}, {&h.hvp, P, "step hvp"},
+      {&h.dir, P, "step direction"}, {&h.jvp, 8 * G, "step jvp"}};
+  for (auto& x : bufs) {
+    const ccm_status s = reserve(*x.buf, x.bytes, x.what);
+    if (s != CCM_OK) return s;
+  }
+  if (!h.cin) CCM_CUDA(cudaStreamCreateWithFlags(&h.cin, cudaStreamNonBlocking), "stream");
+  if (!h.cout) CCM_CUDA(cudaStreamCreateWithFlags(&h.cout, cudaStreamNonBlocking), "stream");
+  for (cudaEvent_t& e : h.ev)
+    if (!e) CCM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+  return CCM_OK;
+}
+
+ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const float* pose_b,
+                                  const ccm_params* prm, const float* ybar, const float* dir,
+                                  float* y, float* grad, float* hvp, float* jvp,
+                                  ccm_stream stream) {
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
+  if (!pose_a || !pose_b || !y) return fail(CCM_ERR_INVALID, "NULL pose or output pointer");
+  if (ybar && !grad) return fail(CCM_ERR_INVALID, "ybar given without grad");
+  if (dir && (!ybar || !hvp)) return fail(CCM_ERR_INVALID, "dir needs ybar, grad and hvp");
+  if (b->n == 0) return CCM_OK;
+  CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  ccm_status s = host_step_state(b);
+  if (s != CCM_OK) return s;
+  HostStep& h = *b->hs;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t P = sizeof(float) * 12 * (size_t)b->n, G8 = sizeof(float) * 8 * (size_t)b->G;
+  const cudaMemcpyKind in = cudaMemcpyHostToDevice, out = cudaMemcpyDeviceToHost;
+  float* pa = static_cast<float*>(h.pa.ptr);
+  float* pb = static_cast<float*>(h.pb.ptr);
+  float* yd = static_cast<float*>(h.y.ptr);
+  float* sv = static_cast<float*>(h.saved.ptr);
+  float* yb = static_cast<float*>(h.ybar.ptr);
+  float* gd = static_cast<float*>(h.grad.ptr);
+  // the side streams start behind the work already queued on `stream` (an
+  // earlier step's kernels still read the buffers they overwrite)
+  CCM_CUDA(cudaEventRecord(h.ev[0], st), "event");
+  CCM_CUDA(cudaMemcpyAsync(pa, pose_a, P, in, st), "pose copy");
+  CCM_CUDA(cudaMemcpyAsync(pb, pose_b, P, in, st), "pose copy");
+  if (ybar) {
+    CCM_CUDA(cudaStreamWaitEvent(h.cin, h.ev[0], 0), "wait");
+    CCM_CUDA(cudaMemcpyAsync(yb, ybar, G8, in, h.cin), "cotangent copy");
+    if (dir) CCM_CUDA(cudaMemcpyAsync(h.dir.ptr, dir, P, in, h.cin), "direction copy");
+    CCM_CUDA(cudaEventRecord(h.ev[1], h.cin), "event");
+  }
+  if ((s = run_forward(b, pa, pb, prm, yd, sv, nullptr, st)) != CCM_OK) return s;
+  CCM_CUDA(cudaEventRecord(h.ev[2], st), "event");
+  CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[2], 0), "wait");
+  CCM_CUDA(cudaMemcpyAsync(y, yd, G8, out, h.cout), "output copy");
+  if (ybar) {
+    CCM_CUDA(cudaStreamWaitEvent(st, h.ev[1], 0), "wait");
+    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, st)) !=
+        CCM_OK)
+      return s;
+    if (dir) {
+      CCM_CUDA(cudaEventRecord(h.ev[3], st), "event");
+      CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[3], 0), "wait");
+      CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, h.cout), "gradient copy");
+      float* hd = static_cast<float*>(h.hvp.ptr);
+      float* jd = jvp ? static_cast<float*>(h.jvp.ptr) : nullptr;
+      if ((s = run_backward(b, pa, pb, prm, sv, yb, static_cast<const float*>(h.dir.ptr),
+                            static_cast<float*>(h.grad2.ptr), hd, jd, nullptr, st)) != CCM_OK)
+        return s;
+      CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, st), "hvp copy");
+      if (jvp) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, st), "jvp copy");
+    } else {
+      CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, st), "gradient copy");
+    }
+  }
+  // later work on `stream` waits for the copies of the side streams
+  CCM_CUDA(cudaEventRecord(h.ev[0], h.cout), "event");
+  CCM_CUDA(cudaStreamWaitEvent(st, h.ev[0], 0), "wait");
+  return CCM_OK;
+}
+
 // Blocks of the reverse kernels for a batch: one per unit of work (item or
 // pair) at most, and no more than stay resident.
 static void set_bwd_grids(const Batch& b, const KParams& kp, bool dual, BwdLaunch* L) {
@@ -678,7 +772,21 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   return CCM_OK;
 }
 
+void HostStep::release() {
+  for (DevBuf* b : {&pa, &pb, &y, &saved, &ybar, &grad, &grad2, &hvp, &dir, &jvp}) b->release();
+  if (cin) cudaStreamDestroy(cin);
+  if (cout) cudaStreamDestroy(cout);
+  for (cudaEvent_t& e : ev)
+    if (e) cudaEventDestroy(e);
+  cin = cout = nullptr;
+}
+
 void Batch::release() {
+  if (hs) {
+    hs->release();
+    delete hs;
+    hs = nullptr;
+  }
   d_pairs.release();
   d_items.release();
   d_item_order.release();

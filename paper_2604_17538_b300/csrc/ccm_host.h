@@ -43,6 +43,14 @@ struct Context {
   void shutdown_serving();
 };
 
+// Device buffers, side streams and events of ccm_contacts_step_host.
+struct HostStep {
+  DevBuf pa, pb, y, saved, ybar, grad, grad2, hvp, dir, jvp;
+  cudaStream_t cin = nullptr, cout = nullptr;   // input and output copies
+  cudaEvent_t ev[4] = {};                       // start, inputs, forward, gradient
+  void release();
+};
+
 struct BatchMaxima {      // largest pieces / bodies a batch touches
   int vmax = 1, fmax = 1, emax = 1, s_planes = 1, s_pieces = 1, f_verts = 1, f_edges = 1;
   int pieces_any = 1;
@@ -68,6 +76,7 @@ struct Batch {
   UnitShape us{};
   int grid = 1;
   BwdOccupancy bwd_occ{};        // reverse kernels' resident blocks per SM
+  HostStep* hs = nullptr;        // ccm_contacts_step_host state (first call)
   void release();
 };
 
