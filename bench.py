@@ -462,12 +462,17 @@ def run_uneven(args, rank, world):
 SERVE_BUDGET = 256 << 20   # HBM budget of the serving context (wave buffers)
 
 
+SERVE_LOADS = (0.1, 0.3, 0.6, 0.9, 1.2)   # offered rates, x the served saturation rate
+
+
 def _serve_requests(sc, rng, n_req, rate):
     """Arrival times (s), pair slices and kinds of ``n_req`` requests: Poisson
-    arrivals at ``rate`` per second, 1-256 environments (body pairs) drawn
-    log-uniformly, half of them forward only, half forward + gradient."""
+    arrivals at ``rate`` per second (all at t = 0 for rate None), 1-256
+    environments (body pairs) drawn log-uniformly, half of them forward only,
+    half forward + gradient."""
     from paper_2604_17538_b300 import scenes
-    arr = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    arr = (np.zeros(n_req) if rate is None
+           else np.cumsum(rng.exponential(1.0 / rate, size=n_req)))
     size = scenes.log_uniform_int(rng, 1, 256, size=n_req)
     start = np.array([rng.integers(0, sc.n_pairs - k + 1) for k in size])
     grad = rng.uniform(size=n_req) < 0.5
@@ -478,12 +483,15 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x), q)) * 1e3 if len(x) else None
 
 
-def run_serve(args, rank, world, n_req=3000, rates=None):
-    """Serving sweep: for each arrival rate, ``n_req`` requests through the
-    continuous-batching loop (ccm_submit / ccm_poll) and the same requests as
-    plain per-request launches (ccm_contacts [+ ccm_contacts_backward] on a
-    batch planned in advance, one stream, launched at arrival).  Reports
-    p50 / p99 latency (arrival to completion) and throughput."""
+def run_serve(args, rank, world, n_req=10000, rates=None):
+    """Serving sweep.  First the saturation rate of the continuous-batching
+    loop (every request queued at t = 0), then, for offered rates of
+    SERVE_LOADS x that rate (or the rates given), ``n_req`` requests with
+    Poisson arrivals through the loop (ccm_submit / ccm_poll) and the same
+    requests as plain per-request launches (ccm_contacts [+
+    ccm_contacts_backward] on a batch planned in advance, one stream,
+    launched at arrival).  Reports p50 / p99 latency (arrival to completion)
+    and throughput."""
     import ctypes as C
     import torch
     from paper_2604_17538_b300 import abi, api, build, scenes
@@ -504,15 +512,18 @@ def run_serve(args, rank, world, n_req=3000, rates=None):
     pp_cum = np.concatenate([[0], np.cumsum(pp_pair)])
     ybar_all = torch.from_numpy(np.random.default_rng(5).normal(
         size=(int(off[-1]), 8)).astype(np.float32)).cuda()
-    rates = rates or [float(r) for r in args.serve_rates.split(",")]
-    results = []
-    for ri, rate in enumerate(rates):
-        rng = np.random.default_rng([rank, ri])
+    L = abi.lib()
+    h = ctx.handle
+
+    def prepare(seed, rate):
+        """Requests as an array of C structs (replayed by the native load
+        generator) and their per-request launch arguments; outputs
+        preallocated as slices."""
+        rng = np.random.default_rng(seed)
         arr, i0, i1, grad = _serve_requests(sc, rng, n_req, rate)
         A = [handles[sc.pair_a[a:b]] for a, b in zip(i0, i1)]
         B = [handles[sc.pair_b[a:b]] for a, b in zip(i0, i1)]
         qp = int(sum(pp_cum[b] - pp_cum[a] for a, b in zip(i0, i1)))
-        # outputs of every request preallocated (slices of one buffer per kind)
         G_req = np.array([off[b] - off[a] for a, b in zip(i0, i1)])
         goff = np.concatenate([[0], np.cumsum(G_req)])
         poff = np.concatenate([[0], np.cumsum(i1 - i0)])
@@ -521,107 +532,100 @@ def run_serve(args, rank, world, n_req=3000, rates=None):
         yb = [ybar_all[off[a]:off[b]] if g else None for a, b, g in zip(i0, i1, grad)]
         ys = [y_all[goff[k]:goff[k + 1]] for k in range(n_req)]
         gs = [g_all[poff[k]:poff[k + 1]] for k in range(n_req)]
-        row = {"rate_req_s": rate, "requests": n_req, "piece_pairs": qp}
-
-        # requests as prepared C structs: the client loop below does one
-        # ctypes call per submission (no per-request Python marshalling)
-        keep = []
-        reqs = []
+        keep, reqs = [y_all, g_all], (abi.ccm_request * n_req)()
         for k in range(n_req):
             Ak = np.ascontiguousarray(A[k], np.uint64)
             Bk = np.ascontiguousarray(B[k], np.uint64)
             keep += [Ak, Bk]
-            reqs.append(C.byref(abi.ccm_request(
+            reqs[k] = abi.ccm_request(
                 int(i1[k] - i0[k]), Ak.ctypes.data, Bk.ctypes.data, pa[i0[k]:i1[k]].data_ptr(),
                 pb[i0[k]:i1[k]].data_ptr(), ys[k].data_ptr(),
-                yb[k].data_ptr() if grad[k] else None, gs[k].data_ptr() if grad[k] else None)))
-        L = abi.lib()
-        submit, drain = L.ccm_submit, L.ccm_poll_completed
-        h = ctx.handle
+                yb[k].data_ptr() if grad[k] else None, gs[k].data_ptr() if grad[k] else None)
+        calls = [(pa[i0[k]:i1[k]].data_ptr(), pb[i0[k]:i1[k]].data_ptr(), ys[k].data_ptr(),
+                  yb[k].data_ptr() if grad[k] else None, gs[k].data_ptr() if grad[k] else None)
+                 for k in range(n_req)]
+        return {"arr": arr, "A": A, "B": B, "qp": qp, "reqs": reqs, "calls": calls, "keep": keep}
 
-        # (1) continuous batching
+    def served(P):
+        """Continuous batching: the native load generator (ccm_serve_replay)
+        submits each request at its arrival time and drains completions."""
+        arr = np.ascontiguousarray(P["arr"], np.float64)
         srv = api.Server(ctx, max_wave_pairs=0, max_wave_requests=1024)
         torch.cuda.synchronize()
-        lat = np.zeros(n_req)
-        lag = np.zeros(n_req)
-        index = {}
-        tk = C.c_uint64()
-        cap = 4096
-        done_t = np.zeros(cap, np.uint64)
-        done_l = np.zeros(cap, np.float64)
-        nd = C.c_int64()
-        n_done = 0
-        tb = time.perf_counter()
-        k = 0
-        while n_done < n_req:
-            now = time.perf_counter() - tb
-            while k < n_req and arr[k] <= now:
-                lag[k] = time.perf_counter() - tb - arr[k]
-                abi.check(submit(h, reqs[k], C.byref(tk)))
-                index[tk.value] = k
-                k += 1
-            abi.check(drain(h, done_t.ctypes.data, done_l.ctypes.data, cap, C.byref(nd)))
-            for j in range(nd.value):
-                kk = index.pop(int(done_t[j]))
-                lat[kk] = lag[kk] + done_l[j]
-            n_done += nd.value
-        t_srv = time.perf_counter() - tb
+        lat, lag = np.zeros(n_req), np.zeros(n_req)
+        el = C.c_double()
+        abi.check(L.ccm_serve_replay(h, C.cast(P["reqs"], C.c_void_p), arr.ctypes.data, n_req,
+                                     lag.ctypes.data, lat.ctypes.data, C.byref(el)))
+        t_srv = el.value
         st = srv.stats()
         srv.close()
-        row["served"] = {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
-                         "qps": qp / t_srv, "req_s": n_req / t_srv, "waves": st["waves"],
-                         "mean_wave_pairs": st["wave_pairs"] / max(1, st["waves"]),
-                         "wave_gpu_ms_mean": 1e3 * st["gpu_s"] / max(1, st["waves"]),
-                         "wave_form_ms_mean": 1e3 * st["form_s"] / max(1, st["waves"]),
-                         "client_lag_p99_ms": _pct(lag, 99)}
+        return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "qps": P["qp"] / t_srv, "req_s": n_req / t_srv, "waves": st["waves"],
+                "mean_wave_pairs": st["wave_pairs"] / max(1, st["waves"]),
+                "wave_gpu_ms_mean": 1e3 * st["gpu_s"] / max(1, st["waves"]),
+                "wave_form_ms_mean": 1e3 * st["form_s"] / max(1, st["waves"]),
+                "client_lag_p99_ms": _pct(lag, 99)}
 
-        # (2) plain per-request launches, in arrival order on one stream
-        batches = [ctx.batch(A[k], B[k]) for k in range(n_req)]
+    def per_request(P):
+        """Plain per-request launches, in arrival order on one stream."""
+        arr = P["arr"]
+        batches = [ctx.batch(P["A"][k], P["B"][k]) for k in range(n_req)]
         prm = C.byref(api._params(None))
         stream = torch.cuda.current_stream()
         sh = stream.cuda_stream
-        calls = []
-        for k in range(n_req):
-            bh = batches[k].handle
-            p_a, p_b = pa[i0[k]:i1[k]].data_ptr(), pb[i0[k]:i1[k]].data_ptr()
-            calls.append((bh, p_a, p_b, ys[k].data_ptr(),
-                          yb[k].data_ptr() if grad[k] else None,
-                          gs[k].data_ptr() if grad[k] else None))
         fwd, bwd = L.ccm_contacts, L.ccm_contacts_backward
         evs = [torch.cuda.Event() for _ in range(n_req)]
         torch.cuda.synchronize()
-        lat2 = np.zeros(n_req)
-        lag2 = np.zeros(n_req)
+        lat, lag = np.zeros(n_req), np.zeros(n_req)
         fifo = []
         tb = time.perf_counter()
-        k = 0
-        j = 0
+        k = j = 0
         while j < n_req:
             now = time.perf_counter() - tb
             while k < n_req and arr[k] <= now:
-                bh, p_a, p_b, py, pyb, pg = calls[k]
+                bh = batches[k].handle
+                p_a, p_b, py, pyb, pg = P["calls"][k]
                 abi.check(fwd(bh, p_a, p_b, prm, py, sh))
                 if pyb is not None:
                     abi.check(bwd(bh, p_a, p_b, prm, pyb, None, pg, None, None, sh))
                 evs[k].record(stream)
-                lag2[k] = time.perf_counter() - tb - arr[k]
+                lag[k] = time.perf_counter() - tb - arr[k]
                 fifo.append(k)
                 k += 1
             while j < len(fifo) and evs[fifo[j]].query():
                 kk = fifo[j]
-                lat2[kk] = time.perf_counter() - tb - arr[kk]
+                lat[kk] = time.perf_counter() - tb - arr[kk]
                 j += 1
         t_plain = time.perf_counter() - tb
         for bt in batches:
             bt.close()
-        row["per_request_launch"] = {"p50_ms": _pct(lat2, 50), "p99_ms": _pct(lat2, 99),
-                                     "qps": qp / t_plain, "req_s": n_req / t_plain,
-                                     "client_lag_p99_ms": _pct(lag2, 99)}
+        return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "qps": P["qp"] / t_plain, "req_s": n_req / t_plain,
+                "client_lag_p99_ms": _pct(lag, 99)}
+
+    sat = served(prepare([rank, 99], None))
+    if rates is None and args.serve_rates != "auto":
+        rates = [float(r) for r in args.serve_rates.split(",")]
+    loads = None
+    if rates is None:
+        loads = list(SERVE_LOADS)
+        rates = [f * sat["req_s"] for f in loads]
+    results = []
+    for ri, rate in enumerate(rates):
+        P = prepare([rank, ri], rate)
+        row = {"rate_req_s": rate, "requests": n_req, "piece_pairs": P["qp"]}
+        if loads is not None:
+            row["load"] = loads[ri]
+        row["served"] = served(P)
+        row["per_request_launch"] = per_request(P)
         results.append(row)
     return {"geometry": f"uneven pool: {sc.n_pairs} placed pairs over "
                         f"{len(npb)} bodies, pieces/body log-U[1,64], hull points log-U[8,512]",
             "requests": "Poisson arrivals; 1-256 envs log-uniform; 50/50 fwd vs fwd+grad",
             "hbm_budget_bytes": SERVE_BUDGET, "generation_s": t_gen,
+            "saturation": {"requests": n_req, "arrivals": "all at t = 0",
+                           "req_s": sat["req_s"], "qps": sat["qps"],
+                           "mean_wave_pairs": sat["mean_wave_pairs"]},
             "latency": "arrival to completion as seen by the host (ms)", "sweep": results}
 
 
@@ -637,8 +641,10 @@ def main():
     ap.add_argument("--workload", default="hull", choices=["hull", "uneven", "serve"])
     ap.add_argument("--pairs", type=int, default=65536)
     ap.add_argument("--serve-pairs", type=int, default=8192)
-    ap.add_argument("--serve-rates", default="2000,8000,32000,128000")
-    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-rates", default="auto",
+                    help="offered rates (req/s, comma-separated) or 'auto': "
+                         "0.1-1.2 x the measured saturation rate")
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

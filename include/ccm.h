@@ -406,6 +406,24 @@ typedef struct {
 /* Errors: CCM_ERR_INVALID (not started). */
 CCM_API ccm_status ccm_serve_stats(ccm_ctx ctx, ccm_serve_counters* out);
 
+/* Load generator for measuring the serving loop without a client in the way:
+ * on the calling thread, submits reqs[k] (host array of n requests) when
+ * arrival_s[k] seconds (non-decreasing, host array) have passed since the
+ * call began -- busy-waiting on a steady clock, retrying after draining when
+ * the queue answers CCM_ERR_BUSY -- and drains completions with
+ * ccm_poll_completed until all n are done.  Writes, per request (host arrays,
+ * may be NULL), lag_s[k] = submission time - arrival time (the generator's own
+ * delay) and latency_s[k] = completion - arrival as the host sees it; *elapsed_s
+ * (may be NULL) gets the time from the call's start to the last completion.
+ * The requests' buffers must stay valid until the call returns.  Requires a
+ * started serving loop; blocks until every request is done.  The paper has no
+ * counterpart: this only measures the loop.  Errors: those of ccm_submit and
+ * ccm_poll_completed (requests submitted before an error still complete in
+ * the loop). */
+CCM_API ccm_status ccm_serve_replay(ccm_ctx ctx, const ccm_request* reqs,
+                                    const double* arrival_s, int64_t n, double* lag_s,
+                                    double* latency_s, double* elapsed_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,8 @@ _SIGS = {
     "ccm_contacts_save": (C.c_int, [C.c_void_p] * 7),
     "ccm_contacts_backward_saved": (C.c_int, [C.c_void_p] * 11),
     "ccm_contacts_step_host": (C.c_int, [C.c_void_p] * 11),
+    "ccm_serve_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
     "ccm_contacts_backward_counted": (C.c_int, [C.c_void_p] * 12),
     "ccm_peak_probe": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ccm_default_serve_config": (None, [C.c_void_p]),

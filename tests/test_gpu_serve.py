@@ -236,3 +236,62 @@ def test_stop_runs_queued_requests(dev, uneven):
         compare(y.double().cpu().numpy(), yb.double().cpu().numpy(), "drained",
                 a_slack=weight_slack(uneven))
         batch.close()
+
+
+def test_replay_submits_on_schedule_and_matches_direct_submission(dev, uneven):
+    """ccm_serve_replay (the native load generator): every request completes,
+    none is submitted before its arrival, latency >= lag >= 0, and its results
+    are bitwise those of the same requests submitted through ccm_submit."""
+    import ctypes as C
+    import torch
+    from paper_2604_17538_b300 import abi, api
+    ctx, handles, pa, pb = dev
+    rng = np.random.default_rng(12)
+    reqs = _requests(uneven, rng, 24)
+    # reference: the same requests through ccm_submit, all queued before one wave
+    srv = api.Server(ctx, max_wave_pairs=512, max_wave_requests=64)
+    try:
+        srv.hold(True)
+        subs = [_submit(srv, uneven, handles, pa, pb, r, seed=4) for r in reqs]
+        srv.hold(False)
+        _wait_all(srv, [s[0] for s in subs])
+    finally:
+        srv.close()
+    n = len(reqs)
+    arr = np.cumsum(rng.exponential(2e-4, size=n))
+    keep, table = [], (abi.ccm_request * n)()
+    outs = []
+    for k, (i0, i1, grad) in enumerate(reqs):
+        A = np.ascontiguousarray(handles[uneven.pair_a[i0:i1]], np.uint64)
+        B = np.ascontiguousarray(handles[uneven.pair_b[i0:i1]], np.uint64)
+        G = int(uneven.group_offsets()[i1] - uneven.group_offsets()[i0])
+        y = torch.empty((G, 8), device="cuda")
+        g = torch.empty((i1 - i0, 12), device="cuda") if grad else None
+        yb = _ybar(uneven, i0, i1, 4) if grad else None
+        keep += [A, B, y, g, yb]
+        outs.append((y, g))
+        table[k] = abi.ccm_request(i1 - i0, A.ctypes.data, B.ctypes.data,
+                                   pa[i0:i1].data_ptr(), pb[i0:i1].data_ptr(), y.data_ptr(),
+                                   yb.data_ptr() if grad else None,
+                                   g.data_ptr() if grad else None)
+    lag, lat, el = np.full(n, -1.0), np.full(n, -1.0), C.c_double()
+    srv = api.Server(ctx, max_wave_pairs=512, max_wave_requests=64)
+    try:
+        abi.check(abi.lib().ccm_serve_replay(ctx.handle, C.cast(table, C.c_void_p),
+                                             arr.ctypes.data, n, lag.ctypes.data,
+                                             lat.ctypes.data, C.byref(el)))
+        assert srv.stats()["served"] == n
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    assert np.all(lag >= 0.0) and np.all(lat >= lag) and np.all(lat < 60.0)
+    assert el.value >= arr[-1] and el.value >= float((arr + lat).max()) - 1e-3
+    # results are independent of the wave mix (bitwise)
+    for (_, y0, g0, _), (y, g) in zip(subs, outs):
+        assert torch.equal(y0, y)
+        if g is not None:
+            assert torch.equal(g0, g)
+    # argument errors
+    bad = np.array([1.0, 0.5])
+    assert abi.lib().ccm_serve_replay(ctx.handle, C.cast(table, C.c_void_p), bad.ctypes.data,
+                                      2, None, None, None) == abi.CCM_ERR_INVALID
