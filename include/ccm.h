@@ -204,22 +204,23 @@ CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pos
 /* One step from host memory, for callers whose poses and cotangents live on
  * the host: copies pose_a, pose_b (host [n,12]) and, if given, ybar (host
  * [G,8]) and dir (host [n,12]) into device buffers the batch owns, runs
- * ccm_contacts_save, then (with ybar) the gradient pass and (with dir) the
- * H dir / J dir pass of ccm_contacts_backward_saved, and copies back y (host
+ * ccm_contacts_save, then (with dir) the H dir / J dir pass and (with ybar)
+ * the gradient pass of ccm_contacts_backward_saved, and copies back y (host
  * [G,8]), grad (host [n,12]; required with ybar) and, with dir, hvp (host
  * [n,12]; required) and jvp (host [G,8]; optional).  Results are those of
  * the device calls on the same data.  The ybar / dir copies run on a second
- * stream during the forward kernel, and y (and, with dir, grad) are copied
- * back on a third stream while the next pass runs; only the pose copy and
- * the last pass's outputs are not hidden behind a kernel.  Host buffers
- * should be pinned (cudaHostAlloc, torch pin_memory) so that the copies are
- * asynchronous.  Asynchronous on `stream`: the outputs are complete once
- * the work queued on `stream` up to this call is (synchronize it before
- * reading them); later work on `stream` waits for every copy.  The first
- * call allocates the device buffers (the poses, y, the record, ybar, two
- * gradients, hvp, dir and jvp: 52 n + (8 + CCM_SAVED_FLOATS + 8) G floats)
- * and two streams, kept until ccm_batch_destroy; later calls allocate
- * nothing.  Calls on one batch must be ordered on one stream.
+ * stream during the forward kernel (after the pose copy, which the forward
+ * waits for), and y, hvp and jvp are copied back on a third stream while the
+ * next pass runs; only the pose copy and the copy of the last pass's output
+ * (grad, or y for a forward alone) are not hidden behind a kernel.  Host
+ * buffers should be pinned (cudaHostAlloc, torch pin_memory) so that the
+ * copies are asynchronous.  Asynchronous on `stream`: the outputs are
+ * complete once the work queued on `stream` up to this call is (synchronize
+ * it before reading them); later work on `stream` waits for every copy.  The
+ * first call allocates the device buffers (the poses, y, the record, ybar,
+ * two gradients, hvp, dir and jvp: 52 n + (8 + CCM_SAVED_FLOATS + 8) G
+ * floats) and two streams, kept until ccm_batch_destroy; later calls
+ * allocate nothing.  Calls on one batch must be ordered on one stream.
  * Errors: CCM_ERR_INVALID (NULL pointer a mode needs, dir without ybar),
  * CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a,

@@ -427,10 +427,12 @@ ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const fl
   float* yb = static_cast<float*>(h.ybar.ptr);
   float* gd = static_cast<float*>(h.grad.ptr);
   // the side streams start behind the work already queued on `stream` (an
-  // earlier step's kernels still read the buffers they overwrite)
-  CCM_CUDA(cudaEventRecord(h.ev[0], st), "event");
+  // earlier step's kernels still read the buffers they overwrite) and behind
+  // the pose copies, which the forward waits for: sharing the link with the
+  // cotangent copy would delay it
   CCM_CUDA(cudaMemcpyAsync(pa, pose_a, P, in, st), "pose copy");
   CCM_CUDA(cudaMemcpyAsync(pb, pose_b, P, in, st), "pose copy");
+  CCM_CUDA(cudaEventRecord(h.ev[0], st), "event");
   if (ybar) {
     CCM_CUDA(cudaStreamWaitEvent(h.cin, h.ev[0], 0), "wait");
     CCM_CUDA(cudaMemcpyAsync(yb, ybar, G8, in, h.cin), "cotangent copy");
@@ -443,23 +445,21 @@ ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const fl
   CCM_CUDA(cudaMemcpyAsync(y, yd, G8, out, h.cout), "output copy");
   if (ybar) {
     CCM_CUDA(cudaStreamWaitEvent(st, h.ev[1], 0), "wait");
-    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, st)) !=
-        CCM_OK)
-      return s;
-    if (dir) {
-      CCM_CUDA(cudaEventRecord(h.ev[3], st), "event");
-      CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[3], 0), "wait");
-      CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, h.cout), "gradient copy");
+    if (dir) {   // the H u / J u pass first: its larger outputs copy back during the gradient pass
       float* hd = static_cast<float*>(h.hvp.ptr);
       float* jd = jvp ? static_cast<float*>(h.jvp.ptr) : nullptr;
       if ((s = run_backward(b, pa, pb, prm, sv, yb, static_cast<const float*>(h.dir.ptr),
                             static_cast<float*>(h.grad2.ptr), hd, jd, nullptr, st)) != CCM_OK)
         return s;
-      CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, st), "hvp copy");
-      if (jvp) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, st), "jvp copy");
-    } else {
-      CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, st), "gradient copy");
+      CCM_CUDA(cudaEventRecord(h.ev[3], st), "event");
+      CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[3], 0), "wait");
+      CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, h.cout), "hvp copy");
+      if (jvp) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, h.cout), "jvp copy");
     }
+    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, st)) !=
+        CCM_OK)
+      return s;
+    CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, st), "gradient copy");
   }
   // later work on `stream` waits for the copies of the side streams
   CCM_CUDA(cudaEventRecord(h.ev[0], h.cout), "event");
