@@ -33,19 +33,31 @@ def _time(fn, reps=5):
     return a.elapsed_time(b) / reps
 
 
-def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verbose=False):
+def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verbose=False,
+             saved=True):
     """Picks the fastest forward shape, then the fastest reverse-pass shape
-    (timed with a direction when one is given, i.e. on the dual kernel)."""
+    (timed with a direction when one is given, i.e. on the dual kernel).
+    ``saved`` (default): time the path a simulation step runs -- the forward
+    keeping its record (``ccm_contacts_save``) and the reverse pass from it
+    (``ccm_contacts_backward_saved``, per body pair); else the record-free
+    calls.  The record does not depend on the shape, so one serves every
+    reverse-pass candidate."""
     import torch
     log = {"items": {}, "forward": {}, "reverse": {}}
     if ybar is None:
         ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
+    rec = batch.saved_buffer(pose_a.device) if saved else None
+
+    def fwd():
+        return batch.contacts(pose_a, pose_b, params, saved=rec)
+
+    def bwd():
+        return batch.backward(pose_a, pose_b, ybar, direction, params, saved=rec)
     gbest = None
     for cand in GROUP_CANDIDATES:
         try:
             batch.set_tuning(**cand)
-            t = _time(lambda: (batch.contacts(pose_a, pose_b, params),
-                               batch.backward(pose_a, pose_b, ybar, direction, params)))
+            t = _time(lambda: (fwd(), bwd()))
         except Exception as ex:
             log["items"][str(cand)] = repr(ex)
             continue
@@ -57,7 +69,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
     for cand in FWD_CANDIDATES:
         try:
             batch.set_tuning(**cand)
-            t = _time(lambda: batch.contacts(pose_a, pose_b, params))
+            t = _time(fwd)
         except Exception as ex:   # a shape the device cannot hold
             log["forward"][str(cand)] = repr(ex)
             continue
@@ -65,11 +77,13 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
         if best is None or t < best[0]:
             best = (t, cand)
     batch.set_tuning(**best[1])
+    if rec is not None:
+        fwd()                     # the record of these poses for the reverse candidates
     bbest = None
     for cand in BWD_CANDIDATES:
         try:
             batch.set_tuning(**cand)
-            t = _time(lambda: batch.backward(pose_a, pose_b, ybar, direction, params))
+            t = _time(bwd)
         except Exception as ex:
             log["reverse"][str(cand)] = repr(ex)
             continue

@@ -93,3 +93,30 @@ def test_work_item_size_and_budgets_change_only_rounding(ctx, uneven):
         err = np.abs(g - g0).max(1)
         assert np.all(err <= GRAD_RTOL * np.abs(g0).max(1) + 1e-6), (t, float(err.max()))
     batch.close()
+
+
+def test_autotune_times_the_saved_record_path(ctx, uneven):
+    """The autotuner times the forward keeping its record and the per-pair
+    reverse pass from it (the path a step runs), keeps a shape from its
+    candidate lists, and that shape changes results only by rounding."""
+    import torch
+    from paper_2604_17538_b300 import api, tune
+    batch, pa, pb = api.scene_to_device(uneven, ctx)
+    rng = np.random.default_rng(6)
+    ybar = torch.from_numpy(rng.normal(size=(batch.n_groups, 8)).astype(np.float32)).cuda()
+    saved = batch.saved_buffer()
+    y0 = batch.contacts(pa, pb, saved=saved).double().cpu().numpy()
+    g0 = batch.backward(pa, pb, ybar, saved=saved)[0].double().cpu().numpy()
+    tuning, log = tune.autotune(batch, pa, pb, ybar)
+    for kind, cands in (("items", tune.GROUP_CANDIDATES), ("forward", tune.FWD_CANDIDATES),
+                        ("reverse", tune.BWD_CANDIDATES)):
+        assert len(log[kind]) == len(cands)
+        assert any(isinstance(t, float) for t in log[kind].values()), kind
+    assert dict(groups=tuning["groups"]) in tune.GROUP_CANDIDATES
+    assert dict(item_vb=tuning["item_vb"], item_eb=tuning["item_eb"]) in tune.BWD_CANDIDATES
+    y = batch.contacts(pa, pb, saved=saved).double().cpu().numpy()
+    compare(y, y0, "autotuned", a_slack=weight_slack(uneven))
+    g = batch.backward(pa, pb, ybar, saved=saved)[0].double().cpu().numpy()
+    err = np.abs(g - g0).max(1)
+    assert np.all(err <= GRAD_RTOL * np.abs(g0).max(1) + 1e-6), float(err.max())
+    batch.close()
