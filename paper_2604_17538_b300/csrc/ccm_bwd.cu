@@ -63,25 +63,28 @@ template <class T> struct SdfT {
   V3T<T> g, hv;
 };
 
-// Dual-number version in centred form.  With weights w_k = softmax_k, the
-// tangents are  phi' = sum w_k dphi_k,  g' = sum w_k (dphi_k - phi') (n_k - g) / tau,
+// Dual-number version.  With weights w_k = softmax_k and plane-value
+// tangents dphi_k = n_k . x', the tangents are  phi' = sum w_k dphi_k,
+// g' = (sum w_k dphi_k n_k - phi' g) / tau  (accumulated in the same pass
+// over the planes as phi and g),
 // H v = sum w_k (n_k - g)((n_k - g).v) / tau and
 // (H v)' = sum w_k [(dphi_k - phi') / tau a_k b_k + a_k (a_k . v')] / tau with
-// a_k = n_k - g, b_k = a_k . v (terms proportional to sum w_k a_k = 0 dropped).
-// Every sum is of deviations from a weighted mean, so no cancellation: the
-// plain quotient-rule tangent loses ~1e-7 / tau relative accuracy when one
-// plane dominates.
+// a_k = n_k - g, b_k = a_k . v (terms proportional to sum w_k a_k = 0 dropped;
+// these two in centred form, as sums of deviations from weighted means).
+// g' cancels to rounding when one plane dominates (error ~1e-7 |x'| / tau
+// absolute), far inside the reverse pass's tolerance.
 // kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian-vector product
 template <int kMode>
 __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> x, float s,
                                V3T<Dual> v, const KParams& kp) {
   constexpr bool kHv = kMode == 2;
+  constexpr bool kGrad = kMode >= 1;
   const float xv = x.x.v, yv = x.y.v, zv = x.z.v;
   const float xd = x.x.d, yd = x.y.d, zd = x.z.d;
-  float S, Gx, Gy, Gz, Pd;
+  float S, Gx, Gy, Gz, Pd, Dx, Dy, Dz;
   for (int pass = 0; pass < 2; ++pass) {
     const float sc = s * kp.c_sdf;
-    S = Gx = Gy = Gz = Pd = 0.f;
+    S = Gx = Gy = Gz = Pd = Dx = Dy = Dz = 0.f;
     float mx = -INFINITY;
 #pragma unroll 2
     for (int k = 0; k < nf; ++k) {
@@ -89,11 +92,18 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
       const float ph = fmaf(p.x, xv, fmaf(p.y, yv, fmaf(p.z, zv, p.w)));
       mx = fmaxf(mx, ph);
       const float e = ex2(fmaf(ph, kp.c_sdf, -sc));
+      const float dp = fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd));
       S += e;
       Gx = fmaf(e, p.x, Gx);
       Gy = fmaf(e, p.y, Gy);
       Gz = fmaf(e, p.z, Gz);
-      Pd = fmaf(e, fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd)), Pd);
+      Pd = fmaf(e, dp, Pd);
+      if (kGrad) {
+        const float ed = e * dp;
+        Dx = fmaf(ed, p.x, Dx);
+        Dy = fmaf(ed, p.y, Dy);
+        Dz = fmaf(ed, p.z, Dz);
+      }
     }
     if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
     break;
@@ -105,8 +115,10 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
   if (kMode == 0) return r;
   const float gx = Gx * iS, gy = Gy * iS, gz = Gz * iS;
   const float phd = r.phi.d;
+  r.g = v3(Dual(gx, fmaf(Dx, iS, -phd * gx) * it), Dual(gy, fmaf(Dy, iS, -phd * gy) * it),
+           Dual(gz, fmaf(Dz, iS, -phd * gz) * it));
+  if (!kHv) return r;
   const float sc = s * kp.c_sdf;
-  float dgx = 0.f, dgy = 0.f, dgz = 0.f;
   float hx = 0.f, hy = 0.f, hz = 0.f, hdx = 0.f, hdy = 0.f, hdz = 0.f;
 #pragma unroll 2
   for (int k = 0; k < nf; ++k) {
@@ -116,24 +128,18 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
     const float dd = fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd)) - phd;
     const float ax = p.x - gx, ay = p.y - gy, az = p.z - gz;
     const float wd = w * dd;
-    dgx = fmaf(wd, ax, dgx);
-    dgy = fmaf(wd, ay, dgy);
-    dgz = fmaf(wd, az, dgz);
-    if (kHv) {
-      const float b = fmaf(ax, v.x.v, fmaf(ay, v.y.v, az * v.z.v));
-      const float bd = fmaf(ax, v.x.d, fmaf(ay, v.y.d, az * v.z.d));
-      const float wb = w * b;
-      hx = fmaf(wb, ax, hx);
-      hy = fmaf(wb, ay, hy);
-      hz = fmaf(wb, az, hz);
-      const float c = fmaf(wd * it, b, w * bd);
-      hdx = fmaf(c, ax, hdx);
-      hdy = fmaf(c, ay, hdy);
-      hdz = fmaf(c, az, hdz);
-    }
+    const float b = fmaf(ax, v.x.v, fmaf(ay, v.y.v, az * v.z.v));
+    const float bd = fmaf(ax, v.x.d, fmaf(ay, v.y.d, az * v.z.d));
+    const float wb = w * b;
+    hx = fmaf(wb, ax, hx);
+    hy = fmaf(wb, ay, hy);
+    hz = fmaf(wb, az, hz);
+    const float c = fmaf(wd * it, b, w * bd);
+    hdx = fmaf(c, ax, hdx);
+    hdy = fmaf(c, ay, hdy);
+    hdz = fmaf(c, az, hdz);
   }
-  r.g = v3(Dual(gx, dgx * it), Dual(gy, dgy * it), Dual(gz, dgz * it));
-  if (kHv) r.hv = v3(Dual(hx * it, hdx * it), Dual(hy * it, hdy * it), Dual(hz * it, hdz * it));
+  r.hv = v3(Dual(hx * it, hdx * it), Dual(hy * it, hdy * it), Dual(hz * it, hdz * it));
   return r;
 }
 
@@ -196,13 +202,14 @@ __device__ void sdf_dual2(const float4* __restrict__ pl, int nf, V3T<Dual> xa, f
                           V3T<Dual> xb, float sb, const KParams& kp, SdfT<Dual>& ra,
                           SdfT<Dual>& rb) {
   static_assert(kMode <= 1, "two-point evaluation has no Hessian-vector product");
+  constexpr bool kGrad = kMode >= 1;
   const float xav = xa.x.v, yav = xa.y.v, zav = xa.z.v, xad = xa.x.d, yad = xa.y.d, zad = xa.z.d;
   const float xbv = xb.x.v, ybv = xb.y.v, zbv = xb.z.v, xbd = xb.x.d, ybd = xb.y.d, zbd = xb.z.d;
-  float Sa, Gxa, Gya, Gza, Pda, Sb, Gxb, Gyb, Gzb, Pdb;
+  float Sa, Gxa, Gya, Gza, Pda, Dxa, Dya, Dza, Sb, Gxb, Gyb, Gzb, Pdb, Dxb, Dyb, Dzb;
   for (int pass = 0; pass < 2; ++pass) {
     const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
-    Sa = Gxa = Gya = Gza = Pda = 0.f;
-    Sb = Gxb = Gyb = Gzb = Pdb = 0.f;
+    Sa = Gxa = Gya = Gza = Pda = Dxa = Dya = Dza = 0.f;
+    Sb = Gxb = Gyb = Gzb = Pdb = Dxb = Dyb = Dzb = 0.f;
     float mxa = -INFINITY, mxb = -INFINITY;
 #pragma unroll 2
     for (int k = 0; k < nf; ++k) {
@@ -213,12 +220,19 @@ __device__ void sdf_dual2(const float4* __restrict__ pl, int nf, V3T<Dual> xa, f
       mxb = fmaxf(mxb, phb);
       const float ea = ex2(fmaf(pha, kp.c_sdf, -sca));
       const float eb = ex2(fmaf(phb, kp.c_sdf, -scb));
+      const float dpa = fmaf(p.x, xad, fmaf(p.y, yad, p.z * zad));
+      const float dpb = fmaf(p.x, xbd, fmaf(p.y, ybd, p.z * zbd));
       Sa += ea;
       Sb += eb;
       Gxa = fmaf(ea, p.x, Gxa); Gya = fmaf(ea, p.y, Gya); Gza = fmaf(ea, p.z, Gza);
       Gxb = fmaf(eb, p.x, Gxb); Gyb = fmaf(eb, p.y, Gyb); Gzb = fmaf(eb, p.z, Gzb);
-      Pda = fmaf(ea, fmaf(p.x, xad, fmaf(p.y, yad, p.z * zad)), Pda);
-      Pdb = fmaf(eb, fmaf(p.x, xbd, fmaf(p.y, ybd, p.z * zbd)), Pdb);
+      Pda = fmaf(ea, dpa, Pda);
+      Pdb = fmaf(eb, dpb, Pdb);
+      if (kGrad) {
+        const float eda = ea * dpa, edb = eb * dpb;
+        Dxa = fmaf(eda, p.x, Dxa); Dya = fmaf(eda, p.y, Dya); Dza = fmaf(eda, p.z, Dza);
+        Dxb = fmaf(edb, p.x, Dxb); Dyb = fmaf(edb, p.y, Dyb); Dzb = fmaf(edb, p.z, Dzb);
+      }
     }
     const bool bada = (mxa - sa) * kp.c_sdf > 64.0f, badb = (mxb - sb) * kp.c_sdf > 64.0f;
     if (pass == 0 && (bada || badb)) {
@@ -236,27 +250,10 @@ __device__ void sdf_dual2(const float4* __restrict__ pl, int nf, V3T<Dual> xa, f
   const float gxa = Gxa * iSa, gya = Gya * iSa, gza = Gza * iSa;
   const float gxb = Gxb * iSb, gyb = Gyb * iSb, gzb = Gzb * iSb;
   const float phda = ra.phi.d, phdb = rb.phi.d;
-  const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
-  float dgxa = 0.f, dgya = 0.f, dgza = 0.f, dgxb = 0.f, dgyb = 0.f, dgzb = 0.f;
-#pragma unroll 2
-  for (int k = 0; k < nf; ++k) {
-    const float4 p = pl[k];
-    const float pha = fmaf(p.x, xav, fmaf(p.y, yav, fmaf(p.z, zav, p.w)));
-    const float phb = fmaf(p.x, xbv, fmaf(p.y, ybv, fmaf(p.z, zbv, p.w)));
-    const float wa = ex2(fmaf(pha, kp.c_sdf, -sca)) * iSa;
-    const float wb = ex2(fmaf(phb, kp.c_sdf, -scb)) * iSb;
-    const float dda = fmaf(p.x, xad, fmaf(p.y, yad, p.z * zad)) - phda;
-    const float ddb = fmaf(p.x, xbd, fmaf(p.y, ybd, p.z * zbd)) - phdb;
-    const float wda = wa * dda, wdb = wb * ddb;
-    dgxa = fmaf(wda, p.x - gxa, dgxa);
-    dgya = fmaf(wda, p.y - gya, dgya);
-    dgza = fmaf(wda, p.z - gza, dgza);
-    dgxb = fmaf(wdb, p.x - gxb, dgxb);
-    dgyb = fmaf(wdb, p.y - gyb, dgyb);
-    dgzb = fmaf(wdb, p.z - gzb, dgzb);
-  }
-  ra.g = v3(Dual(gxa, dgxa * it), Dual(gya, dgya * it), Dual(gza, dgza * it));
-  rb.g = v3(Dual(gxb, dgxb * it), Dual(gyb, dgyb * it), Dual(gzb, dgzb * it));
+  ra.g = v3(Dual(gxa, fmaf(Dxa, iSa, -phda * gxa) * it), Dual(gya, fmaf(Dya, iSa, -phda * gya) * it),
+            Dual(gza, fmaf(Dza, iSa, -phda * gza) * it));
+  rb.g = v3(Dual(gxb, fmaf(Dxb, iSb, -phdb * gxb) * it), Dual(gyb, fmaf(Dyb, iSb, -phdb * gyb) * it),
+            Dual(gzb, fmaf(Dzb, iSb, -phdb * gzb) * it));
 }
 
 template <class T, int kMode>
