@@ -63,16 +63,16 @@ template <class T> struct SdfT {
   V3T<T> g, hv;
 };
 
-// Dual-number version.  With weights w_k = softmax_k and plane-value
-// tangents dphi_k = n_k . x', the tangents are  phi' = sum w_k dphi_k,
-// g' = (sum w_k dphi_k n_k - phi' g) / tau  (accumulated in the same pass
-// over the planes as phi and g),
-// H v = sum w_k (n_k - g)((n_k - g).v) / tau and
-// (H v)' = sum w_k [(dphi_k - phi') / tau a_k b_k + a_k (a_k . v')] / tau with
-// a_k = n_k - g, b_k = a_k . v (terms proportional to sum w_k a_k = 0 dropped;
-// these two in centred form, as sums of deviations from weighted means).
-// g' cancels to rounding when one plane dominates (error ~1e-7 |x'| / tau
-// absolute), far inside the reverse pass's tolerance.
+// Dual-number version, one pass over the planes.  With unnormalised weights
+// e_k = 2^((phi_k - s) c), S = sum e_k, w_k = e_k / S and plane-value tangents
+// dphi_k = n_k . x':  phi' = sum w_k dphi_k,  g' = (D / S - phi' g) / tau with
+// D = sum e_k dphi_k n_k, and for the Hessian-vector product
+// H v = (A / S - g (g . v)) / tau with A = sum e_k (n_k . v) n_k, whose tangent
+// (w_k' = w_k (dphi_k - phi') / tau) is
+// (H v)' = [(B - phi' A) / (S tau) + C / S - g' (g . v) - g (g' . v + g . v')] / tau,
+// B = sum e_k dphi_k (n_k . v) n_k, C = sum e_k (n_k . v') n_k.  The sums
+// cancel to rounding where one plane dominates (absolute error ~1e-7 |x'| / tau),
+// far inside the reverse pass's tolerance.
 // kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian-vector product
 template <int kMode>
 __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> x, float s,
@@ -81,10 +81,11 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
   constexpr bool kGrad = kMode >= 1;
   const float xv = x.x.v, yv = x.y.v, zv = x.z.v;
   const float xd = x.x.d, yd = x.y.d, zd = x.z.d;
-  float S, Gx, Gy, Gz, Pd, Dx, Dy, Dz;
+  float S, Gx, Gy, Gz, Pd, Dx, Dy, Dz, Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
   for (int pass = 0; pass < 2; ++pass) {
     const float sc = s * kp.c_sdf;
     S = Gx = Gy = Gz = Pd = Dx = Dy = Dz = 0.f;
+    Ax = Ay = Az = Bx = By = Bz = Cx = Cy = Cz = 0.f;
     float mx = -INFINITY;
 #pragma unroll 2
     for (int k = 0; k < nf; ++k) {
@@ -104,6 +105,14 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
         Dy = fmaf(ed, p.y, Dy);
         Dz = fmaf(ed, p.z, Dz);
       }
+      if (kHv) {
+        const float q = fmaf(p.x, v.x.v, fmaf(p.y, v.y.v, p.z * v.z.v));
+        const float qd = fmaf(p.x, v.x.d, fmaf(p.y, v.y.d, p.z * v.z.d));
+        const float eq = e * q, eqd = eq * dp, ew = e * qd;
+        Ax = fmaf(eq, p.x, Ax); Ay = fmaf(eq, p.y, Ay); Az = fmaf(eq, p.z, Az);
+        Bx = fmaf(eqd, p.x, Bx); By = fmaf(eqd, p.y, By); Bz = fmaf(eqd, p.z, Bz);
+        Cx = fmaf(ew, p.x, Cx); Cy = fmaf(ew, p.y, Cy); Cz = fmaf(ew, p.z, Cz);
+      }
     }
     if (pass == 0 && (mx - s) * kp.c_sdf > 64.0f) { s = mx; continue; }
     break;
@@ -115,31 +124,20 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
   if (kMode == 0) return r;
   const float gx = Gx * iS, gy = Gy * iS, gz = Gz * iS;
   const float phd = r.phi.d;
-  r.g = v3(Dual(gx, fmaf(Dx, iS, -phd * gx) * it), Dual(gy, fmaf(Dy, iS, -phd * gy) * it),
-           Dual(gz, fmaf(Dz, iS, -phd * gz) * it));
+  const float gdx = fmaf(Dx, iS, -phd * gx) * it, gdy = fmaf(Dy, iS, -phd * gy) * it,
+              gdz = fmaf(Dz, iS, -phd * gz) * it;
+  r.g = v3(Dual(gx, gdx), Dual(gy, gdy), Dual(gz, gdz));
   if (!kHv) return r;
-  const float sc = s * kp.c_sdf;
-  float hx = 0.f, hy = 0.f, hz = 0.f, hdx = 0.f, hdy = 0.f, hdz = 0.f;
-#pragma unroll 2
-  for (int k = 0; k < nf; ++k) {
-    const float4 p = pl[k];
-    const float ph = fmaf(p.x, xv, fmaf(p.y, yv, fmaf(p.z, zv, p.w)));
-    const float w = ex2(fmaf(ph, kp.c_sdf, -sc)) * iS;
-    const float dd = fmaf(p.x, xd, fmaf(p.y, yd, p.z * zd)) - phd;
-    const float ax = p.x - gx, ay = p.y - gy, az = p.z - gz;
-    const float wd = w * dd;
-    const float b = fmaf(ax, v.x.v, fmaf(ay, v.y.v, az * v.z.v));
-    const float bd = fmaf(ax, v.x.d, fmaf(ay, v.y.d, az * v.z.d));
-    const float wb = w * b;
-    hx = fmaf(wb, ax, hx);
-    hy = fmaf(wb, ay, hy);
-    hz = fmaf(wb, az, hz);
-    const float c = fmaf(wd * it, b, w * bd);
-    hdx = fmaf(c, ax, hdx);
-    hdy = fmaf(c, ay, hdy);
-    hdz = fmaf(c, az, hdz);
-  }
-  r.hv = v3(Dual(hx * it, hdx * it), Dual(hy * it, hdy * it), Dual(hz * it, hdz * it));
+  const float gv = fmaf(gx, v.x.v, fmaf(gy, v.y.v, gz * v.z.v));
+  const float gdv = fmaf(gdx, v.x.v, fmaf(gdy, v.y.v, gdz * v.z.v)) +
+                    fmaf(gx, v.x.d, fmaf(gy, v.y.d, gz * v.z.d));
+  const float iSt = iS * it;
+  r.hv = v3(Dual(fmaf(Ax, iS, -gx * gv) * it,
+                 (fmaf(fmaf(-phd, Ax, Bx), iSt, fmaf(Cx, iS, -fmaf(gdx, gv, gx * gdv)))) * it),
+            Dual(fmaf(Ay, iS, -gy * gv) * it,
+                 (fmaf(fmaf(-phd, Ay, By), iSt, fmaf(Cy, iS, -fmaf(gdy, gv, gy * gdv)))) * it),
+            Dual(fmaf(Az, iS, -gz * gv) * it,
+                 (fmaf(fmaf(-phd, Az, Bz), iSt, fmaf(Cz, iS, -fmaf(gdz, gv, gz * gdv)))) * it));
   return r;
 }
 
