@@ -573,31 +573,46 @@ void merge_maxima(BatchMaxima* m, const BatchMaxima& b) {
   m->f_edges = std::max(m->f_edges, b.f_edges);
 }
 
+void body_chunks(const Context& c, int32_t body, const UnitShape& us,
+                 std::vector<PieceChunk>* out) {
+  const BodyRec& F = c.bodies[body];
+  // the kernels' chunking: at most us.groups pieces within the budgets
+  for (int fc0 = 0; fc0 < F.np;) {
+    int fc1 = fc0, V = 0, E = 0;
+    int64_t feats = 0;
+    while (fc1 < F.np && fc1 - fc0 < us.groups) {
+      const PieceRec& p = c.pieces[F.p0 + fc1];
+      if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
+      V += p.nv;
+      E += p.ne;
+      feats += p.nv + p.ne;
+      ++fc1;
+    }
+    out->push_back(PieceChunk{(uint16_t)fc0, (uint16_t)fc1, feats});
+    fc0 = fc1;
+  }
+}
+
+void push_items(const std::vector<PieceChunk>& chunks, int32_t unit, int32_t s_np,
+                std::vector<WorkItem>* items, std::vector<int64_t>* cost) {
+  for (const PieceChunk& ch : chunks) {
+    items->push_back(WorkItem{unit, ch.fc0, ch.fc1});
+    // directions, plus features times SDF pieces, plus staging S
+    cost->push_back((int64_t)(ch.fc1 - ch.fc0) * s_np + ch.feats * s_np / 8 + s_np);
+  }
+}
+
 void make_items(const Context& c, const PairRec* pairs, int64_t n, int64_t unit_pair0,
                 const UnitShape& us, std::vector<WorkItem>* items, std::vector<int64_t>* cost,
                 std::vector<int64_t>* item_off) {
+  std::vector<PieceChunk> ch;
   for (int64_t i = 0; i < n; ++i) {
     for (int side = 0; side < 2; ++side) {
-      const BodyRec& F = c.bodies[side == 0 ? pairs[i].bodyA : pairs[i].bodyB];
-      const BodyRec& S = c.bodies[side == 0 ? pairs[i].bodyB : pairs[i].bodyA];
-      // the kernels' chunking: at most us.groups pieces within the budgets
-      for (int fc0 = 0; fc0 < F.np;) {
-        int fc1 = fc0, V = 0, E = 0;
-        int64_t feats = 0;
-        while (fc1 < F.np && fc1 - fc0 < us.groups) {
-          const PieceRec& p = c.pieces[F.p0 + fc1];
-          if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
-          V += p.nv;
-          E += p.ne;
-          feats += p.nv + p.ne;
-          ++fc1;
-        }
-        items->push_back(WorkItem{(int32_t)(2 * (unit_pair0 + i) + side), (uint16_t)fc0,
-                                  (uint16_t)fc1});
-        // directions, plus features times SDF pieces, plus staging S
-        cost->push_back((int64_t)(fc1 - fc0) * S.np + feats * S.np / 8 + S.np);
-        fc0 = fc1;
-      }
+      const int32_t f = side == 0 ? pairs[i].bodyA : pairs[i].bodyB;
+      const int32_t s = side == 0 ? pairs[i].bodyB : pairs[i].bodyA;
+      ch.clear();
+      body_chunks(c, f, us, &ch);
+      push_items(ch, (int32_t)(2 * (unit_pair0 + i) + side), c.bodies[s].np, items, cost);
     }
     if (item_off) item_off->push_back((int64_t)items->size());
   }

@@ -91,6 +91,19 @@ ccm_status cuda_fail(cudaError_t e, const char* what);
 ccm_status make_kparams(const ccm_params* p, KParams* k);
 BatchMaxima body_maxima(const Context& c, int32_t body);
 void merge_maxima(BatchMaxima* m, const BatchMaxima& b);
+// A run of feature pieces [fc0, fc1) of one body that one work item covers
+// (at most us.groups pieces within the vertex and edge budgets), with its
+// vertex + edge count.
+struct PieceChunk {
+  uint16_t fc0, fc1;
+  int64_t feats;
+};
+void body_chunks(const Context& c, int32_t body, const UnitShape& us,
+                 std::vector<PieceChunk>* out);
+// The items (and estimated costs) of unit `unit` from its feature body's
+// chunks against an SDF body of s_np pieces.
+void push_items(const std::vector<PieceChunk>& chunks, int32_t unit, int32_t s_np,
+                std::vector<WorkItem>* items, std::vector<int64_t>* cost);
 // Work items of the n pairs for shape `us`, appended in pair order: unit
 // indices are 2 (unit_pair0 + i) + side; cost[] gets each item's estimated
 // cost and item_off[] (if not NULL) the running item count after each pair.

@@ -104,6 +104,7 @@ struct Serving {
   BatchMaxima mx;                  // largest pieces the launch shape holds
   bool per_pair = false;           // per-pair reverse pass (every body <= kHitS pieces)
   std::vector<int8_t> fit_cache;   // per body: -1 unknown, 0 no, 1 yes (ctx->mu held)
+  std::vector<std::vector<PieceChunk>> chunk_cache;   // per body, under `us` (ctx->mu held)
   WaveSet sets[2];
   std::thread worker;
   std::mutex mu;
@@ -127,6 +128,16 @@ struct Serving {
                      (!per_pair || m.s_pieces <= kHitS);
     }
     return fit_cache[b] == 1;
+  }
+
+  // A body's feature-piece chunks under the serving shape, computed once: a
+  // submission then builds its items from a few chunks per pair side instead
+  // of walking every piece.
+  const std::vector<PieceChunk>& chunks(const Context& c, int32_t b) {
+    if ((size_t)b >= chunk_cache.size()) chunk_cache.resize(c.bodies.size());
+    std::vector<PieceChunk>& v = chunk_cache[b];
+    if (v.empty()) body_chunks(c, b, us, &v);
+    return v;
   }
 };
 
@@ -676,7 +687,15 @@ ccm_status ccm_submit(ccm_ctx ctx, const ccm_request* req, ccm_ticket* out) {
     }
     p.item_off.assign(1, 0);
     std::vector<int64_t> cost;
-    make_items(*c, p.pairs.data(), req->n_pairs, 0, sv->us, &p.items, &cost, &p.item_off);
+    p.items.reserve(2 * req->n_pairs);
+    cost.reserve(2 * req->n_pairs);
+    p.item_off.reserve(req->n_pairs + 1);
+    for (int64_t i = 0; i < req->n_pairs; ++i) {   // make_items, from the cached chunks
+      const int32_t a = p.pairs[i].bodyA, b = p.pairs[i].bodyB;
+      push_items(sv->chunks(*c, a), (int32_t)(2 * i), c->bodies[b].np, &p.items, &cost);
+      push_items(sv->chunks(*c, b), (int32_t)(2 * i + 1), c->bodies[a].np, &p.items, &cost);
+      p.item_off.push_back((int64_t)p.items.size());
+    }
     p.pcls.resize(req->n_pairs);
     for (int64_t i = 0; i < req->n_pairs; ++i) {
       int64_t pc = 0;
