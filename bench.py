@@ -61,11 +61,14 @@ def work_model(c, cv, ch):
 
 
 def kernel_source_hash():
-    """sha256 of the CUDA sources, to tell whether recorded ncu counters still apply."""
+    """sha256 of the contact kernels' device sources (the forward and reverse
+    kernels and the headers they include, not the host-side runtime), to
+    tell whether recorded ncu counters still apply."""
     import glob
     import hashlib
     d = os.path.join(ROOT, "paper_2604_17538_b300", "csrc")
-    files = sorted(glob.glob(os.path.join(d, "*.cu*"))) + sorted(glob.glob(os.path.join(d, "*.h")))
+    files = sorted(glob.glob(os.path.join(d, "*.cuh"))) + [
+        os.path.join(d, f) for f in ("ccm_fwd.cu", "ccm_fwd.h", "ccm_bwd.cu", "ccm_bwd.h")]
     return hashlib.sha256(b"".join(open(f, "rb").read() for f in files)).hexdigest()
 
 
