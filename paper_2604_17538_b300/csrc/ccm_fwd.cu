@@ -272,23 +272,27 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
     const float margin = 1e-6f * (1.0f + fabsf(tr[0]) + fabsf(tr[1]) + fabsf(tr[2]));
 
     for (int fc0 = it.fc0; fc0 < it.fc1;) {
-      // F chunk [fc0, fc1): up to us.groups pieces within the vertex / edge
-      // budgets (the host cut the item to one such chunk)
-      int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < it.fc1 && fc1 - fc0 < us.groups) {
-        const PieceRec p = g.pieces[F.p0 + fc1];
-        if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
-        V += p.nv;
-        E += p.ne;
-        ++fc1;
+      // F chunk [fc0, fc1): up to us.groups (<= 32) pieces within the vertex /
+      // edge budgets (the host cut the item to one such chunk), read one per
+      // lane: the chunk is the prefix of lanes whose running sums fit
+      PieceRec p{};
+      const bool valid = fc0 + lane < it.fc1 && lane < us.groups;
+      if (valid) p = g.pieces[F.p0 + fc0 + lane];
+      int iv = valid ? p.nv : 0, ie = valid ? p.ne : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
+        if (lane >= o) { iv += a; ie += b; }
       }
-      const int nfc = fc1 - fc0;
+      const bool in_chunk = valid && iv <= us.vert_budget && ie <= us.edge_budget;
+      const int nfc = __popc(__ballot_sync(kFull, in_chunk));   // a prefix of the lanes
       if (nfc == 0) break;   // unreachable: the host sizes the budgets >= every piece
-      const PieceRec pfirst = g.pieces[F.p0 + fc0];
+      const int fc1 = fc0 + nfc;
+      const int V = __shfl_sync(kFull, iv, nfc - 1), E = __shfl_sync(kFull, ie, nfc - 1);
+      const int pv0 = __shfl_sync(kFull, p.v0, 0), pe0 = __shfl_sync(kFull, p.e0, 0);
       __syncwarp();   // the previous chunk's data is no longer read
       if (lane < nfc) {
-        const PieceRec p = g.pieces[F.p0 + fc0 + lane];
-        sl.fp[lane] = make_int4(p.v0 - pfirst.v0, p.nv, p.e0 - pfirst.e0, p.ne);
+        sl.fp[lane] = make_int4(p.v0 - pv0, p.nv, p.e0 - pe0, p.ne);
         const float3 c = xform(Rr, tr, p.sphere);
         sl.fs[lane] = make_float4(c.x, c.y, c.z, p.sphere.w);
         part_zero(sl.acc[lane]);
@@ -296,32 +300,39 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
       }
       for (int i = lane; i < V; i += 64) {   // two loads in flight per lane
         const bool two = i + 32 < V;
-        const float4 v0 = __ldg(g.verts + pfirst.v0 + i);
-        const float4 v1 = two ? __ldg(g.verts + pfirst.v0 + i + 32) : v0;
+        const float4 v0 = __ldg(g.verts + pv0 + i);
+        const float4 v1 = two ? __ldg(g.verts + pv0 + i + 32) : v0;
         const float3 x0 = xform(Rr, tr, v0), x1 = xform(Rr, tr, v1);
         sl.xs[i] = make_float4(x0.x, x0.y, x0.z, 0.f);
         if (two) sl.xs[i + 32] = make_float4(x1.x, x1.y, x1.z, 0.f);
       }
-      stage_copy(sl.edges, g.edges + pfirst.e0, E, lane);
+      stage_copy(sl.edges, g.edges + pe0, E, lane);
 
       for (int sc0 = 0; sc0 < S.np;) {
-        // S chunk [sc0, sc1) within the plane / piece budgets
+        // S chunk [sc0, sc1) within the plane / piece budgets: pieces read 32
+        // at a time (one per lane); the chunk ends before the first piece whose
+        // planes overflow.  A body's planes are contiguous, piece after piece.
         int sc1 = sc0, P = 0;
+        __syncwarp();   // the previous S chunk's planes are no longer read
         while (sc1 < S.np && sc1 - sc0 < us.spiece_budget) {
-          const int nf = g.pieces[S.p0 + sc1].nf;
-          if (P + nf > us.plane_budget) break;
-          P += nf;
-          ++sc1;
+          const int si = sc1 + lane;
+          const int nf = si < S.np && si - sc0 < us.spiece_budget ? g.pieces[S.p0 + si].nf : 0;
+          int incl = nf;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+          }
+          const bool fits = nf > 0 && P + incl <= us.plane_budget;
+          const int take = __popc(__ballot_sync(kFull, fits));   // a prefix of the lanes
+          if (fits) sl.sp[si - sc0] = make_int2(P + incl - nf, nf);
+          if (take > 0) P += __shfl_sync(kFull, incl, take - 1);
+          sc1 += take;
+          if (take < 32) break;
         }
         const int nsc = sc1 - sc0;
         if (nsc == 0) break;   // unreachable, as above
-        const int f_first = g.pieces[S.p0 + sc0].f0;
-        __syncwarp();   // the previous S chunk's planes are no longer read
-        for (int q = lane; q < nsc; q += 32) {
-          const PieceRec p = g.pieces[S.p0 + sc0 + q];
-          sl.sp[q] = make_int2(p.f0 - f_first, p.nf);
-        }
-        stage_copy(sl.planes, g.planes + f_first, P, lane);
+        stage_copy(sl.planes, g.planes + g.pieces[S.p0 + sc0].f0, P, lane);
         __syncwarp();
 
         // gate the directions (fc, sc), 32 at a time, collecting live ones
