@@ -61,6 +61,7 @@ struct Pending {
   std::vector<uint8_t> pcls;      // cost class per pair (sum of its items' costs)
   std::vector<int64_t> item_off;  // [n + 1], from 0
   ReqDesc d;
+  double t_submit = 0.0;
 };
 
 enum TicketState { kQueued = 0, kRunning = 1, kDone = 2 };
@@ -115,6 +116,7 @@ struct Serving {
   std::unordered_map<uint64_t, TicketInfo> tickets;
   std::deque<uint64_t> completed;   // done, in completion order, until retired
   uint64_t next_ticket = 1;
+  int64_t queued_pairs = 0;         // body pairs of the queued requests
   ccm_serve_counters counters{};
   cudaError_t async_error = cudaSuccess;
 
@@ -140,6 +142,10 @@ struct Serving {
     return v;
   }
 };
+
+// Longest wait of a queued request for a running wave before a second,
+// overlapping wave is launched for it (seconds).
+constexpr double kSecondWaveWait = 0.25e-3;
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -368,6 +374,7 @@ static void launch_wave(Serving* sv, WaveSet& s, std::unique_lock<std::mutex>& l
       G += q.d.G;
       I += ni;
       sv->tickets[q.ticket].state = kRunning;
+      sv->queued_pairs -= q.d.n;
       take.push_back(std::move(sv->queue.front()));
       sv->queue.pop_front();
     }
@@ -512,15 +519,29 @@ static void worker_main(Serving* sv) {
     }
     if (sv->stop) sv->held = false;   // stopping runs what is queued
     for (WaveSet& s : sv->sets) {
-      if (!s.busy && !sv->held && !sv->queue.empty()) {
-        launch_wave(sv, s, lk);
-        progressed = true;
-      }
+      if (s.busy || sv->held || sv->queue.empty()) continue;
+      // With the other set's wave still running, a second wave goes out only
+      // for a queue that fills half a wave, or whose oldest request has
+      // waited kSecondWaveWait: otherwise the queue waits for the running
+      // wave and leaves as one larger wave (fewer, larger waves under load,
+      // no added wait on an idle loop).
+      const bool other_busy = sv->sets[0].busy || sv->sets[1].busy;
+      if (other_busy && !sv->stop && 2 * sv->queued_pairs < sv->cap_pairs &&
+          now_s() - sv->queue.front().t_submit < kSecondWaveWait)
+        continue;
+      launch_wave(sv, s, lk);
+      progressed = true;
     }
     const bool any_busy = sv->sets[0].busy || sv->sets[1].busy;
     if (sv->stop && sv->queue.empty() && !any_busy) break;
-    // woken by a submit, a hold change, a stop or a wave's completion callback
-    if (!progressed) sv->cv.wait_for(lk, std::chrono::milliseconds(50));
+    // woken by a submit, a hold change, a stop or a wave's completion
+    // callback; a queue held back for a running wave is looked at again
+    // when its oldest request has waited kSecondWaveWait
+    if (!progressed) {
+      const bool waiting = !sv->queue.empty() && !sv->held;
+      sv->cv.wait_for(lk, waiting ? std::chrono::microseconds(100)
+                                  : std::chrono::microseconds(50000));
+    }
   }
 }
 
@@ -716,8 +737,10 @@ ccm_status ccm_submit(ccm_ctx ctx, const ccm_request* req, ccm_ticket* out) {
   if ((int64_t)sv->queue.size() >= sv->cfg.max_queued)
     return fail(CCM_ERR_BUSY, "request queue full (%lld)", (long long)sv->cfg.max_queued);
   p.ticket = sv->next_ticket++;
-  sv->tickets[p.ticket] = TicketInfo{kQueued, now_s(), 0.0};
+  p.t_submit = now_s();
+  sv->tickets[p.ticket] = TicketInfo{kQueued, p.t_submit, 0.0};
   *out = p.ticket;
+  sv->queued_pairs += p.d.n;
   sv->queue.push_back(std::move(p));
   sv->cv.notify_one();
   return CCM_OK;
