@@ -678,14 +678,18 @@ void default_tuning(ccm_tuning* t) {
 ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   if (t.item_v < 1 || t.item_e < 1 || t.item_vb < 1 || t.item_eb < 1 || t.item_v > 8192 ||
       t.item_e > 16384 || t.item_vb > 8192 || t.item_eb > 16384 || t.fwd_warps < 1 ||
-      t.fwd_warps > 4 || t.groups < 1 || t.groups > kGroupsPerChunk)
+      t.fwd_warps > 4 || t.groups < 1 || t.groups > kGroupsPerChunk ||
+      (t.stage_planes != 0 && (t.stage_planes < 16 || t.stage_planes > 4096)) ||
+      (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)))
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
-  us.plane_budget = std::max(mx.fmax, std::min(mx.s_planes, 1024));
+  const int cap_p = t.stage_planes ? t.stage_planes : 1024;
+  const int cap_v = t.stage_verts ? t.stage_verts : 512;
+  us.plane_budget = std::max(mx.fmax, std::min(mx.s_planes, cap_p));
   us.spiece_budget = std::min(mx.s_pieces, 256);
-  us.vert_budget = std::max(mx.vmax, std::min(mx.f_verts, 512));
-  us.edge_budget = std::max(mx.emax, std::min(mx.f_edges, 1536));
+  us.vert_budget = std::max(mx.vmax, std::min(mx.f_verts, cap_v));
+  us.edge_budget = std::max(mx.emax, std::min(mx.f_edges, 3 * cap_v));
   us.item_v = std::max(mx.vmax, t.item_v);
   us.item_e = std::max(mx.emax, t.item_e);
   us.item_vb = std::max(mx.vmax, t.item_vb);

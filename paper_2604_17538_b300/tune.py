@@ -3,10 +3,11 @@
 Times the passes of a batch on its own poses and keeps the fastest shape; the
 choice is written back into the batch.  First the work-item size (feature
 pieces per warp task: small items balance uneven bodies over the warps, large
-ones stage the SDF body's planes fewer times), timed on forward + reverse
-pass together since both passes run the same items; then the forward's and
-the reverse pass's shared-memory budgets, which trade lane utilisation (bigger
-lists of live piece pairs) against resident warps (smaller slices).
+ones stage the SDF body's planes fewer times) and then the staging budgets
+(planes and vertices held at once: smaller slices, more resident warps, more
+chunks), each timed on forward + reverse pass together since both passes use
+them; then the forward's and the reverse pass's list budgets, which trade lane
+utilisation (bigger lists of live piece pairs) against resident warps.
 """
 from __future__ import annotations
 
@@ -16,6 +17,10 @@ FWD_CANDIDATES = [dict(item_v=v, item_e=e, fwd_warps=w)
                   for (v, e), w in itertools.product([(128, 256), (256, 512), (512, 1024)], [1, 2, 4])]
 BWD_CANDIDATES = [dict(item_vb=v, item_eb=e) for v, e in [(64, 128), (128, 256), (256, 512), (512, 1024)]]
 GROUP_CANDIDATES = [dict(groups=g) for g in (4, 8, 16, 32)]
+# staging budgets (planes of an SDF-body chunk, vertices of a feature chunk):
+# smaller slices keep more warps resident on bodies with many large pieces
+STAGE_CANDIDATES = [dict(stage_planes=p, stage_verts=v)
+                    for p, v in [(0, 0), (512, 256), (256, 128), (128, 64)]]
 
 
 def _time(fn, reps=5):
@@ -43,7 +48,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
     calls.  The record does not depend on the shape, so one serves every
     reverse-pass candidate."""
     import torch
-    log = {"items": {}, "forward": {}, "reverse": {}}
+    log = {"items": {}, "stage": {}, "forward": {}, "reverse": {}}
     if ybar is None:
         ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
     rec = batch.saved_buffer(pose_a.device) if saved else None
@@ -65,6 +70,18 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
         if gbest is None or t < gbest[0]:
             gbest = (t, cand)
     batch.set_tuning(**gbest[1])
+    sbest = None
+    for cand in STAGE_CANDIDATES:
+        try:
+            batch.set_tuning(**cand)
+            t = _time(lambda: (fwd(), bwd()))
+        except Exception as ex:
+            log["stage"][str(cand)] = repr(ex)
+            continue
+        log["stage"][str(cand)] = t
+        if sbest is None or t < sbest[0]:
+            sbest = (t, cand)
+    batch.set_tuning(**sbest[1])
     best = None
     for cand in FWD_CANDIDATES:
         try:
