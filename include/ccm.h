@@ -128,6 +128,9 @@ CCM_API ccm_status ccm_output_size(ccm_ctx ctx, int64_t n, const ccm_geom* A, co
  * unit that ccm_contacts and ccm_contacts_backward run on; poses change
  * between calls, pairs do not.  Calls on one batch share its workspace
  * (reverse-pass slots, work counters): issue them in order on one stream.
+ * The one exception: after a ccm_contacts_save, a ccm_contacts_backward_saved
+ * without dir and one with dir (separate output buffers) may run
+ * concurrently on two streams when every body has at most 256 pieces.
  * Synchronous; allocates.
  * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_batch_create(ccm_ctx ctx, int64_t n, const ccm_geom* A, const ccm_geom* B,
@@ -208,7 +211,9 @@ CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pos
  * the host: copies pose_a, pose_b (host [n,12]) and, if given, ybar (host
  * [G,8]) and dir (host [n,12]) into device buffers the batch owns, runs
  * ccm_contacts_save, then (with dir) the H dir / J dir pass and (with ybar)
- * the gradient pass of ccm_contacts_backward_saved, and copies back y (host
+ * the gradient pass of ccm_contacts_backward_saved (on a per-pair batch,
+ * every body <= 256 pieces, the two passes run concurrently on two
+ * streams), and copies back y (host
  * [G,8]), grad (host [n,12]; required with ybar) and, with dir, hvp (host
  * [n,12]; required) and jvp (host [G,8]; optional).  Results are those of
  * the device calls on the same data.  The ybar / dir copies run on a second

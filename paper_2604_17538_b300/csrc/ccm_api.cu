@@ -443,9 +443,16 @@ ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const fl
   CCM_CUDA(cudaEventRecord(h.ev[2], st), "event");
   CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[2], 0), "wait");
   CCM_CUDA(cudaMemcpyAsync(y, yd, G8, out, h.cout), "output copy");
+  // With dir on a per-pair batch the gradient pass runs on the input-copy
+  // stream, concurrently with the H u pass (they count their work on separate
+  // words; the per-item path shares its slots, so there both stay in order on
+  // `stream`, the H u pass first so that its larger outputs copy back during
+  // the gradient pass).
+  const bool conc = ybar && dir && b->per_pair;
   if (ybar) {
     CCM_CUDA(cudaStreamWaitEvent(st, h.ev[1], 0), "wait");
-    if (dir) {   // the H u / J u pass first: its larger outputs copy back during the gradient pass
+    if (conc) CCM_CUDA(cudaStreamWaitEvent(h.cin, h.ev[2], 0), "wait");
+    if (dir) {
       float* hd = static_cast<float*>(h.hvp.ptr);
       float* jd = jvp ? static_cast<float*>(h.jvp.ptr) : nullptr;
       if ((s = run_backward(b, pa, pb, prm, sv, yb, static_cast<const float*>(h.dir.ptr),
@@ -456,10 +463,15 @@ ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const fl
       CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, h.cout), "hvp copy");
       if (jvp) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, h.cout), "jvp copy");
     }
-    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, st)) !=
+    cudaStream_t gs = conc ? h.cin : st;
+    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, gs)) !=
         CCM_OK)
       return s;
-    CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, st), "gradient copy");
+    CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, gs), "gradient copy");
+    if (conc) {
+      CCM_CUDA(cudaEventRecord(h.ev[4], h.cin), "event");
+      CCM_CUDA(cudaStreamWaitEvent(st, h.ev[4], 0), "wait");
+    }
   }
   // later work on `stream` waits for the copies of the side streams
   CCM_CUDA(cudaEventRecord(h.ev[0], h.cout), "event");
@@ -729,8 +741,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
     if ((st = upload(bt->d_pair_order, items_by_cost(pcost), "pair order")) != CCM_OK) return st;
   }
   bt->per_pair = bt->mx.s_pieces <= kHitS;
-  if (!bt->d_sched.ptr) {
-    std::vector<int32_t> zeros(2, 0);
+  if (!bt->d_sched.ptr) {   // forward, gradient pass, H u pass
+    std::vector<int32_t> zeros(3, 0);
     if ((st = upload(bt->d_sched, zeros, "work counters")) != CCM_OK) return st;
   }
   if ((int64_t)items.size() != bt->n_items || !bt->d_part.ptr) {
@@ -777,7 +789,9 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.saved = saved;
   L.pair_order = saved && b->per_pair ? static_cast<const int32_t*>(b->d_pair_order.ptr) : nullptr;
   L.counters = counters;
-  L.sched = static_cast<int*>(b->d_sched.ptr) + 1;
+  // the gradient and the H u pass count on separate words: with a saved record
+  // they may run concurrently on two streams
+  L.sched = static_cast<int*>(b->d_sched.ptr) + (dir ? 2 : 1);
   L.kp = kp;
   L.us = b->us;
   L.part = static_cast<float*>(b->d_part.ptr);

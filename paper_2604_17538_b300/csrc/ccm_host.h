@@ -47,7 +47,7 @@ struct Context {
 struct HostStep {
   DevBuf pa, pb, y, saved, ybar, grad, grad2, hvp, dir, jvp;
   cudaStream_t cin = nullptr, cout = nullptr;   // input and output copies
-  cudaEvent_t ev[4] = {};                       // start, inputs, forward, gradient
+  cudaEvent_t ev[5] = {};   // pose copy / end, inputs, forward, H u pass, gradient pass
   void release();
 };
 
@@ -70,7 +70,7 @@ struct Batch {
   DevBuf d_part;                 // [n_items, 24] per-item slots of the reverse pass
   DevBuf d_pair_order;           // pairs by decreasing cost (per-pair reverse pass)
   bool per_pair = false;         // every body has <= kHitS pieces
-  DevBuf d_sched;                // [2] work counters of the forward and reverse launches
+  DevBuf d_sched;                // [3] work counters: forward, gradient pass, H u pass
   BatchMaxima mx;
   ccm_tuning tuning{};
   UnitShape us{};
