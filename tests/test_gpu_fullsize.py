@@ -1,0 +1,137 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times, on sampled outputs the oracle recomputes pair by pair:
+
+* the 4096-environment step: 4096 pairs of two 8-piece bodies (seed 2), default
+  launch shape, the forward keeping its record, then the gradient pass and the
+  H u / J u pass running concurrently on two streams;
+* the uneven batch: 65,536 body pairs (seed 4), autotuned shape, forward and
+  gradient from the record.
+
+A seeded sample of pairs is taken out as a sub-scene (same geometry and
+poses) for the oracle; over the whole launch every output must be finite and
+every empty group exactly (d_max, 0, 0, 0)."""
+import numpy as np
+import pytest
+
+from gpu_util import COND_FACTOR, GRAD_RTOL, compare, fp32_sensitivity, weight_slack
+from paper_2604_17538_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+D_MAX = 0.01   # the default d_max of ccm_default_params
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_17538_b300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _rows(off, idx):
+    return np.concatenate([np.arange(off[i], off[i + 1]) for i in idx])
+
+
+def _check_whole(y):
+    assert np.all(np.isfinite(y))
+    empty = y[:, 1] == 0.0
+    assert np.all(y[empty, 0] == np.float32(D_MAX)) and np.all(y[empty, 2:] == 0.0)
+
+
+def _check_pairs(got, ref, tol, what):
+    got = np.asarray(got, np.float64)
+    assert np.all(np.isfinite(got)), what
+    err = np.abs(got - ref).max(1)
+    scale = np.abs(ref).max(1)
+    bad = err > tol * scale + 1e-6
+    assert not bad.any(), (what, int(bad.sum()), float((err / (scale + 1e-30)).max()))
+
+
+def test_hull_4096_step_sampled_against_oracle(oracle_lib, ctx):
+    import torch
+    from paper_2604_17538_b300 import api
+    sc = scenes.hull_env_scene(seed=2, n_envs=4096, workers=0)
+    batch, pa, pb = api.scene_to_device(sc, ctx)
+    n, G = batch.n_pairs, batch.n_groups
+    rng = np.random.default_rng(3)
+    ybar = rng.normal(size=(G, 8)).astype(np.float32)
+    u = rng.normal(size=(n, 12))
+    u = (u / np.linalg.norm(u, axis=1, keepdims=True)).astype(np.float32)
+    yb, ut = torch.from_numpy(ybar).cuda(), torch.from_numpy(u).cuda()
+    # the bench step: record, then both reverse passes concurrently
+    saved = batch.saved_buffer()
+    g = torch.empty((n, 12), device="cuda")
+    g2, h = torch.empty_like(g), torch.empty_like(g)
+    j = torch.empty((G, 8), device="cuda")
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    y = batch.contacts(pa, pb, saved=saved)
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        batch.backward(pa, pb, yb, saved=saved, out=(g, None, None))
+    batch.backward(pa, pb, yb, ut, want_jvp=True, saved=saved, out=(g2, h, j))
+    main.wait_stream(side)
+    torch.cuda.synchronize()
+    y, g, g2, h, j = (t.double().cpu().numpy() for t in (y, g, g2, h, j))
+    _check_whole(y)
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(h)) and np.all(np.isfinite(j))
+
+    off = sc.group_offsets()
+    idx = np.sort(np.random.default_rng(17).choice(n, 32, replace=False))
+    sub = sc.take(idx)
+    rows = _rows(off, idx)
+    compare(y[rows], oracle_lib.forward(sub), "4096-env y (sampled)", a_slack=weight_slack(sub))
+    yb_s, u_s = ybar[rows], u[idx]
+    go, ho, jo, _ = oracle_lib.hvp(sub, yb_s, u_s)
+    kg, kh = fp32_sensitivity(oracle_lib, sub, yb_s, u_s)
+    tol_g = np.maximum(GRAD_RTOL, COND_FACTOR * kg)
+    tol_h = np.maximum(GRAD_RTOL, COND_FACTOR * kh)
+    _check_pairs(g[idx], go, tol_g, "gradient")
+    _check_pairs(g2[idx], go, tol_g, "gradient (dual pass)")
+    _check_pairs(h[idx], ho, tol_h, "H u")
+    soff = sub.group_offsets()
+    js = j[rows]
+    for k in range(sub.n_pairs):
+        a, b = soff[k], soff[k + 1]
+        assert np.abs(js[a:b] - jo[a:b]).max() <= GRAD_RTOL * np.abs(jo[a:b]).max() + 1e-6, k
+    assert np.abs(go).max() > 0 and np.abs(ho).max() > 0
+    batch.close()
+
+
+def test_uneven_65536_autotuned_sampled_against_oracle(oracle_lib, ctx):
+    import torch
+    from paper_2604_17538_b300 import api, tune
+    sc = scenes.uneven_scene(seed=4, n_pairs=65536, workers=0)
+    batch, pa, pb = api.scene_to_device(sc, ctx)
+    n, G = batch.n_pairs, batch.n_groups
+    ybar = np.random.default_rng(3).normal(size=(G, 8)).astype(np.float32)
+    yb = torch.from_numpy(ybar).cuda()
+    tune.autotune(batch, pa, pb, yb)
+    saved = batch.saved_buffer()
+    y = batch.contacts(pa, pb, saved=saved)
+    g, _, _ = batch.backward(pa, pb, yb, saved=saved)
+    torch.cuda.synchronize()
+    y, g = y.double().cpu().numpy(), g.double().cpu().numpy()
+    _check_whole(y)
+    assert np.all(np.isfinite(g))
+
+    off = sc.group_offsets()
+    npb = np.diff(sc.geom.body_piece_off)
+    pp = npb[sc.pair_a] * npb[sc.pair_b]
+    rng = np.random.default_rng(19)
+    # a sample across the range of sizes the oracle recomputes in seconds:
+    # pairs of up to 256 piece pairs, and the largest pieces counts among them
+    light = np.nonzero(pp <= 256)[0]
+    idx = np.sort(np.concatenate([rng.choice(light, 20, replace=False),
+                                  light[np.argsort(pp[light])[-4:]]]))
+    idx = np.unique(idx)
+    sub = sc.take(idx)
+    rows = _rows(off, idx)
+    compare(y[rows], oracle_lib.forward(sub), "uneven y (sampled)", a_slack=weight_slack(sub))
+    yb_s = ybar[rows]
+    go, _ = oracle_lib.gradient(sub, yb_s)
+    u0 = np.zeros((sub.n_pairs, 12), np.float32)
+    kg, _ = fp32_sensitivity(oracle_lib, sub, yb_s, u0)
+    _check_pairs(g[idx], go, np.maximum(GRAD_RTOL, COND_FACTOR * kg), "uneven gradient")
+    batch.close()
