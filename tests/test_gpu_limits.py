@@ -78,6 +78,31 @@ def test_body_of_300_pieces_against_oracle(oracle_lib, ctx):
     sc = scenes.Scene(geom, np.zeros(3, np.int64), np.ones(3, np.int64),
                       np.stack(poses_a).astype(np.float32), np.stack(poses_b).astype(np.float32))
     _check(oracle_lib, ctx, sc, 5)
+    _host_step_equals_device_calls(ctx, sc)
+
+
+def _host_step_equals_device_calls(ctx, sc):
+    """ccm_contacts_step_host on a batch whose reverse passes cannot run per
+    pair (so they stay in order on one stream) returns the device calls'
+    results bitwise."""
+    import torch
+    from paper_2604_17538_b300 import api
+    batch, pa, pb = api.scene_to_device(sc, ctx)
+    rng = np.random.default_rng(21)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    yb_h = pin(rng.normal(size=(batch.n_groups, 8)))
+    u_h = pin(rng.normal(size=(batch.n_pairs, 12)))
+    saved = batch.saved_buffer()
+    y = batch.contacts(pa, pb, saved=saved)
+    g, _, _ = batch.backward(pa, pb, yb_h.cuda(), saved=saved)
+    _, h, j = batch.backward(pa, pb, yb_h.cuda(), u_h.cuda(), want_jvp=True, saved=saved)
+    torch.cuda.synchronize()
+    ref = [t.cpu().numpy() for t in (y, g, h, j)]
+    out = batch.step_host(pin(sc.pose_a), pin(sc.pose_b), yb_h, u_h, want_jvp=True)
+    torch.cuda.synchronize()
+    for name, a, b in zip("yghj", out, ref):
+        assert np.array_equal(a.numpy(), b), name
+    batch.close()
 
 
 def test_large_pieces_against_oracle(oracle_lib, ctx):
