@@ -50,7 +50,8 @@ class ccm_body_desc(C.Structure):
 class ccm_tuning(C.Structure):
     _fields_ = [("item_v", C.c_int32), ("item_e", C.c_int32), ("item_vb", C.c_int32),
                 ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("groups", C.c_int32),
-                ("stage_planes", C.c_int32), ("stage_verts", C.c_int32)]
+                ("stage_planes", C.c_int32), ("stage_verts", C.c_int32),
+                ("groups_b", C.c_int32)]
 
 
 class ccm_serve_config(C.Structure):

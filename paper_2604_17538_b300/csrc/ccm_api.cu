@@ -692,7 +692,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
       t.item_e > 16384 || t.item_vb > 8192 || t.item_eb > 16384 || t.fwd_warps < 1 ||
       t.fwd_warps > 4 || t.groups < 1 || t.groups > kGroupsPerChunk ||
       (t.stage_planes != 0 && (t.stage_planes < 16 || t.stage_planes > 4096)) ||
-      (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)))
+      (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)) ||
+      t.groups_b < 0 || t.groups_b > kGroupsPerChunk)
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -707,6 +708,9 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   us.item_vb = std::max(mx.vmax, t.item_vb);
   us.item_eb = std::max(mx.emax, t.item_eb);
   us.groups = std::min(t.groups, mx.pieces_any);
+  // the reverse pass's chunks: a handful of (marked) groups keeps a chunk's
+  // directions in one list, which its adjoint sweep then reuses
+  us.groups_b = std::min(us.groups, t.groups_b ? t.groups_b : 4);
   us.hit_words = std::min(kHitWords, (mx.s_pieces + 31) / 32);
   us.slice_bytes = unit_slice_bytes(us);
   us.warps = t.fwd_warps;

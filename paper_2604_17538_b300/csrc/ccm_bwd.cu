@@ -430,19 +430,19 @@ template <class T> __host__ __device__ constexpr int group_table_bytes() {
 
 template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShape& u) {
   int b = 0;
-  b += align16i(4 * u.groups);
+  b += align16i(4 * u.groups_b);
   b += align16i((int)sizeof(PoseT<T>) * 2);
   b += align16i((int)sizeof(V3T<T>));
   b += align16i((int)sizeof(T) * 18);
   b += align16i((int)sizeof(PoseT<T>) * 2);
   b += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
-  b += align16i(4 * u.hit_words * u.groups);
+  b += align16i(4 * u.hit_words * u.groups_b);
   b += 16 * u.plane_budget;
   b += align16i(8 * 2 * u.spiece_budget);
   b += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   b += align16i(4 * u.edge_budget);
-  b += 16 * u.groups * 2;
-  b += align16i(group_table_bytes<T>() * u.groups);
+  b += 16 * u.groups_b * 2;
+  b += align16i(group_table_bytes<T>() * u.groups_b);
   b += align16i(4 * kPending) * 2;
   b += align16i(4 * (kPending + 1)) * 2;
   b += align16i(4 * u.item_vb);
@@ -456,25 +456,25 @@ template <class T> __host__ __device__ inline int bwd_slice_bytes(const UnitShap
 
 template <class T> __device__ inline BwdSlice<T> bwd_slice(unsigned char* p, const UnitShape& u) {
   BwdSlice<T> s;
-  s.gside = reinterpret_cast<int*>(p);          p += align16i(4 * u.groups);
+  s.gside = reinterpret_cast<int*>(p);          p += align16i(4 * u.groups_b);
   s.spose = reinterpret_cast<PoseT<T>*>(p);     p += align16i((int)sizeof(PoseT<T>) * 2);
   s.tba = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>));
   s.pacc = reinterpret_cast<T*>(p);             p += align16i((int)sizeof(T) * 18);
   s.rel = reinterpret_cast<PoseT<T>*>(p);       p += align16i((int)sizeof(PoseT<T>) * 2);
   s.memo = reinterpret_cast<int*>(p);
   p += align16i(4 * (kMemoHead + (u.item_vb + 31) / 32 + (u.item_eb + 31) / 32));
-  s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * u.hit_words * u.groups);
+  s.hit = reinterpret_cast<uint32_t*>(p);       p += align16i(4 * u.hit_words * u.groups_b);
   s.hw = u.hit_words;
   s.planes = reinterpret_cast<float4*>(p);     p += 16 * u.plane_budget;
   s.sp = reinterpret_cast<int2*>(p);           p += align16i(8 * 2 * u.spiece_budget);
   s.xs = reinterpret_cast<V3T<T>*>(p);         p += align16i((int)sizeof(V3T<T>) * u.vert_budget);
   s.edges = reinterpret_cast<uint32_t*>(p);    p += align16i(4 * u.edge_budget);
-  s.fp = reinterpret_cast<int4*>(p);           p += 16 * u.groups;
-  s.fs = reinterpret_cast<float4*>(p);         p += 16 * u.groups;
+  s.fp = reinterpret_cast<int4*>(p);           p += 16 * u.groups_b;
+  s.fs = reinterpret_cast<float4*>(p);         p += 16 * u.groups_b;
   // a group's blend partial (sweep 1) and its adjoint coefficients (sweep 2)
   // share one slot: the coefficients are formed from the partial in registers
   s.acc = reinterpret_cast<PartT<T>*>(p);
-  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i(group_table_bytes<T>() * u.groups);
+  s.coef = reinterpret_cast<Coef<T>*>(p);      p += align16i(group_table_bytes<T>() * u.groups_b);
   s.dir = reinterpret_cast<int*>(p);           p += align16i(4 * kPending);
   s.dsub = reinterpret_cast<int*>(p);          p += align16i(4 * kPending);
   s.pv = reinterpret_cast<int*>(p);            p += align16i(4 * (kPending + 1));
@@ -1113,7 +1113,7 @@ bwd_unit_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 
     for (int fc0 = it.fc0; fc0 < it.fc1;) {
       int fc1 = fc0, V = 0, E = 0;
-      while (fc1 < it.fc1 && fc1 - fc0 < us.groups) {
+      while (fc1 < it.fc1 && fc1 - fc0 < us.groups_b) {
         const PieceRec p = g.pieces[F.p0 + fc1];
         if (V + p.nv > us.vert_budget || E + p.ne > us.edge_budget) break;
         V += p.nv;
@@ -1407,9 +1407,9 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
     const int ncand = bA.np + bB.np;   // group rows goff + c; c < npA: A's pieces (side 0)
     int cand = 0;
     for (;;) {
-      // the next chunk: up to us.groups marked groups within the budgets
+      // the next chunk: up to us.groups_b marked groups within the budgets
       int nfc = 0, V = 0, E = 0;
-      while (cand < ncand && nfc < us.groups) {
+      while (cand < ncand && nfc < us.groups_b) {
         const int c = cand + lane;
         bool live = false;
         int nv = 0, ne = 0;
@@ -1426,7 +1426,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
         while (m) {
           const int l = __ffs(m) - 1;
           const int nv_l = __shfl_sync(kFull, nv, l), ne_l = __shfl_sync(kFull, ne, l);
-          if (nfc == us.groups || V + nv_l > us.vert_budget || E + ne_l > us.edge_budget) {
+          if (nfc == us.groups_b || V + nv_l > us.vert_budget || E + ne_l > us.edge_budget) {
             next = cand + l;   // starts the next chunk
             break;
           }

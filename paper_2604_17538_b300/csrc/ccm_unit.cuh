@@ -32,6 +32,7 @@ struct UnitShape {
   int32_t groups;         // feature pieces (groups) per chunk, <= kGroupsPerChunk
   int32_t item_vb;        // item budgets of the reverse pass
   int32_t item_eb;
+  int32_t groups_b;       // groups per chunk of the reverse pass (<= groups)
   int32_t hit_words;      // hit words per group kept in shared memory:
                           // ceil(largest S body's pieces / 32) <= kHitWords
 };

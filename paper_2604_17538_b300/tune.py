@@ -7,7 +7,9 @@ ones stage the SDF body's planes fewer times) and then the staging budgets
 (planes and vertices held at once: smaller slices, more resident warps, more
 chunks), each timed on forward + reverse pass together since both passes use
 them; then the forward's and the reverse pass's list budgets, which trade lane
-utilisation (bigger lists of live piece pairs) against resident warps.
+utilisation (bigger lists of live piece pairs) against resident warps, and the
+reverse pass's chunk size (fewer pieces per chunk keep a chunk's directions in
+one list, which its adjoint sweep reuses).
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ import itertools
 FWD_CANDIDATES = [dict(item_v=v, item_e=e, fwd_warps=w)
                   for (v, e), w in itertools.product([(128, 256), (256, 512), (512, 1024)], [1, 2, 4])]
 BWD_CANDIDATES = [dict(item_vb=v, item_eb=e) for v, e in [(64, 128), (128, 256), (256, 512), (512, 1024)]]
+# feature pieces per chunk of the reverse pass (at most the work item's)
+CHUNK_CANDIDATES = [dict(groups_b=g) for g in (2, 4, 8, 16)]
 GROUP_CANDIDATES = [dict(groups=g) for g in (4, 8, 16, 32)]
 # staging budgets (planes of an SDF-body chunk, vertices of a feature chunk):
 # smaller slices keep more warps resident on bodies with many large pieces
@@ -48,7 +52,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
     calls.  The record does not depend on the shape, so one serves every
     reverse-pass candidate."""
     import torch
-    log = {"items": {}, "stage": {}, "forward": {}, "reverse": {}}
+    log = {"items": {}, "stage": {}, "forward": {}, "reverse": {}, "chunks": {}}
     if ybar is None:
         ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
     rec = batch.saved_buffer(pose_a.device) if saved else None
@@ -108,6 +112,18 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
         if bbest is None or t < bbest[0]:
             bbest = (t, cand)
     batch.set_tuning(**bbest[1])
+    cbest = None
+    for cand in CHUNK_CANDIDATES:
+        try:
+            batch.set_tuning(**cand)
+            t = _time(bwd)
+        except Exception as ex:
+            log["chunks"][str(cand)] = repr(ex)
+            continue
+        log["chunks"][str(cand)] = t
+        if cbest is None or t < cbest[0]:
+            cbest = (t, cand)
+    batch.set_tuning(**cbest[1])
     if verbose:
         for k, v in log.items():
             for c, t in sorted(v.items(), key=lambda x: (isinstance(x[1], str), x[1])):

@@ -82,6 +82,7 @@ def test_work_item_size_and_budgets_change_only_rounding(ctx, uneven):
     slack = weight_slack(uneven)
     for t in (dict(groups=1), dict(groups=3, item_v=64, item_e=128, item_vb=64, item_eb=128),
               dict(groups=16, stage_planes=64, stage_verts=32),
+              dict(groups=16, groups_b=1), dict(groups=8, groups_b=16),
               dict(groups=32, item_v=1024, item_e=2048, item_vb=512, item_eb=1024, fwd_warps=1),
               dict(groups=8, fwd_warps=4)):
         batch.set_tuning(**t)
@@ -110,7 +111,8 @@ def test_autotune_times_the_saved_record_path(ctx, uneven):
     g0 = batch.backward(pa, pb, ybar, saved=saved)[0].double().cpu().numpy()
     tuning, log = tune.autotune(batch, pa, pb, ybar)
     for kind, cands in (("items", tune.GROUP_CANDIDATES), ("stage", tune.STAGE_CANDIDATES),
-                        ("forward", tune.FWD_CANDIDATES), ("reverse", tune.BWD_CANDIDATES)):
+                        ("forward", tune.FWD_CANDIDATES), ("reverse", tune.BWD_CANDIDATES),
+                        ("chunks", tune.CHUNK_CANDIDATES)):
         assert len(log[kind]) == len(cands)
         assert any(isinstance(t, float) for t in log[kind].values()), kind
     assert dict(groups=tuning["groups"]) in tune.GROUP_CANDIDATES
