@@ -19,7 +19,7 @@ FWD_CANDIDATES = [dict(item_v=v, item_e=e, fwd_warps=w)
                   for (v, e), w in itertools.product([(128, 256), (256, 512), (512, 1024)], [1, 2, 4])]
 BWD_CANDIDATES = [dict(item_vb=v, item_eb=e) for v, e in [(64, 128), (128, 256), (256, 512), (512, 1024)]]
 # feature pieces per chunk of the reverse pass (at most the work item's)
-CHUNK_CANDIDATES = [dict(groups_b=g) for g in (2, 4, 8, 16)]
+CHUNK_CANDIDATES = [dict(groups_b=g) for g in (2, 3, 4, 5, 8, 16)]
 GROUP_CANDIDATES = [dict(groups=g) for g in (4, 8, 16, 32)]
 # staging budgets (planes of an SDF-body chunk, vertices of a feature chunk):
 # smaller slices keep more warps resident on bodies with many large pieces
