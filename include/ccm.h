@@ -159,7 +159,7 @@ typedef struct {
                                  the largest piece's), 0 or 16..4096 */
   int32_t stage_verts;        /* most feature-piece vertices staged at once, edges
                                  3x that (0: 512; at least the largest piece's), 0 or 16..4096 */
-  int32_t groups_b;           /* reverse pass: feature pieces per chunk (0: 3; at most
+  int32_t groups_b;           /* reverse pass: feature pieces per chunk (0: 4; at most
                                  groups), 0..32 */
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);

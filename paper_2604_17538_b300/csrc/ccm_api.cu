@@ -710,7 +710,7 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   us.groups = std::min(t.groups, mx.pieces_any);
   // the reverse pass's chunks: a handful of (marked) groups keeps a chunk's
   // directions in one list, which its adjoint sweep then reuses
-  us.groups_b = std::min(us.groups, t.groups_b ? t.groups_b : 3);
+  us.groups_b = std::min(us.groups, t.groups_b ? t.groups_b : 4);
   us.hit_words = std::min(kHitWords, (mx.s_pieces + 31) / 32);
   us.slice_bytes = unit_slice_bytes(us);
   us.warps = t.fwd_warps;
