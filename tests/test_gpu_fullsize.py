@@ -3,7 +3,8 @@ times, on sampled outputs the oracle recomputes pair by pair:
 
 * the 4096-environment step: 4096 pairs of two 8-piece bodies (seed 2), default
   launch shape, the forward keeping its record, then the gradient pass and the
-  H u / J u pass running concurrently on two streams;
+  H u / J u pass running concurrently on two streams -- its derivatives also
+  against central differences (h = 1e-5, FP64) on 256 sampled environments;
 * the uneven batch: 65,536 body pairs (seed 4), autotuned shape, forward and
   gradient from the record.
 
@@ -49,7 +50,9 @@ def _check_pairs(got, ref, tol, what):
     assert not bad.any(), (what, int(bad.sum()), float((err / (scale + 1e-30)).max()))
 
 
-def test_hull_4096_step_sampled_against_oracle(oracle_lib, ctx):
+@pytest.fixture(scope="module")
+def hull_step(ctx):
+    """The 4096-environment scene and the bench step's outputs on it."""
     import torch
     from paper_2604_17538_b300 import api
     sc = scenes.hull_env_scene(seed=2, n_envs=4096, workers=0)
@@ -73,7 +76,17 @@ def test_hull_4096_step_sampled_against_oracle(oracle_lib, ctx):
     batch.backward(pa, pb, yb, ut, want_jvp=True, saved=saved, out=(g2, h, j))
     main.wait_stream(side)
     torch.cuda.synchronize()
-    y, g, g2, h, j = (t.double().cpu().numpy() for t in (y, g, g2, h, j))
+    out = dict(sc=sc, ybar=ybar, u=u)
+    out.update({k: t.double().cpu().numpy() for k, t in (("y", y), ("g", g), ("g2", g2),
+                                                          ("h", h), ("j", j))})
+    batch.close()
+    return out
+
+
+def test_hull_4096_step_sampled_against_oracle(oracle_lib, hull_step):
+    sc, ybar, u = hull_step["sc"], hull_step["ybar"], hull_step["u"]
+    y, g, g2, h, j = (hull_step[k] for k in ("y", "g", "g2", "h", "j"))
+    n = sc.n_pairs
     _check_whole(y)
     assert np.all(np.isfinite(g)) and np.all(np.isfinite(h)) and np.all(np.isfinite(j))
 
@@ -96,7 +109,71 @@ def test_hull_4096_step_sampled_against_oracle(oracle_lib, ctx):
         a, b = soff[k], soff[k + 1]
         assert np.abs(js[a:b] - jo[a:b]).max() <= GRAD_RTOL * np.abs(jo[a:b]).max() + 1e-6, k
     assert np.abs(go).max() > 0 and np.abs(ho).max() > 0
-    batch.close()
+
+
+def _exp_so3(w):
+    """Rotation matrices Exp([w]x) of rotation vectors w [n,3] (Rodrigues)."""
+    th = np.linalg.norm(w, axis=1)[:, None, None]
+    K = np.zeros((len(w), 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -w[:, 2], w[:, 1], -w[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = w[:, 2], -w[:, 1], w[:, 0]
+    s = np.where(th > 0, np.sin(th) / np.where(th > 0, th, 1), 1.0)
+    c = np.where(th > 0, (1 - np.cos(th)) / np.where(th > 0, th * th, 1), 0.5)
+    return np.eye(3)[None] + s * K + c * (K @ K)
+
+
+def _moved(sc, xi):
+    """The scene with every pair moved to Exp(xi) T in the twist chart
+    (R <- Exp([w]x) R, t <- t + v per body; xi = (w_A, v_A, w_B, v_B)), FP64 poses."""
+    out = sc.take(np.arange(sc.n_pairs))
+    for P, col in ((sc.pose_a, 0), (sc.pose_b, 6)):
+        R, t = scenes.unpack_pose(P.astype(np.float64))
+        R2 = _exp_so3(xi[:, col:col + 3]) @ R
+        t2 = t + xi[:, col + 3:col + 6]
+        Q = np.concatenate([R2.reshape(-1, 9), t2], axis=1)
+        if col == 0:
+            out.pose_a = Q
+        else:
+            out.pose_b = Q
+    return out
+
+
+def test_hull_4096_derivatives_against_central_differences(oracle_lib, hull_step):
+    """Gradient and H u of the bench step on 256 sampled environments against
+    central differences in FP64: of L = <ybar, y> along each twist coordinate
+    for the gradient, and of the fixed-chart gradient along +-h u for H u.
+
+    The step is h = 1e-5.  At h = 1e-4 the truncation error is not small next
+    to every pair's gradient: with softness 5e-3 a grazing pair's loss bends
+    on a scale below 1e-4, and there the difference misses even the FP64
+    oracle's analytic derivative by more than the derivative itself.  At
+    1e-5 it stays within 1e-4 (gradient) and 3e-4 (H u) of it on this sample,
+    so the bar adds a 1e-3 allowance to the oracle-parity bar."""
+    sc, ybar, u = hull_step["sc"], hull_step["ybar"], hull_step["u"]
+    g, h = hull_step["g"], hull_step["h"]
+    hstep = 1e-5
+    idx = np.sort(np.random.default_rng(23).choice(sc.n_pairs, 256, replace=False))
+    sub = sc.take(idx)
+    rows = _rows(sc.group_offsets(), idx)
+    yb_s, u_s = ybar[rows].astype(np.float64), u[idx].astype(np.float64)
+    soff = sub.group_offsets()
+
+    def loss(s):
+        y = oracle_lib.forward(s)
+        return np.array([np.sum(y[soff[i]:soff[i + 1]] * yb_s[soff[i]:soff[i + 1]])
+                         for i in range(s.n_pairs)])
+    fd_g = np.zeros((sub.n_pairs, 12))
+    for k in range(12):
+        xi = np.zeros((sub.n_pairs, 12))
+        xi[:, k] = hstep
+        fd_g[:, k] = (loss(_moved(sub, xi)) - loss(_moved(sub, -xi))) / (2 * hstep)
+    gp, _ = oracle_lib.gradient(sub, yb_s, xi=hstep * u_s)
+    gm, _ = oracle_lib.gradient(sub, yb_s, xi=-hstep * u_s)
+    fd_h = (gp - gm) / (2 * hstep)
+    kg, kh = fp32_sensitivity(oracle_lib, sub, ybar[rows], u[idx])
+    _check_pairs(g[idx], fd_g, np.maximum(GRAD_RTOL, COND_FACTOR * kg) + 1e-3, "gradient vs FD")
+    _check_pairs(h[idx], fd_h, np.maximum(GRAD_RTOL, COND_FACTOR * kh) + 1e-3, "H u vs FD")
+    assert np.abs(fd_g).max() > 0 and np.abs(fd_h).max() > 0
 
 
 def test_uneven_65536_autotuned_sampled_against_oracle(oracle_lib, ctx):
