@@ -1,6 +1,7 @@
 """Uneven batches (pieces per body log-uniform in [1, 64], hull points
 log-uniform in [8, 512]): forward, gradient and H u parity with the oracle,
-and bit-identical results for a pair alone and inside the batch."""
+and bit-identical results for a pair alone and inside the batch, and for a
+CUDA-graph replay and the eager calls."""
 import numpy as np
 import pytest
 
@@ -122,4 +123,65 @@ def test_autotune_times_the_saved_record_path(ctx, uneven):
     g = batch.backward(pa, pb, ybar, saved=saved)[0].double().cpu().numpy()
     err = np.abs(g - g0).max(1)
     assert np.all(err <= GRAD_RTOL * np.abs(g0).max(1) + 1e-6), float(err.max())
+    batch.close()
+
+
+def test_graph_replay_equals_eager_calls(ctx, uneven):
+    """The forward with its record, the gradient pass and the H u / J u pass
+    captured once in a CUDA graph: every replay returns the eager calls'
+    results bitwise (the work counters restart each replay), and a replay
+    after the poses change in place returns the eager results at the new
+    poses."""
+    import torch
+    from paper_2604_17538_b300 import api
+    batch, pa, pb = api.scene_to_device(uneven, ctx)
+    n, G = batch.n_pairs, batch.n_groups
+    rng = np.random.default_rng(31)
+    yb = torch.from_numpy(rng.normal(size=(G, 8)).astype(np.float32)).cuda()
+    u = torch.from_numpy(rng.normal(size=(n, 12)).astype(np.float32)).cuda()
+    saved = batch.saved_buffer()
+    y = torch.empty((G, 8), device="cuda")
+    g, g2, h = (torch.empty((n, 12), device="cuda") for _ in range(3))
+    j = torch.empty((G, 8), device="cuda")
+
+    def calls():
+        batch.contacts(pa, pb, out=y, saved=saved)
+        batch.backward(pa, pb, yb, out=(g, None, None), saved=saved)
+        batch.backward(pa, pb, yb, u, want_jvp=True, out=(g2, h, j), saved=saved)
+
+    def eager():
+        calls()
+        torch.cuda.synchronize()
+        return [t.cpu().numpy().copy() for t in (y, g, g2, h, j)]
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):              # first calls (allocations) outside the capture
+        for _ in range(2):
+            calls()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ref0 = eager()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        calls()
+    for _ in range(3):
+        for t in (y, g, g2, h, j):
+            t.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        for name, a, b in zip(("y", "grad", "grad (dual)", "H u", "J u"), (y, g, g2, h, j), ref0):
+            assert np.array_equal(a.cpu().numpy(), b), name
+
+    pa_new = pa.clone()
+    pa_new[:, 9:] += 2e-3                      # move every body A: other contacts
+    pa.copy_(pa_new)
+    ref1 = eager()
+    for t in (y, g, g2, h, j):
+        t.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    for name, a, b in zip(("y", "grad", "grad (dual)", "H u", "J u"), (y, g, g2, h, j), ref1):
+        assert np.array_equal(a.cpu().numpy(), b), name
+    assert not np.array_equal(ref0[0], ref1[0]) and not np.array_equal(ref0[3], ref1[3])
     batch.close()
