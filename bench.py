@@ -79,6 +79,57 @@ def derived_peaks(n_sm=148, clock_ghz=2.032, sfu_per_clk=32):
             "ex2_tops": n_sm * sfu_per_clk * clock_ghz / 1e3}
 
 
+def alu_roofline(local, per, model, workload_key):
+    """Roofline object of the dominant contact kernel: ``per`` = average
+    launch duration (s) of each pass from CUDA events, ``model`` = the
+    algorithmic (FLOP, ex2) of one launch of each pass (work_model).  The
+    FP32 and ex2 peaks are derived from the SM count and the maximum clock,
+    the ex2 rate per clock from the library's probe.  DRAM traffic per launch
+    comes from profiles/traffic.json when a record there matches the kernel,
+    the workload (``workload_key``) and the current kernel sources."""
+    import ctypes as C
+    import torch
+    from paper_2604_17538_b300 import abi
+    probe = {}
+    try:
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        abi.check(abi.lib().ccm_peak_probe(local, C.byref(a), C.byref(b), C.byref(c)))
+        probe = {"ffma_tflops": a.value, "ffma2_tflops": b.value, "ex2_tops": c.value}
+    except Exception as ex:  # measurement aid only
+        probe = {"error": str(ex)}
+    props = torch.cuda.get_device_properties(local)
+    sfu_per_clk = 32
+    if "ex2_tops" in probe:
+        # per-SM per-clock ex2 rate implied by the probe, rounded to the unit width
+        r = probe["ex2_tops"] * 1e12 / (props.multi_processor_count * 2.032e9)
+        sfu_per_clk = max(16, int(round(r / 16.0)) * 16)
+    peaks = derived_peaks(props.multi_processor_count, 2.032, sfu_per_clk)
+    dom = max(per, key=per.get)
+    flop, ex2 = model[dom]
+    fp32_ach = flop / per[dom] / 1e12
+    ex2_ach = ex2 / per[dom] / 1e12
+    fr_fp32 = fp32_ach / peaks["fp32_tflops"]
+    fr_ex2 = ex2_ach / peaks["ex2_tops"]
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        # counters only count while the kernel sources are the ones captured
+        for tr in json.load(open(tpath)):
+            if (tr.get("kernel") == dom
+                    and all(tr.get(k) == v for k, v in workload_key.items())
+                    and tr.get("source_sha256") == kernel_source_hash()):
+                traffic = tr.get("bytes_per_launch")
+    return {"bound": "alu", "kernel": dom, "pipe": "fp32" if fr_fp32 >= fr_ex2 else "sfu_ex2",
+            "achieved": fp32_ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": max(fr_fp32, fr_ex2), "frac_fp32": fr_fp32, "frac_ex2": fr_ex2,
+            "ex2_achieved_tops": ex2_ach, "ex2_peak_tops": peaks["ex2_tops"],
+            "ms_per_launch": 1e3 * per[dom],
+            "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz; ex2: SM x "
+                           f"{sfu_per_clk}/clk x 2.032 GHz (per-clock rate from the probe)",
+            "probe": probe, "traffic": traffic, "flop_per_launch": flop,
+            "ex2_per_launch": ex2}
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -278,44 +329,8 @@ def run_ours(args, rank, world):
 
     out = None
     if rank == 0:
-        probe = {}
-        try:
-            import ctypes as C
-            a, b, c = C.c_double(), C.c_double(), C.c_double()
-            abi.check(abi.lib().ccm_peak_probe(local, C.byref(a), C.byref(b), C.byref(c)))
-            probe = {"ffma_tflops": a.value, "ffma2_tflops": b.value, "ex2_tops": c.value}
-        except Exception as ex:  # measurement aid only
-            probe = {"error": str(ex)}
-        props = torch.cuda.get_device_properties(local)
-        sfu_per_clk = 32
-        if "ex2_tops" in probe:
-            # per-SM per-clock ex2 rate implied by the probe, rounded to the unit width
-            per = probe["ex2_tops"] * 1e12 / (props.multi_processor_count * 2.032e9)
-            sfu_per_clk = max(16, int(round(per / 16.0)) * 16)
-        peaks = derived_peaks(props.multi_processor_count, 2.032, sfu_per_clk)
         per = {"forward": t_fwd / K, "vjp": t_vjp / K, "hvp": t_hvp / K}
-        dom = max(per, key=per.get)
-        flop, ex2 = model[dom]
-        fp32_ach = flop / per[dom] / 1e12
-        ex2_ach = ex2 / per[dom] / 1e12
-        fr_fp32 = fp32_ach / peaks["fp32_tflops"]
-        fr_ex2 = ex2_ach / peaks["ex2_tops"]
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tpath):
-            tr = json.load(open(tpath))
-            # counters only count while the kernel sources are the ones captured
-            if (tr.get("kernel") == dom and tr.get("envs") == args.envs
-                    and tr.get("source_sha256") == kernel_source_hash()):
-                traffic = tr.get("bytes_per_launch")
-        roof = {"bound": "alu", "kernel": dom, "pipe": "fp32" if fr_fp32 >= fr_ex2 else "sfu_ex2",
-                "achieved": fp32_ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
-                "frac": max(fr_fp32, fr_ex2), "frac_fp32": fr_fp32, "frac_ex2": fr_ex2,
-                "ex2_achieved_tops": ex2_ach, "ex2_peak_tops": peaks["ex2_tops"],
-                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz; ex2: SM x "
-                               f"{sfu_per_clk}/clk x 2.032 GHz (per-clock rate from the probe)",
-                "probe": probe, "traffic": traffic, "flop_per_launch": flop,
-                "ex2_per_launch": ex2}
+        roof = alu_roofline(local, per, model, {"envs": args.envs})
         out = {
             "metric": METRIC, "value": total_pp * K / t_step, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_step / K,
@@ -412,8 +427,8 @@ def run_reference(args, rank, world):
 
 def run_uneven(args, rank, world):
     """Uneven batch: 65,536 body pairs, pieces per body log-uniform in [1, 64],
-    hull points log-uniform in [8, 512]; autotuned shape; forward + gradient
-    captured once in a CUDA graph and replayed."""
+    hull points log-uniform in [8, 512]; autotuned shape (or the one --tuning
+    gives); forward + gradient captured once in a CUDA graph and replayed."""
     from paper_2604_17538_b300 import scenes
     t0 = time.perf_counter()
     from paper_2604_17538_b300 import shard
@@ -429,7 +444,12 @@ def run_uneven(args, rank, world):
     n, G = batch.n_pairs, batch.n_groups
     rng = np.random.default_rng(3 + rank)
     ybar = torch.from_numpy(rng.normal(size=(G, 8)).astype(np.float32)).cuda()
-    tuning, _ = tune.autotune(batch, pa, pb, ybar)
+    if args.tuning:
+        # a fixed launch shape (for profiling without the autotuner's launches)
+        tuning = {k: int(v) for k, v in (x.split("=") for x in args.tuning.split(","))}
+        batch.set_tuning(**tuning)
+    else:
+        tuning, _ = tune.autotune(batch, pa, pb, ybar)
     y = torch.empty((G, 8), device="cuda")
     grad = torch.empty((n, 12), device="cuda")
     saved = batch.saved_buffer()
@@ -467,9 +487,38 @@ def run_uneven(args, rank, world):
         b.synchronize()
         t += a.elapsed_time(b) / 1e3
     clocks = sampler.stop()
+
+    # per-kernel times for the roofline: the same two calls eagerly, with an
+    # event between them, L2 flushed before each step (a second loop, not
+    # part of the headline value)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(cur)
+        batch.contacts(pa, pb, out=y, saved=saved)
+        ev[k][1].record(cur)
+        batch.backward(pa, pb, ybar, out=(grad, None, None), saved=saved)
+        ev[k][2].record(cur)
+    torch.cuda.synchronize()
+    t_fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    t_vjp = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    # exact work counters of both passes (after the timed loops)
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
+    batch.contacts(pa, pb, counters=cnt)
+    cnt_v = torch.zeros(8, dtype=torch.int64, device="cuda")
+    batch.backward(pa, pb, ybar, saved=saved, counters=cnt_v)
+    counters = dict(zip(abi.COUNTER_NAMES, cnt.cpu().tolist()))
+    counters_vjp = dict(zip(abi.BWD_COUNTER_NAMES, cnt_v.cpu().tolist()))
+    model = work_model(counters, counters_vjp, counters_vjp)
+    t_fwd, t_vjp = shard.reduce_max([t_fwd, t_vjp], "cuda")
     pp_all, t, _ = shard.job_rate(sc.piece_pairs(), t, "cuda")
     if rank != 0:
         return None, sc
+    K = args.steps
+    roof = alu_roofline(local, {"forward": t_fwd / K, "vjp": t_vjp / K},
+                        {"forward": model["forward"], "vjp": model["vjp"]},
+                        {"pairs": args.pairs,   # DRAM bytes depend on the staging shape
+                         "tuning": ",".join(f"{k}={v}" for k, v in tuning.items())})
     npb = np.diff(sc.geom.body_piece_off)
     return {
         "metric": METRIC, "value": pp_all * args.steps / t, "unit": UNIT, "n_gpus": world,
@@ -482,7 +531,14 @@ def run_uneven(args, rank, world):
                    "pieces_per_body_mean": float(npb[sc.pair_a].mean()),
                    "l2": "flushed between timed steps (512 MiB write, untimed)",
                    "tuning": tuning, "generation_s": t_gen},
-        "gpu_launches": 3 * args.steps, "clocks": clocks,
+        "breakdown": {"ms_forward": 1e3 * t_fwd / K, "ms_vjp": 1e3 * t_vjp / K,
+                      "note": "eager calls timed in a second loop; the headline replays "
+                              "both in one CUDA graph"},
+        # per step: the forward keeping its record and the per-pair gradient
+        # pass from it (bodies of more than 256 pieces would add the
+        # per-work-item reduction kernel)
+        "gpu_launches": (2 if npb.max() <= 256 else 3) * args.steps, "roofline": roof,
+        "work_counters": {"forward": counters, "vjp": counters_vjp}, "clocks": clocks,
     }, sc
 
 
@@ -670,6 +726,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="hull", choices=["hull", "uneven", "serve"])
     ap.add_argument("--pairs", type=int, default=65536)
+    ap.add_argument("--tuning", default="",
+                    help="uneven workload: a fixed launch shape (key=value,... of "
+                         "ccm_tuning fields) instead of autotuning it")
     ap.add_argument("--serve-pairs", type=int, default=8192)
     ap.add_argument("--serve-rates", default="auto",
                     help="offered rates (req/s, comma-separated) or 'auto': "
