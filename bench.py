@@ -446,8 +446,8 @@ def run_uneven(args, rank, world):
     ybar = torch.from_numpy(rng.normal(size=(G, 8)).astype(np.float32)).cuda()
     if args.tuning:
         # a fixed launch shape (for profiling without the autotuner's launches)
-        tuning = {k: int(v) for k, v in (x.split("=") for x in args.tuning.split(","))}
-        batch.set_tuning(**tuning)
+        batch.set_tuning(**{k: int(v) for k, v in (x.split("=") for x in args.tuning.split(","))})
+        tuning = batch.get_tuning()
     else:
         tuning, _ = tune.autotune(batch, pa, pb, ybar)
     y = torch.empty((G, 8), device="cuda")

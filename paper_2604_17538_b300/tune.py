@@ -6,10 +6,12 @@ pieces per warp task: small items balance uneven bodies over the warps, large
 ones stage the SDF body's planes fewer times) and then the staging budgets
 (planes and vertices held at once: smaller slices, more resident warps, more
 chunks), each timed on forward + reverse pass together since both passes use
-them; then the forward's and the reverse pass's list budgets, which trade lane
-utilisation (bigger lists of live piece pairs) against resident warps, and the
-reverse pass's chunk size (fewer pieces per chunk keep a chunk's directions in
-one list, which its adjoint sweep reuses).
+them; then the forward's list budgets and warps per block, which trade lane
+utilisation (bigger lists of live piece pairs) against resident warps; then the
+two fastest staging budgets crossed with the two fastest forward shapes, timed
+together (both set the resident warps); then the reverse pass's list budgets
+and its chunk size (fewer pieces per chunk keep a chunk's directions in one
+list, which its adjoint sweep reuses).
 """
 from __future__ import annotations
 
@@ -52,7 +54,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
     calls.  The record does not depend on the shape, so one serves every
     reverse-pass candidate."""
     import torch
-    log = {"items": {}, "stage": {}, "forward": {}, "reverse": {}, "chunks": {}}
+    log = {"items": {}, "stage": {}, "forward": {}, "joint": {}, "reverse": {}, "chunks": {}}
     if ybar is None:
         ybar = torch.ones((batch.n_groups, 8), device=pose_a.device)
     rec = batch.saved_buffer(pose_a.device) if saved else None
@@ -74,6 +76,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
         if gbest is None or t < gbest[0]:
             gbest = (t, cand)
     batch.set_tuning(**gbest[1])
+    stage_timed, fwd_timed = [], []
     sbest = None
     for cand in STAGE_CANDIDATES:
         try:
@@ -83,6 +86,7 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
             log["stage"][str(cand)] = repr(ex)
             continue
         log["stage"][str(cand)] = t
+        stage_timed.append((t, cand))
         if sbest is None or t < sbest[0]:
             sbest = (t, cand)
     batch.set_tuning(**sbest[1])
@@ -95,9 +99,28 @@ def autotune(batch, pose_a, pose_b, ybar=None, direction=None, params=None, verb
             log["forward"][str(cand)] = repr(ex)
             continue
         log["forward"][str(cand)] = t
+        fwd_timed.append((t, cand))
         if best is None or t < best[0]:
             best = (t, cand)
     batch.set_tuning(**best[1])
+    # the staging budgets and the forward's shape both set how many warps stay
+    # resident, so the greedy picks are checked jointly: the two fastest of
+    # each, crossed, timed on forward + reverse pass with more repetitions
+    def top2(timed):
+        return [c for _, c in sorted(timed, key=lambda x: x[0])[:2]]
+    jbest = None
+    for sc, fc in itertools.product(top2(stage_timed), top2(fwd_timed)):
+        try:
+            batch.set_tuning(**sc, **fc)
+            t = _time(lambda: (fwd(), bwd()), reps=10)
+        except Exception as ex:
+            log["joint"][str((sc, fc))] = repr(ex)
+            continue
+        log["joint"][str((sc, fc))] = t
+        if jbest is None or t < jbest[0]:
+            jbest = (t, {**sc, **fc})
+    if jbest is not None:
+        batch.set_tuning(**jbest[1])
     if rec is not None:
         fwd()                     # the record of these poses for the reverse candidates
     bbest = None

@@ -116,6 +116,8 @@ def test_autotune_times_the_saved_record_path(ctx, uneven):
                         ("chunks", tune.CHUNK_CANDIDATES)):
         assert len(log[kind]) == len(cands)
         assert any(isinstance(t, float) for t in log[kind].values()), kind
+    assert 1 <= len(log["joint"]) <= 4      # two staging budgets x two forward shapes
+    assert any(isinstance(t, float) for t in log["joint"].values())
     assert dict(groups=tuning["groups"]) in tune.GROUP_CANDIDATES
     assert dict(item_vb=tuning["item_vb"], item_eb=tuning["item_eb"]) in tune.BWD_CANDIDATES
     y = batch.contacts(pa, pb, saved=saved).double().cpu().numpy()
