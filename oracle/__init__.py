@@ -12,11 +12,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                           inside-edge midpoint, one-step convergence on a face.
   * ``transition``     -- knot values and C^2 continuity.
   * ``forward``        -- cube-on-cube closed form and hard limits, rigid-motion
-                          invariance, body-swap symmetry, separation.
+                          invariance, body-swap symmetry, separation; on random
+                          hulls in the hard limit, the deepest brute-force
+                          contact (vertex plane maxima, edge chord midpoints).
   * ``gradient``/``hvp`` -- central finite differences in FP64, rigid-motion
                           null directions, Hessian symmetry.
-  * random-hull blended values beyond those invariants: parity unpinned
-    (the paper prints no worked example).
+  * random-hull blended values at the default softness beyond those
+    invariants and limits: parity unpinned (the paper prints no worked example).
 """
 from __future__ import annotations
 

@@ -6,7 +6,7 @@ import os
 import numpy as np
 import pytest
 
-from geom_util import rot
+from geom_util import cyrus_beck, rot
 from paper_2604_17538_b300 import scenes
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -183,3 +183,64 @@ def test_single_feature_group_reduces_to_its_contact(oracle_lib):
     assert np.abs(g[2:5] - xw).max() < 1e-6
     assert np.abs(g[5:8] - R[0] @ [0, 0, 1]).max() < 1e-6
     assert abs(r[0, 1] - (-0.004)) < 1e-6
+
+
+def _hard_limit_contacts(sc, i):
+    """Per group of pair i, the (phi, world point) of every contact in the
+    hard limit, by brute force: a vertex's phi is its largest plane value in
+    each SDF piece; an edge's contact is the midpoint of its Cyrus-Beck chord
+    through the SDF piece (Sec. 4.2 traces tend to the chord's ends), with
+    that point's largest plane value.  Groups: first A's pieces against B,
+    then B's against A."""
+    g = sc.geom
+    RA, tA = scenes.unpack_pose(sc.pose_a[i:i + 1])
+    RB, tB = scenes.unpack_pose(sc.pose_b[i:i + 1])
+    sides = ((sc.pair_a[i], RA[0], tA[0], sc.pair_b[i], RB[0], tB[0]),
+             (sc.pair_b[i], RB[0], tB[0], sc.pair_a[i], RA[0], tA[0]))
+    groups = []
+    for bF, RF, tF, bS, RS, tS in sides:
+        for fp in range(g.body_piece_off[bF], g.body_piece_off[bF + 1]):
+            V = g.verts[g.piece_v_off[fp]:g.piece_v_off[fp + 1]].astype(np.float64)
+            E = g.edges[g.piece_e_off[fp]:g.piece_e_off[fp + 1]]
+            X = (V @ RF.T + tF - tS) @ RS            # feature vertices in S's frame
+            rows = []
+            for sp in range(g.body_piece_off[bS], g.body_piece_off[bS + 1]):
+                P = g.planes[g.piece_f_off[sp]:g.piece_f_off[sp + 1]].astype(np.float64)
+                for x in X:
+                    rows.append(((P[:, :3] @ x + P[:, 3]).max(), x))
+                for i0, i1 in E:
+                    iv = cyrus_beck(X[i0], X[i1], P)
+                    if iv is not None:
+                        m = X[i0] + 0.5 * (iv[0] + iv[1]) * (X[i1] - X[i0])
+                        rows.append(((P[:, :3] @ m + P[:, 3]).max(), m))
+            groups.append([(phi, RS @ x + tS) for phi, x in rows])
+    return groups
+
+
+def test_hard_limit_depth_is_the_deepest_brute_force_contact(oracle_lib):
+    """Random hulls with every softness -> 0 and a long trace: a group whose
+    deepest contact lies clearly inside (phi < -1e-3, so its gate is 1)
+    returns that contact's depth, and its point when the minimum is unique."""
+    sc = scenes.hull_env_scene(seed=5, n_envs=16, workers=1)
+    prm = oracle_lib.params(tau_sdf=1e-8, tau_trace=1e-8, tau_clip=1e-8, tau_blend=1e-8,
+                            trace_iters=400)
+    y = oracle_lib.forward(sc, prm)
+    off = sc.group_offsets()
+    checked = points = 0
+    for i in range(sc.n_pairs):
+        for k, rows in enumerate(_hard_limit_contacts(sc, i)):
+            if not rows:
+                continue
+            phis = np.array([r[0] for r in rows])
+            j = int(np.argmin(phis))
+            if phis[j] >= -1e-3:
+                continue
+            yy = y[off[i] + k]
+            assert abs(yy[0] - phis[j]) < 1e-5, (i, k, yy[0], phis[j])
+            assert abs(yy[1] - 1.0) < 1e-6
+            checked += 1
+            rest = np.delete(phis, j)
+            if len(rest) == 0 or rest.min() - phis[j] > 1e-4:
+                assert np.abs(yy[2:5] - rows[j][1]).max() < 1e-5, (i, k)
+                points += 1
+    assert checked >= 10 and points >= 5, (checked, points)
