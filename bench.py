@@ -365,15 +365,15 @@ def run_ours(args, rank, world):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(sc, target_s=12.0):
-    """Times the oracle (forward, gradient, H u in one nested-dual pass) on a
-    bounded seeded sample of the environments; returns (qps, cores, sample)."""
+def oracle_sample_rate(sc, target_s=12.0, kind="hvp", what="environments"):
+    """Times the oracle on a bounded seeded sample of the scene's pairs:
+    kind "hvp" = forward, gradient and H u in one nested-dual pass, "grad" =
+    the forward and the gradient; returns (qps, cores, sample, seconds)."""
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(7)
     order = rng.permutation(sc.n_pairs)
-    G_all = int(sc.group_offsets()[-1])
 
     def run(k):
         sub = sc.take(order[:k])
@@ -381,7 +381,11 @@ def oracle_sample_rate(sc, target_s=12.0):
         yb = np.random.default_rng(3).normal(size=(G, 8))
         u = np.random.default_rng(4).normal(size=(k, 12))
         t0 = time.perf_counter()
-        oracle.hvp(sub, yb, u, threads=cores)
+        if kind == "hvp":
+            oracle.hvp(sub, yb, u, threads=cores)
+        else:
+            oracle.forward(sub, threads=cores)
+            oracle.gradient(sub, yb, threads=cores)
         return time.perf_counter() - t0, sub.piece_pairs()
 
     k = min(16, sc.n_pairs)
@@ -389,7 +393,7 @@ def oracle_sample_rate(sc, target_s=12.0):
     while dt < target_s / 4 and k < sc.n_pairs:
         k = min(sc.n_pairs, int(k * max(2.0, target_s / max(dt, 1e-3) / 2)))
         dt, pp = run(k)
-    return pp / dt, cores, f"{k} of {sc.n_pairs} environments ({pp} piece pairs), seeded", dt
+    return pp / dt, cores, f"{k} of {sc.n_pairs} {what} ({pp} piece pairs), seeded", dt
 
 
 def run_reference(args, rank, world):
@@ -525,9 +529,11 @@ def run_uneven(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded convex-hull scenes)",
-        "config": {"workload": f"uneven batch: {args.pairs} body pairs, pieces/body log-U[1,64] "
-                               "(pool of 8192 bodies), hull points log-U[8,512]; fwd + grad in "
+        "config": {"workload": f"uneven batch: {args.pairs} body pairs drawn from a pool of "
+                               f"{sc.geom.n_bodies} distinct bodies ({sc.geom.n_pieces} pieces), "
+                               "pieces/body log-U[1,64], hull points log-U[8,512]; fwd + grad in "
                                "one CUDA graph", "piece_pairs_per_gpu": sc.piece_pairs(),
+                   "bodies": sc.geom.n_bodies, "pieces": sc.geom.n_pieces,
                    "pieces_per_body_mean": float(npb[sc.pair_a].mean()),
                    "l2": "flushed between timed steps (512 MiB write, untimed)",
                    "tuning": tuning, "generation_s": t_gen},
@@ -630,7 +636,8 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
         calls = [(pa[i0[k]:i1[k]].data_ptr(), pb[i0[k]:i1[k]].data_ptr(), ys[k].data_ptr(),
                   yb[k].data_ptr() if grad[k] else None, gs[k].data_ptr() if grad[k] else None)
                  for k in range(n_req)]
-        return {"arr": arr, "A": A, "B": B, "qp": qp, "reqs": reqs, "calls": calls, "keep": keep}
+        return {"arr": arr, "A": A, "B": B, "qp": qp, "reqs": reqs, "calls": calls, "keep": keep,
+                "i0": i0, "i1": i1}
 
     def served(P):
         """Continuous batching: the native load generator (ccm_serve_replay)
@@ -689,6 +696,55 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
                 "qps": P["qp"] / t_plain, "req_s": n_req / t_plain,
                 "client_lag_p99_ms": _pct(lag, 99)}
 
+    def plain_batched(P, reps=5):
+        """The same request mix as plain batched launches on the same GPU:
+        the forward-only requests' pairs as one batch (ccm_contacts), the
+        forward + gradient requests' pairs as another (ccm_contacts_save and
+        ccm_contacts_backward_saved), back to back on one stream, as if every
+        request had arrived at once and been planned together."""
+        cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, np.uint64)
+        kinds = [c[3] is not None for c in P["calls"]]
+        out = {}
+        runs = []
+        for want_grad in (False, True):
+            ks = [k for k in range(n_req) if kinds[k] == want_grad]
+            if not ks:
+                continue
+            A, B = cat([P["A"][k] for k in ks]), cat([P["B"][k] for k in ks])
+            rows = np.concatenate([np.arange(P["i0"][k], P["i1"][k]) for k in ks])
+            bt = ctx.batch(A, B)
+            ra = torch.from_numpy(rows).cuda()
+            p_a, p_b = pa[ra].contiguous(), pb[ra].contiguous()
+            yy = torch.empty((bt.n_groups, 8), device="cuda")
+            if want_grad:
+                gro = torch.cat([ybar_all[off[P["i0"][k]]:off[P["i1"][k]]] for k in ks])
+                rec = bt.saved_buffer()
+                gg = torch.empty((bt.n_pairs, 12), device="cuda")
+                runs.append(lambda bt=bt, p_a=p_a, p_b=p_b, yy=yy, rec=rec, gro=gro, gg=gg: (
+                    bt.contacts(p_a, p_b, out=yy, saved=rec),
+                    bt.backward(p_a, p_b, gro, saved=rec, out=(gg, None, None))))
+            else:
+                runs.append(lambda bt=bt, p_a=p_a, p_b=p_b, yy=yy: bt.contacts(p_a, p_b, out=yy))
+            out.setdefault("batches", []).append(bt)
+        for _ in range(3):
+            for r in runs:
+                r()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            for r in runs:
+                r()
+        b.record()
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3 / reps
+        for bt in out["batches"]:
+            bt.close()
+        return {"ms": 1e3 * t, "qps": P["qp"] / t, "req_s": n_req / t,
+                "note": "all requests at once: forward-only pairs in one batch, forward + "
+                        "gradient pairs in another, planned in advance (not timed), launched "
+                        "back to back; device time (CUDA events), mean of 5"}
+
     sat = served(prepare([rank, 99], None))
     if rates is None and args.serve_rates != "auto":
         rates = [float(r) for r in args.serve_rates.split(",")]
@@ -697,14 +753,28 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
         loads = list(SERVE_LOADS)
         rates = [f * sat["req_s"] for f in loads]
     results = []
-    for ri, rate in enumerate(rates):
+
+    def run_rate(ri, rate, load):
         P = prepare([rank, ri], rate)
         row = {"rate_req_s": rate, "requests": n_req, "piece_pairs": P["qp"]}
-        if loads is not None:
-            row["load"] = loads[ri]
+        if load is not None:
+            row["load"] = load
         row["served"] = served(P)
         row["per_request_launch"] = per_request(P)
         results.append(row)
+        return P
+    for ri, rate in enumerate(rates):
+        P = run_rate(ri, rate, loads[ri] if loads is not None else None)
+    if loads is not None:
+        # past the burst estimate: raise the offered rate until the loop
+        # serves less than it is offered, so that the sweep reaches saturation
+        f = loads[-1]
+        while (results[-1]["served"]["req_s"] >= 0.95 * results[-1]["rate_req_s"]
+               and f < 4.0):
+            f *= 1.5
+            P = run_rate(len(results), f * sat["req_s"], round(f, 3))
+    top = max(results, key=lambda r: r["served"]["req_s"])
+    plain = plain_batched(P)
     return {"geometry": f"uneven pool: {sc.n_pairs} placed pairs over "
                         f"{len(npb)} bodies, pieces/body log-U[1,64], hull points log-U[8,512]",
             "requests": "Poisson arrivals; 1-256 envs log-uniform; 50/50 fwd vs fwd+grad",
@@ -712,6 +782,9 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
             "saturation": {"requests": n_req, "arrivals": "all at t = 0",
                            "req_s": sat["req_s"], "qps": sat["qps"],
                            "mean_wave_pairs": sat["mean_wave_pairs"]},
+            "served_max": {"req_s": top["served"]["req_s"], "qps": top["served"]["qps"],
+                           "at_rate_req_s": top["rate_req_s"]},
+            "plain_batched": plain,
             "latency": "arrival to completion as seen by the host (ms)", "sweep": results}
 
 
@@ -735,6 +808,8 @@ def main():
                          "0.1-1.2 x the measured saturation rate")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven-batch line of the default run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank = int(os.environ.get("RANK", "0"))
@@ -768,6 +843,22 @@ def main():
                 "config": {"workload": "serving loop at the highest swept rate"}, "serving": sv}))
         return
     out, sc = run_ours(args, rank, world)
+    if not args.no_uneven:
+        # the uneven batch (65,536 pairs, forward + gradient, autotuned shape,
+        # one CUDA graph) as its own line inside the default run
+        un, usc = run_uneven(args, rank, world)
+        if rank == 0:
+            if not args.no_cpu_baseline:
+                qps, cores, sample, dt = oracle_sample_rate(usc, target_s=8.0, kind="grad",
+                                                            what="body pairs")
+                un["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": cores,
+                                      "kind": "oracle",
+                                      "sample": sample + f"; fwd + grad, {dt:.1f} s"}
+            out["uneven"] = {k: un[k] for k in ("value", "unit", "ms_per_step", "config",
+                                                "breakdown", "gpu_launches", "roofline",
+                                                "work_counters", "clocks", "cpu_baseline")
+                             if k in un}
+        del usc
     if rank == 0 and not args.no_serve:
         out["serving"] = run_serve(args, rank, world, n_req=args.serve_requests)
     if rank == 0:

@@ -27,6 +27,20 @@
  *     no active contact is (d_max, 0, 0, 0, 0, 0, 0, 0).
  *   - Twist coordinates of a pair (derivatives): (w_A, v_A, w_B, v_B), with
  *     R_X <- Exp([w_X]x) R_X, t_X <- t_X + v_X.
+ *
+ * How the calls map to a per-call signature that passes the pairs each time,
+ * ccm_contacts(ctx, n, A[n], B[n], pose_a, pose_b, params, outputs, stream):
+ *   - the pair list (A[i], B[i]) is planned once by ccm_batch_create, which
+ *     uploads the pair table and the work items and allocates the workspace;
+ *     ccm_contacts(batch, pose_a, pose_b, params, y, stream) then takes only
+ *     what changes between steps (poses and params), so that it neither
+ *     allocates nor synchronises;
+ *   - the outputs are one array y[G, 8] (array of structures, the row layout
+ *     above) rather than separate depth / weight / point / normal arrays;
+ *     the group offsets come from ccm_batch_info (or ccm_output_size);
+ *   - the reverse pass takes its cotangents in the same [G, 8] layout and
+ *     returns 12 twist components per pair (w_A, v_A, w_B, v_B);
+ *   - ccm_poll also returns the request's latency.
  */
 #ifndef CCM_H_
 #define CCM_H_
@@ -252,6 +266,10 @@ CCM_API ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a,
  *     tuning's `groups`); larger batches are rejected with CCM_ERR_INVALID.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process: after a device reset
+ *     (cudaDeviceReset, or a framework that destroys and recreates the
+ *     device's primary context) it is stale, so do not call this entry point
+ *     again in that process.
  *   - Every call on a device shares the array and it keeps the last call's
  *     contents.  Nothing in it needs to start at zero: each call writes every
  *     slot it reads.  Calls that overlap on the GPU (other streams, other

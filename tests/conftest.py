@@ -18,3 +18,14 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Prints the parity comparisons against the plain bars (no FP32
+    conditioning allowances) that the GPU tests recorded."""
+    gu = sys.modules.get("gpu_util")
+    lines = getattr(gu, "REPORT", None) if gu else None
+    if lines:
+        terminalreporter.section("parity against the plain bars")
+        for ln in lines:
+            terminalreporter.write_line(ln)

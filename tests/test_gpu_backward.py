@@ -4,7 +4,7 @@ the C ABI and through torch.autograd (double backward)."""
 import numpy as np
 import pytest
 
-from gpu_util import COND_FACTOR, GRAD_RTOL, fp32_sensitivity
+from gpu_util import COND_FACTOR, GRAD_RTOL, MAX_WIDENED_SHARE, fp32_sensitivity, report_derivs
 from paper_2604_17538_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +37,8 @@ def _inputs(sc, seed=0):
 def _per_pair_check(g, o, what, rtol=GRAD_RTOL, floor=1e-6):
     """||g - o||_inf <= rtol ||o||_inf per pair (rows); rtol may be per pair."""
     assert np.all(np.isfinite(g)), f"{what}: non-finite values"
+    rt = np.broadcast_to(np.asarray(rtol, np.float64), (len(g),))
+    report_derivs(g, o, what, widened=(rt > GRAD_RTOL).sum())
     err = np.abs(g - o).max(1)
     scale = np.abs(o).max(1)
     bad = err > rtol * scale + floor
@@ -69,6 +71,9 @@ def test_gradient_hvp_jvp_match_oracle(oracle_lib, ctx, cases, name):
     tol_h = np.maximum(GRAD_RTOL, COND_FACTOR * kh)
     print(f"{name}: pairs with a widened bar: grad {int((tol_g > GRAD_RTOL).sum())}, "
           f"hvp {int((tol_h > GRAD_RTOL).sum())} of {sc.n_pairs}")
+    # conditioning may widen the bar of a few ill-conditioned pairs, not of many
+    assert (tol_g > GRAD_RTOL).mean() <= MAX_WIDENED_SHARE
+    assert (tol_h > GRAD_RTOL).mean() <= MAX_WIDENED_SHARE
     rg = _per_pair_check(g.double().cpu().numpy(), go, f"{name} gradient", tol_g)
     _per_pair_check(g2.double().cpu().numpy(), go, f"{name} gradient (dual pass)", tol_g)
     rh = _per_pair_check(hv.double().cpu().numpy(), hvo, f"{name} H u", tol_h)

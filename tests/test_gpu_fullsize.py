@@ -14,7 +14,7 @@ every empty group exactly (d_max, 0, 0, 0)."""
 import numpy as np
 import pytest
 
-from gpu_util import COND_FACTOR, GRAD_RTOL, compare, fp32_sensitivity, weight_slack
+from gpu_util import COND_FACTOR, GRAD_RTOL, compare, fp32_sensitivity, report_derivs, weight_slack
 from paper_2604_17538_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +44,8 @@ def _check_whole(y):
 def _check_pairs(got, ref, tol, what):
     got = np.asarray(got, np.float64)
     assert np.all(np.isfinite(got)), what
+    rt = np.broadcast_to(np.asarray(tol, np.float64), (len(got),))
+    report_derivs(got, ref, what, widened=(rt > GRAD_RTOL).sum())
     err = np.abs(got - ref).max(1)
     scale = np.abs(ref).max(1)
     bad = err > tol * scale + 1e-6
@@ -197,11 +199,15 @@ def test_uneven_65536_autotuned_sampled_against_oracle(oracle_lib, ctx):
     npb = np.diff(sc.geom.body_piece_off)
     pp = npb[sc.pair_a] * npb[sc.pair_b]
     rng = np.random.default_rng(19)
-    # a sample across the range of sizes the oracle recomputes in seconds:
-    # pairs of up to 256 piece pairs, and the largest pieces counts among them
+    # a sample across the range of sizes: pairs of up to 256 piece pairs, the
+    # largest counts among them, and the 8 heaviest pairs of the launch (over
+    # 1,024 piece pairs each), whose bodies span many staged chunks in the
+    # autotuned shape
     light = np.nonzero(pp <= 256)[0]
+    heavy = np.argsort(pp, kind="stable")[-8:]
+    assert pp[heavy].min() > 1024
     idx = np.sort(np.concatenate([rng.choice(light, 20, replace=False),
-                                  light[np.argsort(pp[light])[-4:]]]))
+                                  light[np.argsort(pp[light])[-4:]], heavy]))
     idx = np.unique(idx)
     sub = sc.take(idx)
     rows = _rows(off, idx)

@@ -1,6 +1,9 @@
 """The data-parallel (N > 1) path on the CPU: two `gloo` ranks, each with its
 own shard, reduce their timings (max) and their work (sum) into one whole-job
-rate, and their shards come from disjoint, reproducible seed streams."""
+rate, and their shards come from disjoint, reproducible seed streams.  A
+global batch split over the ranks by contiguous pair ranges is gathered back
+in global pair order (the oracle stands in for each rank's GPU outputs in
+this test only)."""
 import os
 import socket
 
@@ -59,3 +62,45 @@ def test_single_process_reductions_are_identities():
     assert shard.reduce_sum([3, 4]) == [3.0, 4.0]
     assert shard.job_rate(10, 2.0) == (10.0, 2.0, 5.0)
     assert shard.shard_seed(2, 0) == 2 and shard.shard_seed(2, 3) == 3002
+
+
+def _gather_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    import oracle
+    from paper_2604_17538_b300 import scenes, shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sc = scenes.hull_env_scene(seed=7, n_envs=5, workers=1)   # one global batch
+        lo, hi = shard.shard_range(sc.n_pairs, rank, world)
+        mine = sc.take(np.arange(lo, hi))
+        ybar = np.random.default_rng(1).normal(size=(int(sc.group_offsets()[-1]), 8))
+        off = sc.group_offsets()
+        y = oracle.forward(mine, threads=1)                        # this rank's rows
+        g, _ = oracle.gradient(mine, ybar[off[lo]:off[hi]], threads=1)
+        y_all = shard.gather_rows(y)
+        g_all = shard.gather_rows(g)
+        if rank == 0:
+            np.savez(os.path.join(out_dir, "gathered.npz"), y=y_all, g=g_all, ybar=ybar)
+        else:
+            assert y_all is None and g_all is None
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_gather_outputs_in_pair_order(tmp_path, oracle_lib):
+    import torch.multiprocessing as mp
+    from paper_2604_17538_b300 import scenes, shard
+    world = 2
+    assert [shard.shard_range(5, k, 2) for k in range(2)] == [(0, 3), (3, 5)]
+    assert [shard.shard_range(2, k, 3) for k in range(3)] == [(0, 1), (1, 2), (2, 2)]
+    mp.start_processes(_gather_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    r = np.load(tmp_path / "gathered.npz")
+    sc = scenes.hull_env_scene(seed=7, n_envs=5, workers=1)
+    y = oracle_lib.forward(sc, threads=1)
+    g, _ = oracle_lib.gradient(sc, r["ybar"], threads=1)
+    assert r["y"].shape == y.shape and np.array_equal(r["y"], y)
+    assert np.array_equal(r["g"], g)
