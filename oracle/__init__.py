@@ -54,7 +54,13 @@ class _Geom(C.Structure):
 
 
 DEFAULTS = dict(tau_sdf=5e-3, tau_trace=5e-3, tau_clip=5e-3, tau_blend=5e-3,
-                d_max=0.01, gate_width=0.01, trace_iters=3)
+                d_max=0.01, gate_width=0.01, trace_iters=3, flags=0)
+
+# forward variants (flags): the other body's SDF as the smooth union of its
+# pieces (Sec. 3.1, Eq. soft_union); contact points projected onto the SDF's
+# isosurface (Sec. 4.1)
+FLAG_BODY_UNION = 2
+FLAG_PROJECT = 4
 
 _lib = None
 
@@ -81,6 +87,8 @@ def lib():
         _lib.ccmo_sigmoid.restype = D
         _lib.ccmo_pair_contacts.argtypes = [P, I64, I64, P, P, P, P, I64]
         _lib.ccmo_pair_contacts.restype = I64
+        _lib.ccmo_body_sdf.argtypes = [P, I64, P, D, P]
+        _lib.ccmo_body_sdf.restype = D
     return _lib
 
 
@@ -89,7 +97,7 @@ def params(**kw) -> Params:
     d.update(kw)
     return Params(float(d["tau_sdf"]), float(d["tau_trace"]), float(d["tau_clip"]),
                   float(d["tau_blend"]), float(d["d_max"]), float(d["gate_width"]),
-                  int(d["trace_iters"]), 0)
+                  int(d["trace_iters"]), int(d["flags"]))
 
 
 def _ptr(a):
@@ -188,6 +196,16 @@ def edge_point(planes, vI, vII, prm=None):
     lib().ccmo_edge_point(_ptr(planes), len(planes), _ptr(a), _ptr(b), C.byref(prm),
                           _ptr(pe), _ptr(al))
     return pe, al
+
+
+def body_sdf(geom, body, x, tau):
+    """(phi, grad phi) of the smooth union of body ``body``'s pieces at x
+    (body frame; Sec. 3.1, Eq. soft_union)."""
+    g = _Packed(geom)
+    x = np.ascontiguousarray(x, np.float64).reshape(3)
+    grad = np.zeros(3)
+    phi = lib().ccmo_body_sdf(g.ref(), int(body), _ptr(x), float(tau), _ptr(grad))
+    return phi, grad
 
 
 def transition(d, d_max=0.01, eps=0.01):

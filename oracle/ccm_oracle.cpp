@@ -28,6 +28,16 @@
 //   * outputs are in world frame, normals point out of the SDF body;
 //   * pose derivatives use the twist chart R <- Exp(w) R, t <- t + v per body.
 //
+// Variants selected by ccmo_params.flags (forward values only):
+//   * kFlagBodyUnion: the SDF of the other body is the smooth union
+//     (Sec. 3.1, Eq. soft_union) of its pieces' SDFs,
+//     phi_S(x) = -tau LSE(-phi_s(x) / tau) over the pieces s, with the same
+//     softness tau_sdf, and every feature of a group gives one contact
+//     against the whole body instead of one per piece;
+//   * kFlagProject: every contact point is moved onto the SDF's isosurface
+//     (Sec. 4.1), proj(p) = p - phi(p) n(p) with n = grad phi, after its
+//     depth and normal were taken at p.
+//
 // Derivatives: the same templated code runs on forward-mode dual numbers.
 // Dual<double,12> gives the exact gradient with respect to the 12 twist
 // coordinates of a pair; Dual<Dual<double,1>,12> gives, in one pass, the
@@ -195,7 +205,7 @@ struct ccmo_params {
   double d_max;       // distance threshold (Sec. 4.3)
   double gate_width;  // transition bandwidth epsilon (Sec. 4.3)
   int32_t trace_iters;  // sphere-trace iterations (three in Sec. 4.2)
-  int32_t flags;      // unused, reserved
+  int32_t flags;      // kFlagBodyUnion | kFlagProject (forward variants)
 };
 struct ccmo_geom {
   const int64_t* body_piece_off;
@@ -266,6 +276,58 @@ T piece_sdf(const double* planes, int F, const V3<T>& x, double tau, V3<T>* grad
   return phi;
 }
 
+// the SDF of one convex piece as a callable: phi(x) and, if grad, grad phi
+struct PieceSdf {
+  const double* planes;
+  int F;
+  double tau;
+  template <class T> T operator()(const V3<T>& x, V3<T>* grad) const {
+    return piece_sdf(planes, F, x, tau, grad);
+  }
+};
+
+// --------------------------------------------------------------------------
+// Sec. 3.1 Eq. soft_union: smooth union of the pieces of one body,
+// phi_S(x) = -tau log sum_s exp(-phi_s(x) / tau), evaluated min-shifted:
+// m - tau log sum_s exp(-(phi_s - m) / tau), m = min_s phi_s.  Its gradient
+// is the softmin-weighted sum of the pieces' gradients.
+// --------------------------------------------------------------------------
+constexpr int32_t kFlagBodyUnion = 2;
+constexpr int32_t kFlagProject = 4;
+
+struct BodyUnionSdf {
+  const ccmo_geom* G;
+  int64_t body;
+  double tau;
+  template <class T> T operator()(const V3<T>& x, V3<T>* grad) const {
+    const int64_t s0 = G->body_piece_off[body], s1 = G->body_piece_off[body + 1];
+    std::vector<T> phis;
+    std::vector<V3<T>> gs;
+    int smin = 0;
+    for (int64_t s = s0; s < s1; ++s) {
+      V3<T> g;
+      const double* planes = G->planes + 4 * G->piece_f_off[s];
+      const int F = (int)(G->piece_f_off[s + 1] - G->piece_f_off[s]);
+      phis.push_back(piece_sdf(planes, F, x, tau, grad ? &g : nullptr));
+      gs.push_back(g);
+      if (val(phis.back()) < val(phis[smin])) smin = (int)phis.size() - 1;
+    }
+    T m = phis[smin];
+    T S(0.0);
+    std::vector<T> e(phis.size());
+    for (size_t k = 0; k < phis.size(); ++k) {
+      e[k] = exp(-(phis[k] - m) / tau);
+      S = S + e[k];
+    }
+    if (grad) {
+      V3<T> g = zero3<T>();
+      for (size_t k = 0; k < phis.size(); ++k) g = g + (e[k] / S) * gs[k];
+      *grad = g;
+    }
+    return m - tau * log(S);
+  }
+};
+
 // --------------------------------------------------------------------------
 // Sec. 4.3: C^2 non-increasing transition, 1 for d <= d_max - eps, 0 for d >= d_max
 // --------------------------------------------------------------------------
@@ -291,29 +353,36 @@ void mollify(Contact<T>& c, const ccmo_params& prm) {
 // --------------------------------------------------------------------------
 // Sec. 4.2: narrow phase
 // --------------------------------------------------------------------------
-// V-SDF: the vertex itself is the contact point
+// Sec. 4.1 isosurface projection of a contact point: p - phi(p) n(p)
 template <class T>
-Contact<T> vertex_contact(const double* planes, int F, const V3<T>& x, const ccmo_params& prm) {
+void project(Contact<T>& c, const ccmo_params& prm) {
+  if (prm.flags & kFlagProject) c.p = c.p - c.phi * c.n;
+}
+
+// V-SDF: the vertex itself is the contact point
+template <class T, class Sdf>
+Contact<T> vertex_contact(const Sdf& sdf, const V3<T>& x, const ccmo_params& prm) {
   Contact<T> c;
   c.p = x;
-  c.phi = piece_sdf(planes, F, x, prm.tau_sdf, &c.n);
+  c.phi = sdf(x, &c.n);
   mollify(c, prm);
+  project(c, prm);
   return c;
 }
 
 // E-SDF: sphere trace corner v_I along +e_t and corner v_II along -e_t,
 //   p_{k+1} = p_k +/- sigmoid(phi(p_k)/tau_trace) phi(p_k) e_t,
 // soft clip both traced points to the edge, and take their midpoint p^e.
-template <class T>
-V3<T> edge_point(const double* planes, int F, const V3<T>& vI, const V3<T>& vII,
+template <class T, class Sdf>
+V3<T> edge_point(const Sdf& sdf, const V3<T>& vI, const V3<T>& vII,
                  const ccmo_params& prm, T* alpha_out = nullptr) {
   V3<T> dv = vII - vI;
   T L = sqrt(dot(dv, dv));
   V3<T> et = (1.0 / L) * dv;
   V3<T> pI = vI, pII = vII;
   for (int k = 0; k < prm.trace_iters; ++k) {
-    T phiI = piece_sdf<T>(planes, F, pI, prm.tau_sdf, nullptr);
-    T phiII = piece_sdf<T>(planes, F, pII, prm.tau_sdf, nullptr);
+    T phiI = sdf(pI, (V3<T>*)nullptr);
+    T phiII = sdf(pII, (V3<T>*)nullptr);
     pI = pI + (sigmoid(phiI / prm.tau_trace) * phiI) * et;
     pII = pII - (sigmoid(phiII / prm.tau_trace) * phiII) * et;
   }
@@ -327,13 +396,14 @@ V3<T> edge_point(const double* planes, int F, const V3<T>& vI, const V3<T>& vII,
   return vI + (0.5 * (cI + cII)) * et;
 }
 
-template <class T>
-Contact<T> edge_contact(const double* planes, int F, const V3<T>& vI, const V3<T>& vII,
+template <class T, class Sdf>
+Contact<T> edge_contact(const Sdf& sdf, const V3<T>& vI, const V3<T>& vII,
                         const ccmo_params& prm) {
   Contact<T> c;
-  c.p = edge_point(planes, F, vI, vII, prm);
-  c.phi = piece_sdf(planes, F, c.p, prm.tau_sdf, &c.n);
+  c.p = edge_point(sdf, vI, vII, prm);
+  c.phi = sdf(c.p, &c.n);
   mollify(c, prm);
+  project(c, prm);
   return c;
 }
 
@@ -390,16 +460,26 @@ void group_contacts(const ccmo_geom& G, int64_t fp, const Pose<T>& PF, int64_t b
     const double* v = G.verts + 3 * (v0 + i);
     xw[i] = apply(PF, V3<T>{T(v[0]), T(v[1]), T(v[2])});
   }
-  for (int64_t s = G.body_piece_off[bodyS]; s < G.body_piece_off[bodyS + 1]; ++s) {
-    const double* planes = G.planes + 4 * G.piece_f_off[s];
-    const int F = (int)(G.piece_f_off[s + 1] - G.piece_f_off[s]);
-    // the features in the SDF body frame
-    std::vector<V3<T>> x(nv);
-    for (int64_t i = 0; i < nv; ++i) x[i] = apply_inverse(PS, xw[i]);
-    for (int64_t i = 0; i < nv; ++i) cs.push_back(vertex_contact(planes, F, x[i], prm));
+  // the features in the SDF body frame
+  std::vector<V3<T>> x(nv);
+  for (int64_t i = 0; i < nv; ++i) x[i] = apply_inverse(PS, xw[i]);
+  if (prm.flags & kFlagBodyUnion) {
+    // one contact per feature against the smooth union of body S's pieces
+    const BodyUnionSdf sdf{&G, bodyS, prm.tau_sdf};
+    for (int64_t i = 0; i < nv; ++i) cs.push_back(vertex_contact(sdf, x[i], prm));
     for (int64_t j = 0; j < ne; ++j) {
       const int32_t* e = G.edges + 2 * (e0 + j);
-      cs.push_back(edge_contact(planes, F, x[e[0]], x[e[1]], prm));
+      cs.push_back(edge_contact(sdf, x[e[0]], x[e[1]], prm));
+    }
+  } else {
+    for (int64_t s = G.body_piece_off[bodyS]; s < G.body_piece_off[bodyS + 1]; ++s) {
+      const PieceSdf sdf{G.planes + 4 * G.piece_f_off[s],
+                         (int)(G.piece_f_off[s + 1] - G.piece_f_off[s]), prm.tau_sdf};
+      for (int64_t i = 0; i < nv; ++i) cs.push_back(vertex_contact(sdf, x[i], prm));
+      for (int64_t j = 0; j < ne; ++j) {
+        const int32_t* e = G.edges + 2 * (e0 + j);
+        cs.push_back(edge_contact(sdf, x[e[0]], x[e[1]], prm));
+      }
     }
   }
   for (auto& c : cs) {
@@ -552,10 +632,21 @@ double ccmo_sdf(const double* planes, int F, const double* x, double tau, double
 void ccmo_edge_point(const double* planes, int F, const double* vI, const double* vII,
                      const ccmo_params* prm, double* pe, double* alpha) {
   double a[4];
-  V3<double> p = edge_point<double>(planes, F, V3<double>{vI[0], vI[1], vI[2]},
+  const PieceSdf sdf{planes, F, prm->tau_sdf};
+  V3<double> p = edge_point<double>(sdf, V3<double>{vI[0], vI[1], vI[2]},
                                     V3<double>{vII[0], vII[1], vII[2]}, *prm, a);
   pe[0] = p.x; pe[1] = p.y; pe[2] = p.z;
   if (alpha) for (int k = 0; k < 4; ++k) alpha[k] = a[k];
+}
+
+// smooth-union SDF of body `body` at x (body frame) and its gradient
+double ccmo_body_sdf(const ccmo_geom* G, int64_t body, const double* x, double tau,
+                     double* grad) {
+  const BodyUnionSdf sdf{G, body, tau};
+  V3<double> g;
+  const double phi = sdf(V3<double>{x[0], x[1], x[2]}, &g);
+  if (grad) { grad[0] = g.x; grad[1] = g.y; grad[2] = g.z; }
+  return phi;
 }
 
 double ccmo_transition(double d, double d_max, double eps) { return transition<double>(d, d_max, eps); }
