@@ -175,6 +175,10 @@ typedef struct {
                                  3x that (0: 512; at least the largest piece's), 0 or 16..4096 */
   int32_t groups_b;           /* reverse pass: feature pieces per chunk (0: 4; at most
                                  groups), 0..32 */
+  int32_t flat_records;       /* capacity of the contact list that ccm_contacts_save keeps
+                                 for the per-contact reverse passes, in records per output
+                                 group (0: 16, and at least 65,536 in all; -1: no list, the
+                                 reverse passes re-gate per pair), -1..4096 */
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
 /* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of
@@ -199,9 +203,10 @@ CCM_API ccm_status ccm_contacts_backward(ccm_batch batch, const float* pose_a, c
                                  float* grad, float* hvp, float* jvp, ccm_stream stream);
 
 /* Floats per output group of the record ccm_contacts_save keeps for the
- * reverse pass: the group's blend partial and which of the SDF body's pieces
- * gave it a contact of non-zero weight. */
-#define CCM_SAVED_FLOATS 26
+ * reverse pass: the group's blend partial, which of the SDF body's pieces
+ * gave it a contact of non-zero weight, and the tag of the contact list the
+ * same call kept in the batch. */
+#define CCM_SAVED_FLOATS 28
 
 /* ccm_contacts that also fills saved (device [G, CCM_SAVED_FLOATS] float32,
  * fully overwritten) for ccm_contacts_backward_saved.  Asynchronous on
@@ -211,11 +216,19 @@ CCM_API ccm_status ccm_contacts_save(ccm_batch batch, const float* pose_a, const
                                      ccm_stream stream);
 
 /* ccm_contacts_backward given the record of a ccm_contacts_save call with the
- * same batch, poses and params: its passes visit only the (piece, piece)
- * directions that gave a contact in the forward pass, the only ones with a
- * non-zero adjoint, instead of re-running the broad phase over all of them.
- * Results equal ccm_contacts_backward's up to float rounding order; a record
- * of other poses gives wrong results.  Asynchronous on `stream`.
+ * same batch, poses and params: its passes visit only the contacts that had
+ * a non-zero weight in the forward pass, the only ones with a non-zero
+ * adjoint, instead of re-running the broad phase over all piece pairs.  When
+ * every body has at most 256 pieces, ccm_contacts_save also keeps a list of
+ * those contacts in the batch (tuning flat_records), and the passes run one
+ * contact per thread from it: recompute the contact, blend each group,
+ * form its adjoint coefficients, back-propagate each contact into a force
+ * and a torque, and sum them per pair in a fixed order.  If the list
+ * overflowed (or without it) they revisit, per pair, the (piece, piece)
+ * directions the record marks.  Results equal ccm_contacts_backward's up to
+ * float rounding order and do not depend on the rest of the batch; a record
+ * of other poses (or a list of another ccm_contacts_save of the batch) gives
+ * wrong results.  Asynchronous on `stream`.
  * Errors: CCM_ERR_INVALID, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pose_a,
                                                const float* pose_b, const ccm_params* prm,
@@ -308,8 +321,10 @@ CCM_API ccm_status ccm_contacts_counted(ccm_batch batch, const float* pose_a, co
  * (saved may be NULL: ccm_contacts_backward) plus device atomics on
  * `counters` (device, CCM_N_COUNTERS int64, zeroed by the caller). */
 enum {
-  CCM_BWD_CNT_DIRS = 0,       /* directions examined by a gate or the hit marks */
-  CCM_BWD_CNT_DIRS_LIVE = 1,  /* directions run through lists */
+  CCM_BWD_CNT_DIRS = 0,       /* directions examined by a gate or the hit marks
+                                 (per-contact passes: contacts evaluated) */
+  CCM_BWD_CNT_DIRS_LIVE = 1,  /* directions run through lists (per-contact passes:
+                                 contacts of a group with a non-zero weight) */
   CCM_BWD_CNT_MAXPASS = 2,    /* plane evaluations of the max-plane passes */
   CCM_BWD_CNT_GATEPASS = 3,   /* plane evaluations of piece-pair gates */
   CCM_BWD_CNT_P1_GRAD = 4,    /* pass 1: plane evaluations with gradient */

@@ -22,7 +22,7 @@ STATUS_NAMES = ["CCM_OK", "CCM_ERR_INVALID", "CCM_ERR_OOM", "CCM_ERR_CUDA", "CCM
                 "CCM_ERR_BUSY", "CCM_ERR_NOT_READY", "CCM_ERR_UNKNOWN_TICKET"]
 CCM_FLAG_NO_CULL = 1
 CCM_N_COUNTERS = 8
-CCM_SAVED_FLOATS = 26
+CCM_SAVED_FLOATS = 28
 COUNTER_NAMES = ["dirs", "dirs_live", "maxpass", "gatepass", "eval_grad", "eval_val",
                  "contacts", "features"]
 BWD_COUNTER_NAMES = ["dirs", "dirs_live", "maxpass", "gatepass", "p1_grad", "p1_val", "p2_hv",
@@ -51,7 +51,7 @@ class ccm_tuning(C.Structure):
     _fields_ = [("item_v", C.c_int32), ("item_e", C.c_int32), ("item_vb", C.c_int32),
                 ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("groups", C.c_int32),
                 ("stage_planes", C.c_int32), ("stage_verts", C.c_int32),
-                ("groups_b", C.c_int32)]
+                ("groups_b", C.c_int32), ("flat_records", C.c_int32)]
 
 
 class ccm_serve_config(C.Structure):

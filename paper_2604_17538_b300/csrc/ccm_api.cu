@@ -330,7 +330,9 @@ ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t) {
   if (!batch || !t) return fail(CCM_ERR_INVALID, "bad arguments");
   Batch* b = reinterpret_cast<Batch*>(batch);
   std::lock_guard<std::mutex> lk(b->ctx->mu);
-  return apply_tuning(b->ctx, b, *t);
+  const ccm_status s = apply_tuning(b->ctx, b, *t);
+  if (s != CCM_OK) return s;
+  return setup_flat(b->ctx, b);
 }
 
 ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
@@ -669,10 +671,89 @@ ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom*
   bt->mx = mx;
   ccm_status s;
   if ((s = upload(bt->d_pairs, pairs, "pairs")) != CCM_OK) return s;
+  {   // pair and side of every output group
+    std::vector<int32_t> rp((size_t)std::max<int64_t>(1, G));
+    for (int64_t i = 0; i < n; ++i) {
+      const int npA = c->bodies[pairs[i].bodyA].np, npB = c->bodies[pairs[i].bodyB].np;
+      for (int q = 0; q < npA + npB; ++q)
+        rp[pairs[i].goff + q] = (int32_t)((i << 1) | (q < npA ? 0 : 1));
+    }
+    if ((s = upload(bt->d_row_pair, rp, "group pairs")) != CCM_OK) return s;
+  }
   bt->pairs = std::move(pairs);
   ccm_tuning t;
   default_tuning(&t);
-  return apply_tuning(c, bt, t);
+  if ((s = apply_tuning(c, bt, t)) != CCM_OK) return s;
+  return setup_flat(c, bt);
+}
+
+ContactList Batch::contact_list() const {
+  ContactList cl{};
+  if (!flat_cap) return cl;
+  cl.recs = static_cast<int4*>(d_frecs.ptr);
+  cl.sorted = static_cast<int4*>(d_fsorted.ptr);
+  cl.cap = flat_cap;
+  cl.ctl = static_cast<unsigned long long*>(d_fctl.ptr);
+  cl.cnt_v = static_cast<int32_t*>(d_fcnt.ptr);
+  cl.cnt_e = cl.cnt_v + G;
+  cl.off_v = static_cast<int32_t*>(d_foff.ptr);
+  cl.off_e = cl.off_v + (G + 1);
+  return cl;
+}
+
+FlatPass Batch::flat_pass(bool dual) const {
+  const DevBuf* b = d_fpass[dual ? 1 : 0];
+  FlatPass f;
+  f.cval = b[0].ptr;
+  f.force = b[1].ptr;
+  f.coef = b[2].ptr;
+  f.oterm = b[3].ptr;
+  f.sched = static_cast<int*>(b[4].ptr);
+  return f;
+}
+
+ccm_status setup_flat(Context* c, Batch* bt) {
+  const int fr = bt->tuning.flat_records;
+  int64_t cap = 0;
+  if (bt->per_pair && bt->G > 0 && fr >= 0)
+    cap = fr > 0 ? fr * bt->G
+                 : std::min<int64_t>(std::max<int64_t>(16 * bt->G, 65536), (int64_t)1 << 24);
+  if (cap == bt->flat_cap) return CCM_OK;
+  for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted})
+    b->release();
+  for (auto& pass : bt->d_fpass)
+    for (DevBuf& b : pass) b.release();
+  bt->flat_cap = 0;
+  if (cap == 0) return CCM_OK;
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+  auto alloc = [&](DevBuf& b, size_t bytes, const char* what) -> ccm_status {
+    const cudaError_t e = cudaMalloc(&b.ptr, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess)
+      return fail(CCM_ERR_OOM, "%s: cudaMalloc(%zu): %s", what, bytes, cudaGetErrorString(e));
+    b.bytes = std::max<size_t>(bytes, 256);
+    return CCM_OK;
+  };
+  const size_t G = (size_t)bt->G;
+  ccm_status s;
+  if ((s = alloc(bt->d_fctl, kCtlWords * sizeof(unsigned long long), "contact list")) != CCM_OK ||
+      (s = alloc(bt->d_fcnt, 2 * G * sizeof(int32_t), "contact counts")) != CCM_OK ||
+      (s = alloc(bt->d_foff, 2 * (G + 1) * sizeof(int32_t), "contact offsets")) != CCM_OK ||
+      (s = alloc(bt->d_frecs, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK ||
+      (s = alloc(bt->d_fsorted, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK)
+    return s;
+  for (int d = 0; d < 2; ++d) {
+    size_t sz[4];
+    flat_pass_bytes(d == 1, cap, bt->G, &sz[0], &sz[1], &sz[2], &sz[3]);
+    for (int q = 0; q < 4; ++q)
+      if ((s = alloc(bt->d_fpass[d][q], sz[q], "per-contact pass")) != CCM_OK) return s;
+    if ((s = alloc(bt->d_fpass[d][4], 3 * sizeof(int), "per-contact pass")) != CCM_OK) return s;
+  }
+  // a list that no forward filled yet reads as overflowed (the per-pair path)
+  unsigned long long init[kCtlWords] = {};
+  init[kCtlOverflow] = 1ull;
+  CCM_CUDA(cudaMemcpy(bt->d_fctl.ptr, init, sizeof(init), cudaMemcpyHostToDevice), "cudaMemcpy");
+  bt->flat_cap = cap;
+  return CCM_OK;
 }
 
 void default_tuning(ccm_tuning* t) {
@@ -693,7 +774,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
       t.fwd_warps > 4 || t.groups < 1 || t.groups > kGroupsPerChunk ||
       (t.stage_planes != 0 && (t.stage_planes < 16 || t.stage_planes > 4096)) ||
       (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)) ||
-      t.groups_b < 0 || t.groups_b > kGroupsPerChunk)
+      t.groups_b < 0 || t.groups_b > kGroupsPerChunk || t.flat_records < -1 ||
+      t.flat_records > 4096)
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -804,6 +886,32 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   L.hvp = hvp;
   L.jvp = dir ? jvp : nullptr;
   set_bwd_grids(*b, kp, dir != nullptr, &L);
+  if (saved && b->per_pair && b->flat_cap > 0) {
+    // the per-contact passes from the forward's contact list; the per-pair
+    // kernel runs only if that list overflowed
+    FlatLaunch F;
+    F.g = L.g;
+    F.pairs = L.pairs;
+    F.row_pair = static_cast<const int32_t*>(b->d_row_pair.ptr);
+    F.n_pairs = b->n;
+    F.G = b->G;
+    F.pose_a = pose_a;
+    F.pose_b = pose_b;
+    F.ybar = ybar;
+    F.dir = dir;
+    F.saved = saved;
+    F.kp = kp;
+    F.cl = b->contact_list();
+    F.fp = b->flat_pass(dir != nullptr);
+    F.grad = grad;
+    F.hvp = hvp;
+    F.jvp = dir ? jvp : nullptr;
+    F.counters = counters;
+    F.n_sm = b->ctx->n_sm;
+    cudaError_t e = launch_flat_backward(F, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "per-contact backward launch");
+    L.only_if = F.fp.sched + 2;
+  }
   cudaError_t e = launch_backward(L, stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return CCM_OK;
@@ -831,6 +939,11 @@ void Batch::release() {
   d_pair_order.release();
   d_sched.release();
   d_part.release();
+  d_row_pair.release();
+  for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted}) b->release();
+  for (auto& pass : d_fpass)
+    for (DevBuf& b : pass) b.release();
+  flat_cap = 0;
 }
 
 ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
@@ -858,8 +971,18 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   L.counters = counters;
   L.sched = static_cast<int*>(b->d_sched.ptr);
   L.grid = b->grid;
+  const bool flat = saved && b->flat_cap > 0;
+  if (flat) {
+    L.cl = b->contact_list();
+    if (++b->list_tag == 0u) b->list_tag = 1u;   // a new tag per list (0: none)
+    L.cl.tag = b->list_tag;
+  }
   cudaError_t e = launch_forward(L, stream);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  if (flat) {
+    e = launch_flat_prep(L.cl, b->G, b->ctx->n_sm, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "contact list launch");
+  }
   return CCM_OK;
 }
 

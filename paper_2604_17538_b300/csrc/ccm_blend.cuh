@@ -137,19 +137,23 @@ __device__ __forceinline__ void mark_hit(uint32_t* hit, int hw, int g, int sg, f
 }
 
 // What ccm_contacts_save keeps per output group for the reverse pass: the
-// group's blend partial (18 floats: M, U, rd, rf, rp, rn, Dd, Da, Dp, Dn) and
-// its hit words (kHitWords uint32, stored bit for bit; words past the
-// shared-memory table's hw are zero).
-constexpr int kSavedFloats = 18 + kHitWords;
+// group's blend partial (18 floats: M, U, rd, rf, rp, rn, Dd, Da, Dp, Dn), its
+// hit words (kHitWords uint32, stored bit for bit; words past the
+// shared-memory table's hw are zero), the tag of the contact list the same
+// forward kept (uint32; 0: none) and one zero word.
+constexpr int kSavedFloats = 18 + kHitWords + 2;
+constexpr int kSavedTag = 18 + kHitWords;
 
 __device__ __forceinline__ void save_group(float* o, const PartT<float>& a, const uint32_t* hit,
-                                           int hw) {
+                                           int hw, uint32_t tag) {
   o[0] = a.M; o[1] = a.U; o[2] = a.rd; o[3] = a.rf;
   o[4] = a.rp.x; o[5] = a.rp.y; o[6] = a.rp.z; o[7] = a.rn.x; o[8] = a.rn.y; o[9] = a.rn.z;
   o[10] = a.Dd; o[11] = a.Da;
   o[12] = a.Dp.x; o[13] = a.Dp.y; o[14] = a.Dp.z; o[15] = a.Dn.x; o[16] = a.Dn.y; o[17] = a.Dn.z;
   uint32_t* h = reinterpret_cast<uint32_t*>(o + 18);
   for (int q = 0; q < kHitWords; ++q) h[q] = q < hw ? hit[q] : 0u;
+  h[kHitWords] = tag;
+  h[kHitWords + 1] = 0u;
 }
 
 }  // namespace ccm

@@ -46,6 +46,9 @@ struct BwdLaunch {
   int* sched;                     // optional work counter (device int), zeroed by the launch
   int grid;        // one-warp blocks of the per-item kernel
   int pair_grid;   // one-warp blocks of the per-pair kernel
+  // if set: the per-pair kernel runs only when this device word is non-zero
+  // (the per-contact kernels did not run: see FlatPass::sched)
+  const int* only_if = nullptr;
 };
 
 // Resident one-warp blocks per SM of the reverse kernels that launch_backward

@@ -295,4 +295,33 @@ __device__ __forceinline__ void relative_pose(const float RS[9], const float tS[
   for (int i = 0; i < 3; ++i) tr[i] = RS[i] * d0 + RS[3 + i] * d1 + RS[6 + i] * d2;
 }
 
+// relative pose S <- F in double precision, computed by lanes 0..11 and
+// broadcast: Rr = R_S^T R_F, tr = R_S^T (t_F - t_S)
+__device__ __forceinline__ void rel_pose_f64(const float* pF, const float* pS, int lane,
+                                             float Rr[9], float tr[3]) {
+  float v = 0.f;
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) acc += (double)__ldg(pS + 3 * k + i) * (double)__ldg(pF + 3 * k + j);
+    v = (float)acc;
+  } else if (lane < 12) {
+    const int i = lane - 9;
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k)
+      acc += (double)__ldg(pS + 3 * k + i) * ((double)__ldg(pF + 9 + k) - (double)__ldg(pS + 9 + k));
+    v = (float)acc;
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Rr[q] = __shfl_sync(kFull, v, q);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) tr[q] = __shfl_sync(kFull, v, 9 + q);
+}
+
+__device__ __forceinline__ float3 xform(const float R[9], const float t[3], float4 v) {
+  return make_float3(fmaf(R[0], v.x, fmaf(R[1], v.y, fmaf(R[2], v.z, t[0]))),
+                     fmaf(R[3], v.x, fmaf(R[4], v.y, fmaf(R[5], v.z, t[1]))),
+                     fmaf(R[6], v.x, fmaf(R[7], v.y, fmaf(R[8], v.z, t[2]))));
+}
+
 }  // namespace ccm

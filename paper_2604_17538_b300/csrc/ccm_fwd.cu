@@ -18,33 +18,45 @@
 
 namespace ccm {
 
-// relative pose S <- F in double precision, computed by lanes 0..11 and
-// broadcast: Rr = R_S^T R_F, tr = R_S^T (t_F - t_S)
-__device__ __forceinline__ void rel_pose_f64(const float* pF, const float* pS, int lane,
-                                             float Rr[9], float tr[3]) {
-  float v = 0.f;
-  if (lane < 9) {
-    const int i = lane / 3, j = lane % 3;
-    double acc = 0.0;
-    for (int k = 0; k < 3; ++k) acc += (double)__ldg(pS + 3 * k + i) * (double)__ldg(pF + 3 * k + j);
-    v = (float)acc;
-  } else if (lane < 12) {
-    const int i = lane - 9;
-    double acc = 0.0;
-    for (int k = 0; k < 3; ++k)
-      acc += (double)__ldg(pS + 3 * k + i) * ((double)__ldg(pF + 9 + k) - (double)__ldg(pS + 9 + k));
-    v = (float)acc;
-  }
-#pragma unroll
-  for (int q = 0; q < 9; ++q) Rr[q] = __shfl_sync(kFull, v, q);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) tr[q] = __shfl_sync(kFull, v, 9 + q);
-}
+// Where the records of a list's contacts point: the global output row and
+// piece index of the F chunk's first group, and the first piece of body S.
+struct ChunkRef {
+  int64_t row;
+  int32_t fpiece;
+  int32_t spiece;
+};
 
-__device__ __forceinline__ float3 xform(const float R[9], const float t[3], float4 v) {
-  return make_float3(fmaf(R[0], v.x, fmaf(R[1], v.y, fmaf(R[2], v.z, t[0]))),
-                     fmaf(R[3], v.x, fmaf(R[4], v.y, fmaf(R[5], v.z, t[1]))),
-                     fmaf(R[6], v.x, fmaf(R[7], v.y, fmaf(R[8], v.z, t[2]))));
+// Appends this round's contacts of non-zero weight (lane's `contrib`: group
+// `key` of the F chunk, SDF piece `s_glob` (global index), piece-local
+// feature `feat` of kind `kind`, 0 vertex / 1 edge) to the contact list.  A
+// contact's rank among its group's contacts of its kind follows the lane
+// order, so it does not depend on where the round's records land.  Records
+// that do not fit set the overflow flag.
+__device__ __forceinline__ void append_contacts(const ContactList& cl, int* gcnt, bool contrib,
+                                                int key, int kind, int feat, int s_glob,
+                                                const ChunkRef& cr, int lane) {
+  const unsigned cm = __ballot_sync(kFull, contrib);
+  if (cm == 0u) return;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned same = __match_any_sync(kFull, contrib ? key : 0x10000 + lane) & cm;
+  int base = 0;
+  if (contrib) base = gcnt[2 * key + kind];
+  __syncwarp();
+  const int rank = __popc(same & lt);
+  if (contrib && rank == 0) gcnt[2 * key + kind] = base + __popc(same);
+  unsigned long long at = 0;
+  if (lane == 0) at = atomicAdd(cl.ctl + kCtlCursor, (unsigned long long)__popc(cm));
+  at = __shfl_sync(kFull, at, 0) + __popc(cm & lt);
+  if (contrib) {
+    const int seq = base + rank;
+    if ((long long)at < cl.cap && seq < (1 << kRankBits) && feat < (1 << kFeatBits)) {
+      const uint32_t w = ((uint32_t)kind << 31) | ((uint32_t)feat << kRankBits) | (uint32_t)seq;
+      cl.recs[at] = make_int4((int)(cr.row + key), s_glob, cr.fpiece + key, (int)w);
+    } else {
+      cl.ctl[kCtlOverflow] = 1ull;   // the reverse passes fall back to re-gating
+    }
+  }
+  __syncwarp();
 }
 
 struct FwdCounts {
@@ -55,7 +67,8 @@ struct FwdCounts {
 // are numbered by the exclusive prefixes sl.pv / sl.pe (totals TV, TE).
 template <bool kCount>
 __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE, int sc0,
-                         const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
+                         const KParams& kp, bool no_cull, int lane, FwdCounts& cnt,
+                         const ContactList& cl, const ChunkRef& cr) {
   // max-plane value of every (direction, vertex) item.  First one plane: the
   // plane attaining the max at the feature piece's centre (from the gate) is
   // far above d_max at the vertices on the far side of the piece, and its
@@ -142,26 +155,32 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
     PartT<float> c;
     part_zero(c);
     int key = 0xffff;
+    bool contrib = false;
+    int feat = 0, s_glob = 0;
     if (k < n_v) {
       const int t = sl.vlist[k];
       const int r = find_dir(sl.pv, nd, t);
       const int code = dsub[r];
       const int4 f = sl.fp[code >> 16];
       const int2 s = sl.sp[code & 0xffff];
-      const float4 x = sl.xs[f.x + t - sl.pv[r]];
+      feat = t - sl.pv[r];
+      const float4 x = sl.xs[f.x + feat];
       const float m = sl.m[t];
       const SdfGrad g = sdf_grad(sl.planes + s.x, s.y, x.x, x.y, x.z, m, kp);
       sl.phi[t] = g.phi;
       key = code >> 16;
+      s_glob = cr.spiece + sc0 + (code & 0xffff);
       if (no_cull || m < kp.d_max) {
         const float w = transition(g.phi, kp);
         const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
         part_from_contact(c, w, dc, v3(x.x, x.y, x.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
         mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
+        contrib = w > 0.f;
         if (kCount) cnt.con += w > 0.f;
       }
       if (kCount) cnt.eg += s.y;
     }
+    if (cl.recs) append_contacts(cl, sl.gcnt, contrib, key, 0, feat, s_glob, cr, lane);
     fold_t(c, key, sl.acc, lane);
   }
   __syncwarp();
@@ -171,13 +190,17 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
     PartT<float> c;
     part_zero(c);
     int key = 0xffff;
+    bool contrib = false;
+    int feat = 0, s_glob = 0;
     if (k < n_e) {
       const int t = sl.elist[k];
       const int r = find_dir(sl.pe, nd, t);
       const int code = dsub[r];
       const int4 f = sl.fp[code >> 16];
       const int2 s = sl.sp[code & 0xffff];
-      const uint32_t e = sl.edges[f.z + t - sl.pe[r]];
+      feat = t - sl.pe[r];
+      s_glob = cr.spiece + sc0 + (code & 0xffff);
+      const uint32_t e = sl.edges[f.z + feat];
       const int i0 = e & 0xffff, i1 = e >> 16;
       const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
       const EdgeContact ec = edge_contact(sl.planes + s.x, s.y, sl.xs[f.x + i0], sl.xs[f.x + i1],
@@ -187,12 +210,14 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       part_from_contact(c, w, dc, v3(ec.px, ec.py, ec.pz), v3(ec.gx, ec.gy, ec.gz), kp.c_blend);
       mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
       key = code >> 16;
+      contrib = w > 0.f;
       if (kCount) {
         cnt.con += w > 0.f;
         cnt.eg += s.y;
         cnt.ev += (unsigned long long)s.y * 2 * (kp.trace_iters > 0 ? kp.trace_iters - 1 : 0);
       }
     }
+    if (cl.recs) append_contacts(cl, sl.gcnt, contrib, key, 1, feat, s_glob, cr, lane);
     fold_t(c, key, sl.acc, lane);
   }
   __syncwarp();
@@ -202,7 +227,8 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
 // budgets and runs each.
 template <bool kCount>
 __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, const UnitShape& us,
-                           const KParams& kp, bool no_cull, int lane, FwdCounts& cnt) {
+                           const KParams& kp, bool no_cull, int lane, FwdCounts& cnt,
+                           const ContactList& cl, const ChunkRef& cr) {
   int start = 0;
   while (start < np) {
     const int r = start + lane;
@@ -231,7 +257,7 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, con
     }
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
-    run_list<kCount>(sl, dsub, nd, TV, TE, sc0, kp, no_cull, lane, cnt);
+    run_list<kCount>(sl, dsub, nd, TV, TE, sc0, kp, no_cull, lane, cnt, cl, cr);
     start += nd;
   }
 }
@@ -243,7 +269,8 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 int64_t n_items, const int64_t* __restrict__ dev_items,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, float* __restrict__ saved,
-                unsigned long long* __restrict__ counters, int* __restrict__ sched) {
+                unsigned long long* __restrict__ counters, int* __restrict__ sched,
+                ContactList cl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -297,7 +324,10 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         sl.fs[lane] = make_float4(c.x, c.y, c.z, p.sphere.w);
         part_zero(sl.acc[lane]);
         for (int q = 0; q < sl.hw; ++q) sl.hit[lane * sl.hw + q] = 0u;
+        sl.gcnt[2 * lane] = 0;
+        sl.gcnt[2 * lane + 1] = 0;
       }
+      const ChunkRef cr{row0 + fc0, F.p0 + fc0, S.p0};
       for (int i = lane; i < V; i += 64) {   // two loads in flight per lane
         const bool two = i + 32 < V;
         const float4 v0 = __ldg(g.verts + pv0 + i);
@@ -354,7 +384,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           const unsigned bal = __ballot_sync(kFull, live);
           const int nl = __popc(bal);
           if (np + nl > kPending) {
-            run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt);
+            run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
             np = 0;
           }
           if (live) {
@@ -365,7 +395,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           np += nl;
           __syncwarp();
         }
-        if (np > 0) run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt);
+        if (np > 0) run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
         sc0 = sc1;
       }
       __syncwarp();
@@ -376,7 +406,11 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         write_group(y + 8 * (row0 + fc0 + lane), acc, RS, tS, kp);
         if (saved)
           save_group(saved + (int64_t)kSavedFloats * (row0 + fc0 + lane), acc,
-                     sl.hit + lane * sl.hw, sl.hw);
+                     sl.hit + lane * sl.hw, sl.hw, cl.recs ? cl.tag : 0u);
+        if (cl.recs) {
+          cl.cnt_v[row0 + fc0 + lane] = sl.gcnt[2 * lane];
+          cl.cnt_e[row0 + fc0 + lane] = sl.gcnt[2 * lane + 1];
+        }
       }
       fc0 = fc1;
     }
@@ -402,12 +436,18 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   }
   const size_t smem = (size_t)L.us.warps * L.us.slice_bytes;
   const int threads = 32 * L.us.warps;
+  ContactList cl = L.cl;
+  if (!L.saved) cl.recs = nullptr;   // the list goes with the saved record
+  if (cl.recs) {
+    const cudaError_t e = cudaMemsetAsync(cl.ctl, 0, kCtlWords * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+  }
   if (L.counters)
     unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched);
+                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl);
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched);
+                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #include "../../include/ccm.h"
 #include "ccm_device.cuh"
 #include "ccm_unit.cuh"
+#include "ccm_clist.cuh"
 
 namespace ccm {
 
@@ -22,6 +23,7 @@ struct FwdLaunch {
   unsigned long long* counters;   // optional work counters (CCM_CNT_*)
   int* sched;                     // optional work counter (device int), zeroed by the launch
   int grid;
+  ContactList cl{};               // with `saved`: the contact list (cl.recs NULL: none)
 };
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);

@@ -11,6 +11,7 @@
 #include "ccm_device.cuh"
 #include "ccm_fwd.h"
 #include "ccm_bwd.h"
+#include "ccm_flat.h"
 
 namespace ccm {
 
@@ -77,6 +78,15 @@ struct Batch {
   int grid = 1;
   BwdOccupancy bwd_occ{};        // reverse kernels' resident blocks per SM
   HostStep* hs = nullptr;        // ccm_contacts_step_host state (first call)
+  // contact list of ccm_contacts_save and the per-contact reverse passes
+  // (ccm_flat.cu); flat_cap = 0: none
+  int64_t flat_cap = 0;
+  uint32_t list_tag = 0;         // tag of the last contact list (0: none yet)
+  DevBuf d_row_pair;             // [G] pair << 1 | side
+  DevBuf d_fctl, d_fcnt, d_foff, d_frecs, d_fsorted;
+  DevBuf d_fpass[2][5];          // [float, Dual][cval, force, coef, oterm, sched]
+  ContactList contact_list() const;
+  FlatPass flat_pass(bool dual) const;
   void release();
 };
 
@@ -115,6 +125,9 @@ std::vector<int32_t> items_by_cost(const std::vector<int64_t>& cost);
 ccm_status build_batch(Context* c, int64_t n, const ccm_geom* A, const ccm_geom* B, Batch* bt);
 void default_tuning(ccm_tuning* t);
 ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t);
+// (Re)allocates the contact list and the per-contact passes' scratch for the
+// batch's tuning (flat_records), or releases them.
+ccm_status setup_flat(Context* c, Batch* bt);
 ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,
                        float* y, float* saved, unsigned long long* counters, cudaStream_t stream);
 ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, const ccm_params* prm,

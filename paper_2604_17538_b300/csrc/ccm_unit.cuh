@@ -63,6 +63,8 @@ struct UnitSlice {
   uint8_t* need;      // [item_v]
   uint16_t* am;       // [item_v] a plane attaining the max-plane value (until the
                       // edge cull, in phi's space)
+  int* gcnt;          // [2 groups] contacts of non-zero weight per group (vertex,
+                      // edge) found so far, for the contact list
 };
 
 // Rounding allowance of the edge cull's plane bound (coordinates are O(1) in
@@ -87,6 +89,7 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += align16i(2 * u.item_v);               // vlist
   b += align16i(2 * u.item_e);               // elist
   b += align16i(u.item_v);                   // need
+  b += align16i(8 * u.groups);               // gcnt
   return b;
 }
 
@@ -111,7 +114,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.phi = reinterpret_cast<float*>(p);               p += align16i(4 * u.item_v);
   s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
   s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
-  s.need = reinterpret_cast<uint8_t*>(p);
+  s.need = reinterpret_cast<uint8_t*>(p);             p += align16i(u.item_v);
+  s.gcnt = reinterpret_cast<int*>(p);
   s.am = reinterpret_cast<uint16_t*>(s.phi);
   return s;
 }

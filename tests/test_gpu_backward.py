@@ -106,7 +106,7 @@ def test_gradient_hvp_jvp_match_oracle(oracle_lib, ctx, cases, name):
     rec = saved.cpu().numpy()
     yh = y.cpu().numpy()
     assert np.array_equal(rec[:, 1] > 0, yh[:, 1] > 0)
-    hits = rec[:, 18:].copy().view(np.uint32)
+    hits = rec[:, 18:26].copy().view(np.uint32)
     assert np.all((hits != 0).any(1) == (yh[:, 1] > 0))
     # counted reverse passes give the same results, and the saved record
     # restricts them to fewer directions than a full re-gating
@@ -124,8 +124,12 @@ def test_gradient_hvp_jvp_match_oracle(oracle_lib, ctx, cases, name):
         got_saved = r_saved[0] if direction is None else r_saved[1]
         assert torch.equal(got_full, ref_full) and torch.equal(got_saved, ref_saved)
         cf, cs = c_full.cpu().numpy(), c_saved.cpu().numpy()
-        assert cf[3] > 0 and cs[3] == 0        # no piece-pair gate with the record
-        assert 0 < cs[1] <= cf[1] and 0 < cs[4] <= cf[4] and cs[6] > 0
+        # with the record the passes run per contact from the forward's
+        # contact list: no piece-pair gate, contacts with a live group among
+        # those evaluated, and fewer plane evaluations than a full re-gating
+        assert cf[3] > 0 and cs[3] == 0
+        assert 0 < cs[1] <= cs[0] and cs[4] > 0 and cs[6] > 0
+        assert cs[2:].sum() < cf[2:].sum()
     batch.close()
 
 
