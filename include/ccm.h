@@ -77,6 +77,17 @@ typedef enum {
 
 /* Flags of ccm_params.flags */
 #define CCM_FLAG_NO_CULL 1u   /* evaluate every feature (culls are exact; for tests) */
+/* Forward variants (ccm_contacts only; the reverse passes and ccm_contacts_save
+ * reject them):
+ *   BODY_UNION: the other body's SDF is the smooth union of its pieces' SDFs,
+ *     phi_S = -tau_sdf log sum_s exp(-phi_s / tau_sdf) (Sec. 3.1, Eq.
+ *     soft_union), and every vertex and edge of a group's piece gives one
+ *     contact against the whole body instead of one per piece;
+ *   PROJECT: every contact point is moved onto the SDF's isosurface,
+ *     p - phi(p) grad phi(p) (Sec. 4.1), after its depth and normal were
+ *     taken at p. */
+#define CCM_FLAG_BODY_UNION 2u
+#define CCM_FLAG_PROJECT 4u
 
 /* Method constants.  The paper fixes none of these values (Sec. 2-4). */
 typedef struct {

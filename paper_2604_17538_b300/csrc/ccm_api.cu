@@ -509,6 +509,8 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
+  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT))
+    return fail(CCM_ERR_INVALID, "the body-union and projection variants are forward only");
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
@@ -698,6 +700,7 @@ ContactList Batch::contact_list() const {
   cl.cnt_e = cl.cnt_v + G;
   cl.off_v = static_cast<int32_t*>(d_foff.ptr);
   cl.off_e = cl.off_v + (G + 1);
+  cl.tile_sum = static_cast<long long*>(d_ftiles.ptr);
   return cl;
 }
 
@@ -719,7 +722,8 @@ ccm_status setup_flat(Context* c, Batch* bt) {
     cap = fr > 0 ? fr * bt->G
                  : std::min<int64_t>(std::max<int64_t>(16 * bt->G, 65536), (int64_t)1 << 24);
   if (cap == bt->flat_cap) return CCM_OK;
-  for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted})
+  for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted,
+                   &bt->d_ftiles})
     b->release();
   for (auto& pass : bt->d_fpass)
     for (DevBuf& b : pass) b.release();
@@ -739,7 +743,9 @@ ccm_status setup_flat(Context* c, Batch* bt) {
       (s = alloc(bt->d_fcnt, 2 * G * sizeof(int32_t), "contact counts")) != CCM_OK ||
       (s = alloc(bt->d_foff, 2 * (G + 1) * sizeof(int32_t), "contact offsets")) != CCM_OK ||
       (s = alloc(bt->d_frecs, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK ||
-      (s = alloc(bt->d_fsorted, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK)
+      (s = alloc(bt->d_fsorted, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK ||
+      (s = alloc(bt->d_ftiles, 2 * (size_t)flat_scan_tiles(bt->G) * sizeof(long long),
+                 "contact list scan")) != CCM_OK)
     return s;
   for (int d = 0; d < 2; ++d) {
     size_t sz[4];
@@ -858,6 +864,8 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
+  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT))
+    return fail(CCM_ERR_INVALID, "the body-union and projection variants are forward only");
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
@@ -940,7 +948,7 @@ void Batch::release() {
   d_sched.release();
   d_part.release();
   d_row_pair.release();
-  for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted}) b->release();
+  for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted, &d_ftiles}) b->release();
   for (auto& pass : d_fpass)
     for (DevBuf& b : pass) b.release();
   flat_cap = 0;
@@ -955,6 +963,24 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  if ((kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT)) && (saved || counters))
+    return fail(CCM_ERR_INVALID,
+                "the body-union and projection variants keep no record and count no work");
+  if (kp.flags & CCM_FLAG_BODY_UNION) {
+    UnionLaunch U;
+    U.g = b->ctx->dev_geom();
+    U.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+    U.row_pair = static_cast<const int32_t*>(b->d_row_pair.ptr);
+    U.G = b->G;
+    U.pose_a = pose_a;
+    U.pose_b = pose_b;
+    U.kp = kp;
+    U.y = y;
+    U.n_sm = b->ctx->n_sm;
+    const cudaError_t e = launch_union_forward(U, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "body-union forward launch");
+    return CCM_OK;
+  }
   FwdLaunch L;
   L.g = b->ctx->dev_geom();
   L.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);

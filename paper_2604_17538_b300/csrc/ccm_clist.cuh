@@ -40,6 +40,7 @@ struct ContactList {
   int32_t* cnt_e;           // [G] edge contacts per group
   int32_t* off_v;           // [G + 1] exclusive prefix of cnt_v
   int32_t* off_e;           // [G + 1] exclusive prefix of cnt_e
+  long long* tile_sum;      // [2 tiles] scratch of the scan (flat_scan_tiles)
 };
 
 enum { kCtlCursor = 0, kCtlOverflow = 1, kCtlNV = 2, kCtlNE = 3, kCtlTag = 4, kCtlWords = 8 };

@@ -28,65 +28,102 @@ namespace ccm {
 // ---------------------------------------------------------------------------
 // fixed order of the list
 // ---------------------------------------------------------------------------
-// Exclusive prefixes of the per-group counts (one block, tiles of 1024 x 4
-// groups, a running carry), and the totals NV, NE.
-__global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_t G) {
-  __shared__ long long wv[32], we[32];
-  __shared__ long long carry[2];
+// Exclusive prefixes of the per-group counts in two kernels over tiles of
+// 4096 groups (1024 threads x 4): the tile totals, then per tile the sum of
+// the totals before it plus the tile's own block scan.  The last tile writes
+// the totals NV, NE and the list's tag.
+constexpr int kScanTile = 4096;
+
+__device__ __forceinline__ void block_scan2(long long& v, long long& e, long long* wv,
+                                            long long* we) {
+  // inclusive block-wide scan of (v, e) over 1024 threads
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  if (t == 0) { carry[0] = 0; carry[1] = 0; }
-  __syncthreads();
-  for (int64_t base = 0; base < G; base += 4096) {
-    int cv[4], ce[4];
-    long long sv = 0, se = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + 4 * t + q;
-      cv[q] = i < G ? cl.cnt_v[i] : 0;
-      ce[q] = i < G ? cl.cnt_e[i] : 0;
-      sv += cv[q];
-      se += ce[q];
-    }
-    long long iv = sv, ie = se;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long a = __shfl_up_sync(kFull, v, o), b = __shfl_up_sync(kFull, e, o);
+    if (lane >= o) { v += a; e += b; }
+  }
+  if (lane == 31) { wv[w] = v; we[w] = e; }
+  __syncthreads();
+  if (w == 0) {
+    long long x = wv[lane], y = we[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const long long a = __shfl_up_sync(kFull, iv, o), b = __shfl_up_sync(kFull, ie, o);
-      if (lane >= o) { iv += a; ie += b; }
+      const long long a = __shfl_up_sync(kFull, x, o), b = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) { x += a; y += b; }
     }
-    if (lane == 31) { wv[w] = iv; we[w] = ie; }
-    __syncthreads();
-    if (w == 0) {
-      long long x = wv[lane], y = we[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long a = __shfl_up_sync(kFull, x, o), b = __shfl_up_sync(kFull, y, o);
-        if (lane >= o) { x += a; y += b; }
-      }
-      wv[lane] = x;
-      we[lane] = y;
-    }
-    __syncthreads();
-    long long pv = carry[0] + iv - sv + (w > 0 ? wv[w - 1] : 0);
-    long long pe = carry[1] + ie - se + (w > 0 ? we[w - 1] : 0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + 4 * t + q;
-      if (i < G) {
-        cl.off_v[i] = (int32_t)pv;
-        cl.off_e[i] = (int32_t)pe;
-      }
-      pv += cv[q];
-      pe += ce[q];
-    }
-    __syncthreads();
-    if (t == 0) { carry[0] += wv[31]; carry[1] += we[31]; }
-    __syncthreads();
+    wv[lane] = x;
+    we[lane] = y;
   }
+  __syncthreads();
+  if (w > 0) { v += wv[w - 1]; e += we[w - 1]; }
+}
+
+__global__ void __launch_bounds__(1024) clist_tile_sum_kernel(ContactList cl, int64_t G,
+                                                              long long* tile_sum) {
+  __shared__ long long wv[32], we[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  long long sv = 0, se = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (base + q < G) { sv += cl.cnt_v[base + q]; se += cl.cnt_e[base + q]; }
+  block_scan2(sv, se, wv, we);
+  if (threadIdx.x == 1023) {
+    tile_sum[2 * blockIdx.x] = sv;
+    tile_sum[2 * blockIdx.x + 1] = se;
+  }
+}
+
+__global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_t G,
+                                                          const long long* tile_sum) {
+  __shared__ long long wv[32], we[32], pre[2];
+  const int t = threadIdx.x;
+  // totals of the tiles before this one
+  long long pv = 0, pe = 0;
+  for (int b = t; b < (int)blockIdx.x; b += 1024) { pv += tile_sum[2 * b]; pe += tile_sum[2 * b + 1]; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pv += __shfl_xor_sync(kFull, pv, o);
+    pe += __shfl_xor_sync(kFull, pe, o);
+  }
+  if ((t & 31) == 0) { wv[t >> 5] = pv; we[t >> 5] = pe; }
+  __syncthreads();
   if (t == 0) {
-    cl.off_v[G] = (int32_t)carry[0];
-    cl.off_e[G] = (int32_t)carry[1];
-    cl.ctl[kCtlNV] = (unsigned long long)carry[0];
-    cl.ctl[kCtlNE] = (unsigned long long)carry[1];
+    long long a = 0, b = 0;
+    for (int w = 0; w < 32; ++w) { a += wv[w]; b += we[w]; }
+    pre[0] = a;
+    pre[1] = b;
+  }
+  __syncthreads();
+  const long long p0v = pre[0], p0e = pre[1];
+  __syncthreads();   // wv / we are reused by the scan
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * t;
+  int cv[4], ce[4];
+  long long sv = 0, se = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    cv[q] = base + q < G ? cl.cnt_v[base + q] : 0;
+    ce[q] = base + q < G ? cl.cnt_e[base + q] : 0;
+    sv += cv[q];
+    se += ce[q];
+  }
+  long long iv = sv, ie = se;
+  block_scan2(iv, ie, wv, we);
+  long long ov = p0v + iv - sv, oe = p0e + ie - se;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (base + q < G) {
+      cl.off_v[base + q] = (int32_t)ov;
+      cl.off_e[base + q] = (int32_t)oe;
+    }
+    ov += cv[q];
+    oe += ce[q];
+  }
+  if (blockIdx.x == gridDim.x - 1 && t == 1023) {
+    cl.off_v[G] = (int32_t)(p0v + iv);
+    cl.off_e[G] = (int32_t)(p0e + ie);
+    cl.ctl[kCtlNV] = (unsigned long long)(p0v + iv);
+    cl.ctl[kCtlNE] = (unsigned long long)(p0e + ie);
     cl.ctl[kCtlTag] = cl.tag;
   }
 }
@@ -109,10 +146,15 @@ __global__ void clist_scatter_kernel(ContactList cl) {
   }
 }
 
+int64_t flat_scan_tiles(int64_t G) { return std::max<int64_t>(1, (G + kScanTile - 1) / kScanTile); }
+
 cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream) {
-  clist_scan_kernel<<<1, 1024, 0, stream>>>(cl, G);
+  const int64_t tiles = flat_scan_tiles(G);
+  clist_tile_sum_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  clist_scan_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   clist_scatter_kernel<<<4 * n_sm, 256, 0, stream>>>(cl);
   return cudaGetLastError();
 }
@@ -303,10 +345,19 @@ __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
   T* ot = static_cast<T*>(L.fp.oterm);
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.G;
        g += (int64_t)gridDim.x * blockDim.x) {
+    T* o = ot + 6 * g;
+    const int64_t v0 = L.cl.off_v[g], v1 = L.cl.off_v[g + 1];
+    const int64_t e0 = L.cl.off_e[g], e1 = L.cl.off_e[g + 1];
+    if (v0 == v1 && e0 == e1) {   // no contact: no adjoint, zero output terms and tangents
+      for (int q = 0; q < 6; ++q) o[q] = T(0.f);
+      if (L.jvp)
+        for (int q = 0; q < 8; ++q) L.jvp[8 * g + q] = 0.f;
+      continue;
+    }
     PartT<T> acc;
     part_zero(acc);
-    fold_range(cval, L.cl.off_v[g], L.cl.off_v[g + 1], L.kp.c_blend, acc);
-    fold_range(cval, NV + L.cl.off_e[g], NV + L.cl.off_e[g + 1], L.kp.c_blend, acc);
+    fold_range(cval, v0, v1, L.kp.c_blend, acc);
+    fold_range(cval, NV + e0, NV + e1, L.kp.c_blend, acc);
     const int rp = L.row_pair[g];
     const int64_t pair = rp >> 1;
     const int side = rp & 1;
@@ -317,7 +368,6 @@ __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
     V3T<T> ow, ov;
     form_coef(acc, L.ybar + 8 * g, PS, L.jvp ? L.jvp + 8 * g : nullptr, cf, ow, ov);
     coef[g] = cf;
-    T* o = ot + 6 * g;
     o[0] = ow.x; o[1] = ow.y; o[2] = ow.z;
     o[3] = ov.x; o[4] = ov.y; o[5] = ov.z;
   }

@@ -42,6 +42,8 @@ struct FlatLaunch {
 // Bytes of one pass's scratch (FlatPass) for capacity cap and G groups.
 void flat_pass_bytes(bool dual, int64_t cap, int64_t G, size_t* cval, size_t* force,
                      size_t* coef, size_t* oterm);
+// Tiles of the scan of G group counts (ContactList::tile_sum holds 2 per tile).
+int64_t flat_scan_tiles(int64_t G);
 // After a forward that filled cl: scan of the group counts and the scatter
 // of the records into their fixed order.
 cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream);

@@ -69,6 +69,7 @@ template <bool kCount>
 __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE, int sc0,
                          const KParams& kp, bool no_cull, int lane, FwdCounts& cnt,
                          const ContactList& cl, const ChunkRef& cr) {
+  const bool project = (kp.flags & CCM_FLAG_PROJECT) != 0u;
   // max-plane value of every (direction, vertex) item.  First one plane: the
   // plane attaining the max at the feature piece's centre (from the gate) is
   // far above d_max at the vertices on the far side of the piece, and its
@@ -173,7 +174,10 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       if (no_cull || m < kp.d_max) {
         const float w = transition(g.phi, kp);
         const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
-        part_from_contact(c, w, dc, v3(x.x, x.y, x.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
+        float3 p = make_float3(x.x, x.y, x.z);
+        if (project) p = make_float3(fmaf(-g.phi, g.gx, p.x), fmaf(-g.phi, g.gy, p.y),
+                                     fmaf(-g.phi, g.gz, p.z));   // Sec. 4.1 projection
+        part_from_contact(c, w, dc, v3(p.x, p.y, p.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
         mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
         contrib = w > 0.f;
         if (kCount) cnt.con += w > 0.f;
@@ -207,7 +211,10 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
                                           sl.m[t0v], sl.m[t1v], sl.phi[t0v], sl.phi[t1v], kp);
       const float w = transition(ec.phi, kp);
       const float dc = fmaf(w, ec.phi - kp.d_max, kp.d_max);
-      part_from_contact(c, w, dc, v3(ec.px, ec.py, ec.pz), v3(ec.gx, ec.gy, ec.gz), kp.c_blend);
+      float3 p = make_float3(ec.px, ec.py, ec.pz);
+      if (project) p = make_float3(fmaf(-ec.phi, ec.gx, p.x), fmaf(-ec.phi, ec.gy, p.y),
+                                   fmaf(-ec.phi, ec.gz, p.z));   // Sec. 4.1 projection
+      part_from_contact(c, w, dc, v3(p.x, p.y, p.z), v3(ec.gx, ec.gy, ec.gz), kp.c_blend);
       mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
       key = code >> 16;
       contrib = w > 0.f;

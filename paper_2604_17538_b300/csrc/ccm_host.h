@@ -12,6 +12,7 @@
 #include "ccm_fwd.h"
 #include "ccm_bwd.h"
 #include "ccm_flat.h"
+#include "ccm_union.h"
 
 namespace ccm {
 
@@ -83,7 +84,7 @@ struct Batch {
   int64_t flat_cap = 0;
   uint32_t list_tag = 0;         // tag of the last contact list (0: none yet)
   DevBuf d_row_pair;             // [G] pair << 1 | side
-  DevBuf d_fctl, d_fcnt, d_foff, d_frecs, d_fsorted;
+  DevBuf d_fctl, d_fcnt, d_foff, d_frecs, d_fsorted, d_ftiles;
   DevBuf d_fpass[2][5];          // [float, Dual][cval, force, coef, oterm, sched]
   ContactList contact_list() const;
   FlatPass flat_pass(bool dual) const;

@@ -16,6 +16,8 @@
 // phi_S is 1-Lipschitz (its gradient is a convex mix of unit-bounded ones),
 // so an edge whose corners satisfy (phi_a + phi_b - L) / 2 >= d_max has no
 // point below d_max.
+#include <algorithm>
+
 #include "ccm_narrow.cuh"
 #include "ccm_union.h"
 
@@ -106,7 +108,7 @@ union_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __
         if (k < fp.nv) {            // V-SDF: the vertex is the contact point
           const float3 x = xform(Rr, tr, g.verts[fp.v0 + k]);
           px = x.x; py = x.y; pz = x.z;
-          live = union_lower_bound(g, S, px, py, pz, kp) < kp.d_max;
+          live = union_lower_bound(g, S, px, py, pz, kp) - 1e-5f < kp.d_max;
           if (live) phi = union_sdf<true>(g, S, px, py, pz, kp, gr);
         } else {                    // E-SDF: sphere trace from both corners
           const uint32_t e = g.edges[fp.e0 + (k - fp.nv)];
