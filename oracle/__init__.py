@@ -7,6 +7,15 @@ mode dual numbers for exact derivatives); this file only builds it and
 marshals numpy arrays through ctypes.
 
 Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
+  * ``body_sdf`` / FLAG_BODY_UNION -- LSE bounds against the pieces' SDFs,
+                          finite differences, far-apart and single-piece limits,
+                          rigid-motion invariance and body-swap symmetry.
+  * FLAG_PROJECT       -- a single half-space and the stacked-cube face: the
+                          projected points lie on the plane.
+  * ``spline_u`` / ``spline_sdf`` / FLAG_SPLINE -- basis partition of unity
+                          and support, interpolation at the nodes, exact
+                          reproduction of linear fields, convergence to a
+                          sphere's SDF, and the stacked-cube closed form.
   * ``sdf``            -- brute-force polytope distance, LSE bounds, tau -> 0 limit.
   * ``edge_point``     -- Cyrus-Beck chord midpoint (many iterations, small tau),
                           inside-edge midpoint, one-step convergence on a face.
@@ -50,7 +59,9 @@ class Params(C.Structure):
 class _Geom(C.Structure):
     _fields_ = [("body_piece_off", C.c_void_p), ("piece_v_off", C.c_void_p),
                 ("piece_f_off", C.c_void_p), ("piece_e_off", C.c_void_p),
-                ("verts", C.c_void_p), ("planes", C.c_void_p), ("edges", C.c_void_p)]
+                ("verts", C.c_void_p), ("planes", C.c_void_p), ("edges", C.c_void_p),
+                ("spline_grid", C.c_void_p), ("spline_dims", C.c_void_p),
+                ("spline_coef", C.c_void_p)]
 
 
 DEFAULTS = dict(tau_sdf=5e-3, tau_trace=5e-3, tau_clip=5e-3, tau_blend=5e-3,
@@ -61,6 +72,9 @@ DEFAULTS = dict(tau_sdf=5e-3, tau_trace=5e-3, tau_clip=5e-3, tau_blend=5e-3,
 # isosurface (Sec. 4.1)
 FLAG_BODY_UNION = 2
 FLAG_PROJECT = 4
+# every SDF piece as its tricubic spline SDF with normal splines (Sec. 3.2);
+# needs a geometry with splines (scenes.attach_splines)
+FLAG_SPLINE = 8
 
 _lib = None
 
@@ -89,6 +103,10 @@ def lib():
         _lib.ccmo_pair_contacts.restype = I64
         _lib.ccmo_body_sdf.argtypes = [P, I64, P, D, P]
         _lib.ccmo_body_sdf.restype = D
+        _lib.ccmo_spline_u.argtypes = [D]
+        _lib.ccmo_spline_u.restype = D
+        _lib.ccmo_spline_sdf.argtypes = [P, I64, P, P]
+        _lib.ccmo_spline_sdf.restype = D
     return _lib
 
 
@@ -115,7 +133,13 @@ class _Packed:
                      np.ascontiguousarray(geom.verts, np.float64),
                      np.ascontiguousarray(geom.planes, np.float64),
                      np.ascontiguousarray(geom.edges, np.int32)]
-        self.s = _Geom(*[a.ctypes.data for a in self.arrs])
+        sp = getattr(geom, "splines", None)
+        if sp is not None:
+            self.arrs += [np.ascontiguousarray(sp.grid, np.float64),
+                          np.ascontiguousarray(sp.dims, np.int64),
+                          np.ascontiguousarray(sp.coef, np.float64)]
+        ptrs = [a.ctypes.data for a in self.arrs]
+        self.s = _Geom(*(ptrs + [None] * (10 - len(ptrs))))
 
     def ref(self):
         return C.byref(self.s)
@@ -206,6 +230,21 @@ def body_sdf(geom, body, x, tau):
     grad = np.zeros(3)
     phi = lib().ccmo_body_sdf(g.ref(), int(body), _ptr(x), float(tau), _ptr(grad))
     return phi, grad
+
+
+def spline_u(t):
+    """The paper's cubic spline basis u(t) (Sec. 3.2)."""
+    return lib().ccmo_spline_u(float(t))
+
+
+def spline_sdf(geom, piece, x):
+    """(phi, n) of piece ``piece``'s tricubic spline SDF and normal splines at
+    x (body frame; Sec. 3.2); ``geom`` must carry splines."""
+    g = _Packed(geom)
+    x = np.ascontiguousarray(x, np.float64).reshape(3)
+    n = np.zeros(3)
+    phi = lib().ccmo_spline_sdf(g.ref(), int(piece), _ptr(x), _ptr(n))
+    return phi, n
 
 
 def transition(d, d_max=0.01, eps=0.01):

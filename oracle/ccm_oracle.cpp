@@ -35,8 +35,14 @@
 //     softness tau_sdf, and every feature of a group gives one contact
 //     against the whole body instead of one per piece;
 //   * kFlagProject: every contact point is moved onto the SDF's isosurface
-//     (Sec. 4.1), proj(p) = p - phi(p) n(p) with n = grad phi, after its
-//     depth and normal were taken at p.
+//     (Sec. 4.1), proj(p) = p - phi(p) n(p) with n the contact normal (grad
+//     phi, or the normal spline), after its depth and normal were taken at p;
+//   * kFlagSpline: every SDF piece is a tricubic spline (Sec. 3.2): the SDF
+//     and the three normal components are each a tensor-product cubic spline
+//     on the piece's voxel grid, s(x) = sum c_{kx,ky,kz} u(.) u(.) u(.) with
+//     the paper's basis u (support [-2, 2]); the contact normal is the normal
+//     spline, not the SDF's gradient.  Outside the grid box the SDF continues
+//     as the spline at the nearest box point plus the distance to the box.
 //
 // Derivatives: the same templated code runs on forward-mode dual numbers.
 // Dual<double,12> gives the exact gradient with respect to the 12 twist
@@ -215,6 +221,13 @@ struct ccmo_geom {
   const double* verts;   // [V,3]
   const double* planes;  // [F,4]
   const int32_t* edges;  // [E,2]
+  // tricubic spline SDFs (Sec. 3.2), or NULL: per piece the grid origin and
+  // voxel size (ox, oy, oz, h), the voxel counts (nx, ny, nz) and the offset
+  // of its coefficients, [(nx+3)(ny+3)(nz+3), 4] rows (phi, n_x, n_y, n_z)
+  // with the z index fastest
+  const double* spline_grid;    // [P,4]
+  const int64_t* spline_dims;   // [P,4]: nx, ny, nz, first coefficient row
+  const double* spline_coef;    // [rows,4]
 };
 }
 
@@ -294,6 +307,67 @@ struct PieceSdf {
 // --------------------------------------------------------------------------
 constexpr int32_t kFlagBodyUnion = 2;
 constexpr int32_t kFlagProject = 4;
+constexpr int32_t kFlagSpline = 8;
+
+// --------------------------------------------------------------------------
+// Sec. 3.2: cubic spline basis u(t) = 4 - 6|t|^2 + 3|t|^3 on |t| <= 1,
+// (2 - |t|)^3 on 1 <= |t| <= 2, 0 beyond, and the tricubic spline of one
+// piece.  Coefficient k of an axis sits at grid node k - 1 (k = 0..N+2), so
+// the nodes i = 0..N and one extra coefficient beyond each end carry the
+// N + 3 basis functions of N voxels.
+// --------------------------------------------------------------------------
+template <class T> T spline_u(const T& t) {
+  const T a = val(t) < 0.0 ? -t : t;
+  if (val(a) <= 1.0) return 4.0 - 6.0 * a * a + 3.0 * a * a * a;
+  if (val(a) <= 2.0) { const T b = 2.0 - a; return b * b * b; }
+  return T(0.0);
+}
+
+struct SplineSdf {
+  const double* grid;   // ox, oy, oz, h
+  const int64_t* dims;  // nx, ny, nz, first row
+  const double* coef;   // [rows, 4]
+  // value of channel ch at t (grid units), t inside [0, N] per axis
+  template <class T> T channel(const T t[3], int ch) const {
+    int64_t i0[3];
+    for (int a = 0; a < 3; ++a) {
+      i0[a] = (int64_t)std::floor(val(t[a]));
+      if (i0[a] > dims[a] - 1) i0[a] = dims[a] - 1;
+      if (i0[a] < 0) i0[a] = 0;
+    }
+    const int64_t ny = dims[1] + 3, nz = dims[2] + 3;
+    T sum(0.0);
+    // the 64 coefficients whose basis functions reach t: k = i0 .. i0 + 3
+    for (int a = 0; a < 4; ++a) {
+      const T ua = spline_u(t[0] - (double)(i0[0] + a - 1));
+      for (int b = 0; b < 4; ++b) {
+        const T ub = spline_u(t[1] - (double)(i0[1] + b - 1));
+        for (int c = 0; c < 4; ++c) {
+          const T uc = spline_u(t[2] - (double)(i0[2] + c - 1));
+          const int64_t row = dims[3] + ((i0[0] + a) * ny + (i0[1] + b)) * nz + (i0[2] + c);
+          sum = sum + coef[4 * row + ch] * (ua * ub * uc);
+        }
+      }
+    }
+    return sum;
+  }
+  template <class T> T operator()(const V3<T>& x, V3<T>* normal) const {
+    // grid units, clamped to the grid box; the distance to the box is added
+    const T xs[3] = {x.x, x.y, x.z};
+    T t[3], out2(0.0);
+    for (int a = 0; a < 3; ++a) {
+      const T u = (xs[a] - grid[a]) / grid[3];
+      const double hi = (double)dims[a];
+      if (val(u) < 0.0) { out2 = out2 + u * u; t[a] = T(0.0); }
+      else if (val(u) > hi) { out2 = out2 + (u - hi) * (u - hi); t[a] = T(hi); }
+      else t[a] = u;
+    }
+    T phi = channel(t, 0);
+    if (val(out2) > 0.0) phi = phi + grid[3] * sqrt(out2);
+    if (normal) *normal = V3<T>{channel(t, 1), channel(t, 2), channel(t, 3)};
+    return phi;
+  }
+};
 
 struct BodyUnionSdf {
   const ccmo_geom* G;
@@ -471,6 +545,16 @@ void group_contacts(const ccmo_geom& G, int64_t fp, const Pose<T>& PF, int64_t b
       const int32_t* e = G.edges + 2 * (e0 + j);
       cs.push_back(edge_contact(sdf, x[e[0]], x[e[1]], prm));
     }
+  } else if (prm.flags & kFlagSpline) {
+    // every SDF piece as its tricubic spline (Sec. 3.2)
+    for (int64_t s = G.body_piece_off[bodyS]; s < G.body_piece_off[bodyS + 1]; ++s) {
+      const SplineSdf sdf{G.spline_grid + 4 * s, G.spline_dims + 4 * s, G.spline_coef};
+      for (int64_t i = 0; i < nv; ++i) cs.push_back(vertex_contact(sdf, x[i], prm));
+      for (int64_t j = 0; j < ne; ++j) {
+        const int32_t* e = G.edges + 2 * (e0 + j);
+        cs.push_back(edge_contact(sdf, x[e[0]], x[e[1]], prm));
+      }
+    }
   } else {
     for (int64_t s = G.body_piece_off[bodyS]; s < G.body_piece_off[bodyS + 1]; ++s) {
       const PieceSdf sdf{G.planes + 4 * G.piece_f_off[s],
@@ -646,6 +730,18 @@ double ccmo_body_sdf(const ccmo_geom* G, int64_t body, const double* x, double t
   V3<double> g;
   const double phi = sdf(V3<double>{x[0], x[1], x[2]}, &g);
   if (grad) { grad[0] = g.x; grad[1] = g.y; grad[2] = g.z; }
+  return phi;
+}
+
+// the paper's 1-D cubic basis u(t) (Sec. 3.2)
+double ccmo_spline_u(double t) { return spline_u<double>(t); }
+
+// tricubic spline SDF of piece `piece` at x (body frame) and its normal spline
+double ccmo_spline_sdf(const ccmo_geom* G, int64_t piece, const double* x, double* normal) {
+  const SplineSdf sdf{G->spline_grid + 4 * piece, G->spline_dims + 4 * piece, G->spline_coef};
+  V3<double> n;
+  const double phi = sdf(V3<double>{x[0], x[1], x[2]}, &n);
+  if (normal) { normal[0] = n.x; normal[1] = n.y; normal[2] = n.z; }
   return phi;
 }
 

@@ -30,7 +30,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "Geometry", "Scene", "unit_cube_piece", "hull_piece", "random_rotations",
+    "Geometry", "Scene", "SplineSet", "attach_splines", "fit_spline", "polytope_sdf", "unit_cube_piece", "hull_piece", "random_rotations",
     "geometry_from_bodies", "cube_pair_scene", "hull_env_scene", "uneven_scene",
     "log_uniform_int", "box_penetration_depth",
 ]
@@ -54,6 +54,7 @@ class Geometry:
     verts: np.ndarray           # float32 [V, 3]
     planes: np.ndarray          # float32 [F, 4]  (nx, ny, nz, h)
     edges: np.ndarray           # int32   [E, 2]  piece-local vertex indices
+    splines: "SplineSet | None" = None   # optional tricubic spline SDF per piece
 
     @property
     def n_bodies(self) -> int:
@@ -79,6 +80,21 @@ class Geometry:
     def subset(self, bodies) -> "Geometry":
         """Geometry holding only ``bodies`` (in that order)."""
         return geometry_from_bodies([self.body_pieces(int(b)) for b in bodies])
+
+
+@dataclass
+class SplineSet:
+    """Tricubic spline SDFs of a geometry's pieces (Sec. 3.2 representation).
+
+    Piece p has a voxel grid with origin ``grid[p, :3]``, voxel size
+    ``grid[p, 3]`` and ``dims[p, :3]`` voxels per axis; its coefficients are
+    the rows ``coef[dims[p, 3] : dims[p, 3] + (nx+3)(ny+3)(nz+3)]`` in
+    (x, y, z) order with z fastest, each row (phi, n_x, n_y, n_z): the SDF
+    spline and the three normal splines.  Coefficient k of an axis belongs to
+    grid node k - 1."""
+    grid: np.ndarray            # float32 [P, 4]
+    dims: np.ndarray            # int64   [P, 4]
+    coef: np.ndarray            # float32 [rows, 4]
 
 
 @dataclass
@@ -193,6 +209,136 @@ def hull_piece(points):
     edges = pairs[np.sort(first)]
     edges = edges[np.lexsort((edges[:, 1], edges[:, 0]))].astype(np.int32)
     return verts.astype(np.float32), np.asarray(planes, np.float32), edges
+
+
+# ----------------------------------------------------------------------------
+# spline SDFs of pieces (asset preparation: the values the paper's linear
+# interpolation system is solved for; evaluating the spline is the method's)
+# ----------------------------------------------------------------------------
+def polytope_sdf(points, verts, planes):
+    """Exact signed distance and its unit gradient of the convex polytope
+    conv(verts) with face planes ``planes`` at ``points`` [m, 3] (float64):
+    inside, the largest plane value and that plane's normal; outside, the
+    distance to the nearest boundary point (over the hull's triangles) and
+    the direction away from it."""
+    from scipy.spatial import ConvexHull
+    X = np.asarray(points, np.float64)
+    V = np.asarray(verts, np.float64)
+    P = np.asarray(planes, np.float64)
+    vals = X @ P[:, :3].T + P[:, 3]
+    k = np.argmax(vals, axis=1)
+    phi = vals[np.arange(len(X)), k]
+    nrm = P[k, :3].copy()
+    out = phi > 0
+    if out.any():
+        Y = X[out]
+        best = np.full(len(Y), np.inf)
+        cp = np.zeros_like(Y)
+        for tri in ConvexHull(V).simplices:
+            q = _closest_on_triangles(Y, V[tri[0]], V[tri[1]], V[tri[2]])
+            d = np.linalg.norm(Y - q, axis=1)
+            better = d < best
+            best[better] = d[better]
+            cp[better] = q[better]
+        phi[out] = best
+        nrm[out] = (Y - cp) / best[:, None]
+    return phi, nrm
+
+
+def _closest_on_triangles(X, a, b, c):
+    """Closest points of triangle abc to the points X [m, 3] (Voronoi regions
+    of the vertices, edges and face, in the standard order)."""
+    ab, ac = b - a, c - a
+    ap = X - a
+    d1, d2 = ap @ ab, ap @ ac
+    bp = X - b
+    d3, d4 = bp @ ab, bp @ ac
+    cp = X - c
+    d5, d6 = cp @ ab, cp @ ac
+    va = d3 * d6 - d5 * d4
+    vb = d5 * d2 - d1 * d6
+    vc = d1 * d4 - d3 * d2
+    den = np.where(va + vb + vc == 0, 1.0, va + vb + vc)
+    v = vb / den
+    w = vc / den
+    res = a + v[:, None] * ab + w[:, None] * ac                       # face
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t_ab = d1 / (d1 - d3)
+        t_ac = d2 / (d2 - d6)
+        t_bc = (d4 - d3) / ((d4 - d3) + (d5 - d6))
+    e_ab = (vc <= 0) & (d1 >= 0) & (d3 <= 0)
+    e_ac = (vb <= 0) & (d2 >= 0) & (d6 <= 0)
+    e_bc = (va <= 0) & ((d4 - d3) >= 0) & ((d5 - d6) >= 0)
+    # regions tested in the order a, b, ab, c, ac, bc (first match wins):
+    # applied here from the last to the first
+    res = np.where(e_bc[:, None], b + np.nan_to_num(t_bc)[:, None] * (c - b), res)
+    res = np.where(e_ac[:, None], a + np.nan_to_num(t_ac)[:, None] * ac, res)
+    res = np.where(((d6 >= 0) & (d5 <= d6))[:, None], c, res)
+    res = np.where(e_ab[:, None], a + np.nan_to_num(t_ab)[:, None] * ab, res)
+    res = np.where(((d3 >= 0) & (d4 <= d3))[:, None], b, res)
+    res = np.where(((d1 <= 0) & (d2 <= 0))[:, None], a, res)
+    return res
+
+
+def spline_interp_matrix(n):
+    """[n+3, n+1]: coefficients of the 1-D cubic spline through the values at
+    the n + 1 nodes of n voxels (Sec. 3.2: c_k + 4 c_{k+1} + c_{k+2} = f_k,
+    the paper's basis centred on the nodes), closed by a zero second
+    derivative at both ends (c_0 - 2 c_1 + c_2 = 0 and the same at node n)."""
+    A = np.zeros((n + 3, n + 3))
+    A[0, 0:3] = [1.0, -2.0, 1.0]
+    for i in range(n + 1):
+        A[i + 1, i:i + 3] = [1.0, 4.0, 1.0]
+    A[n + 2, n:n + 3] = [1.0, -2.0, 1.0]
+    return np.linalg.inv(A)[:, 1:n + 2]
+
+
+def fit_spline(field, origin, h, dims):
+    """Coefficients [(nx+3)(ny+3)(nz+3), C] of the tricubic splines through
+    ``field(points [m,3]) -> values [m, C]`` at the nodes of the grid
+    (``dims`` voxels of size ``h`` from ``origin``), one axis at a time."""
+    nx, ny, nz = (int(d) for d in dims)
+    gx = origin[0] + h * np.arange(nx + 1)
+    gy = origin[1] + h * np.arange(ny + 1)
+    gz = origin[2] + h * np.arange(nz + 1)
+    pts = np.stack(np.meshgrid(gx, gy, gz, indexing="ij"), -1).reshape(-1, 3)
+    F = np.asarray(field(pts), np.float64).reshape(nx + 1, ny + 1, nz + 1, -1)
+    C = np.einsum("ai,ijkc->ajkc", spline_interp_matrix(nx), F)
+    C = np.einsum("bj,ajkc->abkc", spline_interp_matrix(ny), C)
+    C = np.einsum("ck,abkq->abcq", spline_interp_matrix(nz), C)
+    return C.reshape(-1, C.shape[-1])
+
+
+def piece_spline(verts, planes, voxels=16, margin=0.03):
+    """Grid (origin, h), voxel counts and [rows, 4] coefficients of one
+    piece's spline SDF and normal splines, fitted to its exact polytope SDF
+    on its bounding box grown by ``margin`` (cubic voxels, ``voxels`` along
+    the longest side)."""
+    V = np.asarray(verts, np.float64)
+    lo, hi = V.min(0) - margin, V.max(0) + margin
+    h = float((hi - lo).max()) / voxels
+    dims = np.maximum(1, np.ceil((hi - lo) / h - 1e-9)).astype(np.int64)
+    coef = fit_spline(lambda p: np.concatenate(
+        [a.reshape(len(p), -1) for a in polytope_sdf(p, V, planes)], 1), lo, h, dims)
+    return lo, h, dims, coef
+
+
+def attach_splines(geom, voxels=16, margin=None):
+    """``geom`` with a SplineSet of every piece (margin default: 2 voxel
+    sizes' worth of the piece, at least 0.03)."""
+    grid, dims, coefs, row = [], [], [], 0
+    for p in range(geom.n_pieces):
+        v, f, _ = geom.piece(p)
+        ext = float((v.max(0) - v.min(0)).max())
+        m = margin if margin is not None else max(0.03, 2.0 * ext / voxels)
+        o, h, d, c = piece_spline(v, f, voxels, m)
+        grid.append([*o, h])
+        dims.append([*d, row])
+        coefs.append(c)
+        row += len(c)
+    geom.splines = SplineSet(np.asarray(grid, np.float32), np.asarray(dims, np.int64),
+                             np.concatenate(coefs).astype(np.float32))
+    return geom
 
 
 # ----------------------------------------------------------------------------
