@@ -88,6 +88,10 @@ typedef enum {
  *     taken at p. */
 #define CCM_FLAG_BODY_UNION 2u
 #define CCM_FLAG_PROJECT 4u
+/* SPLINE: every SDF piece is its tricubic spline SDF (Sec. 3.2, attached with
+ * ccm_attach_splines), and the contact normal is its normal spline; forward
+ * only, like the two above, and not combined with BODY_UNION. */
+#define CCM_FLAG_SPLINE 8u
 
 /* Method constants.  The paper fixes none of these values (Sec. 2-4). */
 typedef struct {
@@ -137,6 +141,26 @@ CCM_API const char* ccm_last_error(void);
  * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bodies,
                              ccm_geom* out);
+
+/* Tricubic spline SDFs of one body's convex pieces (Sec. 3.2), for
+ * CCM_FLAG_SPLINE.  Piece p has a voxel grid from origin grid[4p..4p+2] with
+ * cubic voxels of size grid[4p+3] > 0 and dims[3p..3p+2] voxels per axis
+ * (1..256); its spline has (nx+3)(ny+3)(nz+3) coefficient rows of 4 floats
+ * (SDF, normal x, y, z), z index fastest, coefficient k of an axis at grid
+ * node k - 1, so that s(x) = sum c u(tx - kx + 1) u(ty - ky + 1) u(tz - kz + 1)
+ * with t = (x - origin) / h and the paper's basis u.  The pieces' rows are
+ * concatenated in `coef`.  Outside its grid box a piece's SDF is the spline
+ * at the nearest box point plus the distance to the box.  All host arrays. */
+typedef struct {
+  const float* grid;       /* [n_pieces, 4] */
+  const int32_t* dims;     /* [n_pieces, 3] */
+  const float* coef;       /* [sum of rows, 4] */
+} ccm_spline_desc;
+
+/* Attaches (or replaces) the spline SDFs of `body`'s pieces, one desc for
+ * the whole body.  Synchronous; allocates.  Errors: CCM_ERR_INVALID (bad
+ * handle, sizes or non-finite values), CCM_ERR_OOM, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_attach_splines(ccm_ctx ctx, ccm_geom body, const ccm_spline_desc* desc);
 
 /* Marks bodies as released: later calls reject their handles.  Batches that
  * were planned before keep working.  Device memory of released bodies is

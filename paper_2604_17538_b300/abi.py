@@ -54,6 +54,10 @@ class ccm_tuning(C.Structure):
                 ("groups_b", C.c_int32), ("flat_records", C.c_int32)]
 
 
+class ccm_spline_desc(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("dims", C.c_void_p), ("coef", C.c_void_p)]
+
+
 class ccm_serve_config(C.Structure):
     _fields_ = [("max_wave_pairs", C.c_int64), ("max_wave_requests", C.c_int64),
                 ("max_queued", C.c_int64), ("params", ccm_params), ("tuning", ccm_tuning)]
@@ -104,6 +108,7 @@ _SIGS = {
     "ccm_serve_hold": (C.c_int, [C.c_void_p, C.c_int]),
     "ccm_poll_completed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "ccm_serve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ccm_attach_splines": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
 }
 
 _lib = None

@@ -59,6 +59,22 @@ class Context:
         check(lib().ccm_load_geometry(self.handle, descs, nb, ptr(out)))
         return out
 
+    def attach_splines(self, geom, handles):
+        """Attaches the tricubic spline SDFs of ``geom.splines`` (a
+        ``scenes.SplineSet``) to the bodies ``handles`` (``load_geometry``'s
+        result for the same geometry)."""
+        sp = geom.splines
+        for b in range(geom.n_bodies):
+            p0, p1 = int(geom.body_piece_off[b]), int(geom.body_piece_off[b + 1])
+            dims = np.ascontiguousarray(sp.dims[p0:p1, :3], np.int32)
+            grid = np.ascontiguousarray(sp.grid[p0:p1], np.float32)
+            r0 = int(sp.dims[p0, 3])
+            r1 = int(sp.dims[p1, 3]) if p1 < len(sp.dims) else len(sp.coef)
+            coef = np.ascontiguousarray(sp.coef[r0:r1], np.float32)
+            desc = abi.ccm_spline_desc(ptr(grid), ptr(dims), ptr(coef))
+            check(lib().ccm_attach_splines(self.handle, C.c_uint64(int(handles[b])),
+                                           C.byref(desc)))
+
     def free_geometry(self, handles):
         h = np.ascontiguousarray(handles, np.uint64)
         check(lib().ccm_free_geometry(self.handle, ptr(h), len(h)))

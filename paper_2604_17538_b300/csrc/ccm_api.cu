@@ -153,7 +153,57 @@ void ccm_destroy(ccm_ctx ctx) {
   c->d_verts.release();
   c->d_planes.release();
   c->d_edges.release();
+  c->d_splines.release();
+  c->d_spline_coef.release();
   delete c;
+}
+
+ccm_status ccm_attach_splines(ccm_ctx ctx, ccm_geom body, const ccm_spline_desc* desc) {
+  if (!ctx || !desc || !desc->grid || !desc->dims || !desc->coef)
+    return fail(CCM_ERR_INVALID, "bad arguments");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  int32_t bi;
+  ccm_status s = c->body_of(body, &bi);
+  if (s != CCM_OK) return s;
+  const BodyRec br = c->bodies[bi];
+  // validate before touching the context
+  int64_t rows = 0;
+  for (int p = 0; p < br.np; ++p) {
+    const float* gq = desc->grid + 4 * p;
+    const int32_t* d = desc->dims + 3 * p;
+    for (int a = 0; a < 4; ++a)
+      if (!std::isfinite(gq[a])) return fail(CCM_ERR_INVALID, "piece %d: non-finite grid", p);
+    if (!(gq[3] > 0.f)) return fail(CCM_ERR_INVALID, "piece %d: voxel size must be > 0", p);
+    for (int a = 0; a < 3; ++a)
+      if (d[a] < 1 || d[a] > 256)
+        return fail(CCM_ERR_INVALID, "piece %d: voxel counts out of [1, 256]", p);
+    rows += (int64_t)(d[0] + 3) * (d[1] + 3) * (d[2] + 3);
+  }
+  if ((int64_t)c->spline_coef.size() + rows >= ((int64_t)1 << 31))
+    return fail(CCM_ERR_INVALID, "too many spline coefficients");
+  for (int64_t i = 0; i < 4 * rows; ++i)
+    if (!std::isfinite(desc->coef[i])) return fail(CCM_ERR_INVALID, "non-finite coefficient");
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->splines.size() < c->pieces.size()) c->splines.resize(c->pieces.size(), SplineRec{});
+  int64_t r0 = 0;
+  for (int p = 0; p < br.np; ++p) {
+    const float* gq = desc->grid + 4 * p;
+    const int32_t* d = desc->dims + 3 * p;
+    const int64_t n = (int64_t)(d[0] + 3) * (d[1] + 3) * (d[2] + 3);
+    SplineRec sr;
+    sr.grid = make_float4(gq[0], gq[1], gq[2], gq[3]);
+    sr.dims = make_int4(d[0], d[1], d[2], (int)c->spline_coef.size());
+    for (int64_t i = 0; i < n; ++i) {
+      const float* q = desc->coef + 4 * (r0 + i);
+      c->spline_coef.push_back(make_float4(q[0], q[1], q[2], q[3]));
+    }
+    c->splines[br.p0 + p] = sr;
+    r0 += n;
+  }
+  CCM_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if ((s = upload(c->d_splines, c->splines, "splines")) != CCM_OK) return s;
+  return upload(c->d_spline_coef, c->spline_coef, "spline coefficients");
 }
 
 ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bodies,
@@ -509,8 +559,9 @@ ccm_status ccm_contacts_backward_noalloc(ccm_batch batch, const float* pose_a,
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
-  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT))
-    return fail(CCM_ERR_INVALID, "the body-union and projection variants are forward only");
+  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT | CCM_FLAG_SPLINE))
+    return fail(CCM_ERR_INVALID,
+                "the body-union, projection and spline variants are forward only");
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
@@ -864,8 +915,9 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   if (kp.flags & CCM_FLAG_NO_CULL) return fail(CCM_ERR_INVALID, "the reverse pass always culls");
-  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT))
-    return fail(CCM_ERR_INVALID, "the body-union and projection variants are forward only");
+  if (kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT | CCM_FLAG_SPLINE))
+    return fail(CCM_ERR_INVALID,
+                "the body-union, projection and spline variants are forward only");
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
   BwdLaunch L;
   L.g = b->ctx->dev_geom();
@@ -963,9 +1015,42 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   ccm_status s = make_kparams(prm, &kp);
   if (s != CCM_OK) return s;
   CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
-  if ((kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT)) && (saved || counters))
+  if ((kp.flags & (CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT | CCM_FLAG_SPLINE)) &&
+      (saved || counters))
     return fail(CCM_ERR_INVALID,
-                "the body-union and projection variants keep no record and count no work");
+                "the body-union, projection and spline variants keep no record and count no work");
+  if (kp.flags & CCM_FLAG_SPLINE) {
+    if (kp.flags & CCM_FLAG_BODY_UNION)
+      return fail(CCM_ERR_INVALID, "the spline variant has no body union");
+    {   // every piece of every body of the batch needs its spline
+      std::lock_guard<std::mutex> lk(b->ctx->mu);
+      const Context& c = *b->ctx;
+      for (const PairRec& pr : b->pairs)
+        for (int32_t bi : {pr.bodyA, pr.bodyB}) {
+          const BodyRec& br = c.bodies[bi];
+          if ((int64_t)c.splines.size() < (int64_t)br.p0 + br.np)
+            return fail(CCM_ERR_INVALID, "body %d has no spline SDF", bi);
+          for (int p = 0; p < br.np; ++p)
+            if (c.splines[br.p0 + p].dims.x == 0)
+              return fail(CCM_ERR_INVALID, "body %d has no spline SDF", bi);
+        }
+    }
+    SplineLaunch Sp;
+    Sp.g = b->ctx->dev_geom();
+    Sp.splines = static_cast<const SplineRec*>(b->ctx->d_splines.ptr);
+    Sp.coef = static_cast<const float4*>(b->ctx->d_spline_coef.ptr);
+    Sp.pairs = static_cast<const PairRec*>(b->d_pairs.ptr);
+    Sp.row_pair = static_cast<const int32_t*>(b->d_row_pair.ptr);
+    Sp.G = b->G;
+    Sp.pose_a = pose_a;
+    Sp.pose_b = pose_b;
+    Sp.kp = kp;
+    Sp.y = y;
+    Sp.n_sm = b->ctx->n_sm;
+    const cudaError_t e = launch_spline_forward(Sp, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spline forward launch");
+    return CCM_OK;
+  }
   if (kp.flags & CCM_FLAG_BODY_UNION) {
     UnionLaunch U;
     U.g = b->ctx->dev_geom();

@@ -43,6 +43,14 @@ struct DevGeom {
   const uint32_t* __restrict__ edges;
 };
 
+// Tricubic spline SDF of a piece (Sec. 3.2): grid origin and voxel size, and
+// the voxel counts with the first of its (nx+3)(ny+3)(nz+3) coefficient rows
+// (float4: SDF, normal x, y, z); nx = 0 for a piece without one.
+struct SplineRec {
+  float4 grid;
+  int4 dims;
+};
+
 // Method constants with the derived factors the kernels use.
 struct KParams {
   float tau_sdf, tau_trace, tau_clip, tau_blend, d_max, gate_width;

@@ -13,6 +13,7 @@
 #include "ccm_bwd.h"
 #include "ccm_flat.h"
 #include "ccm_union.h"
+#include "ccm_spline.h"
 
 namespace ccm {
 
@@ -38,6 +39,11 @@ struct Context {
   std::vector<uint32_t> edges;
   std::vector<uint8_t> alive;
   DevBuf d_pieces, d_bodies, d_verts, d_planes, d_edges;
+  // tricubic spline SDFs (ccm_attach_splines): one record per piece (zero
+  // dims when it has none) and the coefficient rows
+  std::vector<SplineRec> splines;
+  std::vector<float4> spline_coef;
+  DevBuf d_splines, d_spline_coef;
   Serving* serving = nullptr;
 
   DevGeom dev_geom() const;

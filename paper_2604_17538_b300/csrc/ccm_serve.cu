@@ -584,7 +584,7 @@ ccm_status ccm_serve_start(ccm_ctx ctx, const ccm_serve_config* cfg) {
   KParams kp;
   ccm_status st = make_kparams(&cfg->params, &kp);
   if (st != CCM_OK) return st;
-  if (kp.flags & (CCM_FLAG_NO_CULL | CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT))
+  if (kp.flags & (CCM_FLAG_NO_CULL | CCM_FLAG_BODY_UNION | CCM_FLAG_PROJECT | CCM_FLAG_SPLINE))
     return fail(CCM_ERR_INVALID, "the serving loop runs the default method (no flags)");
   CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
   // launch shape from every resident body, independent of any wave's mix
