@@ -214,11 +214,22 @@ typedef struct {
                                  for the per-contact reverse passes, in records per output
                                  group (0: 16, and at least 65,536 in all; -1: no list, the
                                  reverse passes re-gate per pair), -1..4096 */
+  int32_t stage_tma;          /* forward: stage the SDF body's planes into shared memory
+                                 with bulk (TMA) copies (0) or plain loads (-1) */
+  int32_t stage_wait;         /* bound of a bulk copy's wait, in polls of its barrier
+                                 (0: 2^22; -1: none, so that every wait runs out -- for
+                                 tests of the timeout path), -1..2^30 */
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
 /* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of
  * range or too large for shared memory), CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t);
+
+/* Waits for `stream` and reports whether a kernel of the batch stopped on a
+ * bounded device-side wait since the last check (CCM_ERR_TIMEOUT; its outputs
+ * are then incomplete), clearing the flag.  Synchronous.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_TIMEOUT, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_batch_check(ccm_batch batch, ccm_stream stream);
 
 /* Forward pass (Sec. 4.2-4.4).  pose_a, pose_b: device [n,12] float32; y:
  * device [G,8] float32, fully overwritten.  Asynchronous on `stream`.

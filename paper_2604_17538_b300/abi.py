@@ -51,7 +51,8 @@ class ccm_tuning(C.Structure):
     _fields_ = [("item_v", C.c_int32), ("item_e", C.c_int32), ("item_vb", C.c_int32),
                 ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("groups", C.c_int32),
                 ("stage_planes", C.c_int32), ("stage_verts", C.c_int32),
-                ("groups_b", C.c_int32), ("flat_records", C.c_int32)]
+                ("groups_b", C.c_int32), ("flat_records", C.c_int32),
+                ("stage_tma", C.c_int32), ("stage_wait", C.c_int32)]
 
 
 class ccm_spline_desc(C.Structure):
@@ -109,6 +110,7 @@ _SIGS = {
     "ccm_poll_completed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "ccm_serve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ccm_attach_splines": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
+    "ccm_batch_check": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None

@@ -112,7 +112,7 @@ class Batch:
         check(lib().ccm_batch_get_tuning(self.handle, C.byref(t)))
         return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps",
                                            "groups", "stage_planes", "stage_verts", "groups_b",
-                                           "flat_records")}
+                                           "flat_records", "stage_tma", "stage_wait")}
 
     def set_tuning(self, **kw):
         t = abi.ccm_tuning()
@@ -120,6 +120,13 @@ class Batch:
         for k, v in kw.items():
             setattr(t, k, int(v))
         check(lib().ccm_batch_set_tuning(self.handle, C.byref(t)))
+
+    def check(self, stream=None):
+        """``ccm_batch_check``: waits for the stream and raises CcmError
+        (CCM_ERR_TIMEOUT) if a kernel of the batch stopped on a bounded wait."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        check(lib().ccm_batch_check(self.handle, C.c_void_p(s.cuda_stream)))
 
     def close(self):
         if self.handle:

@@ -385,6 +385,21 @@ ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t) {
   return setup_flat(b->ctx, b);
 }
 
+ccm_status ccm_batch_check(ccm_batch batch, ccm_stream stream) {
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
+  CCM_CUDA(cudaSetDevice(b->ctx->device), "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t status = 0;
+  CCM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  CCM_CUDA(cudaMemcpy(&status, b->d_status.ptr, sizeof(status), cudaMemcpyDeviceToHost),
+           "cudaMemcpy");
+  if (status == 0) return CCM_OK;
+  const int32_t zero = 0;
+  CCM_CUDA(cudaMemcpy(b->d_status.ptr, &zero, sizeof(zero), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return fail((ccm_status)status, "a kernel of the batch stopped on a bounded device-side wait");
+}
+
 ccm_status ccm_contacts(ccm_batch batch, const float* pose_a, const float* pose_b,
                         const ccm_params* prm, float* y, ccm_stream stream) {
   return run_forward(reinterpret_cast<Batch*>(batch), pose_a, pose_b, prm, y, nullptr, nullptr,
@@ -832,7 +847,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
       (t.stage_planes != 0 && (t.stage_planes < 16 || t.stage_planes > 4096)) ||
       (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)) ||
       t.groups_b < 0 || t.groups_b > kGroupsPerChunk || t.flat_records < -1 ||
-      t.flat_records > 4096)
+      t.flat_records > 4096 || t.stage_tma < -1 || t.stage_tma > 0 || t.stage_wait < -1 ||
+      t.stage_wait > (1 << 30))
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -851,6 +867,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   // directions in one list, which its adjoint sweep then reuses
   us.groups_b = std::min(us.groups, t.groups_b ? t.groups_b : 4);
   us.hit_words = std::min(kHitWords, (mx.s_pieces + 31) / 32);
+  us.stage_tma = t.stage_tma == 0 ? 1 : 0;
+  us.wait_limit = t.stage_wait == 0 ? (1ll << 22) : (t.stage_wait < 0 ? 0 : t.stage_wait);
   us.slice_bytes = unit_slice_bytes(us);
   us.warps = t.fwd_warps;
   while (us.warps > 1 && us.warps * us.slice_bytes > c->smem_optin) --us.warps;
@@ -887,6 +905,10 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
   if (!bt->d_sched.ptr) {   // forward, gradient pass, H u pass
     std::vector<int32_t> zeros(3, 0);
     if ((st = upload(bt->d_sched, zeros, "work counters")) != CCM_OK) return st;
+  }
+  if (!bt->d_status.ptr) {
+    std::vector<int32_t> zeros(1, 0);
+    if ((st = upload(bt->d_status, zeros, "status word")) != CCM_OK) return st;
   }
   if ((int64_t)items.size() != bt->n_items || !bt->d_part.ptr) {
     bt->d_part.release();
@@ -998,6 +1020,7 @@ void Batch::release() {
   d_item_off.release();
   d_pair_order.release();
   d_sched.release();
+  d_status.release();
   d_part.release();
   d_row_pair.release();
   for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted, &d_ftiles}) b->release();
@@ -1082,6 +1105,7 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   L.counters = counters;
   L.sched = static_cast<int*>(b->d_sched.ptr);
   L.grid = b->grid;
+  L.status = static_cast<int*>(b->d_status.ptr);
   const bool flat = saved && b->flat_cap > 0;
   if (flat) {
     L.cl = b->contact_list();

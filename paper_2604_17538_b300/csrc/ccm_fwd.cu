@@ -277,11 +277,14 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, float* __restrict__ saved,
                 unsigned long long* __restrict__ counters, int* __restrict__ sched,
-                ContactList cl) {
+                ContactList cl, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const UnitSlice sl = unit_slice(smem_raw + (size_t)warp * us.slice_bytes, us);
+  uint32_t phase = 0;   // parity of the warp's next bulk-copy barrier phase
+  if (us.stage_tma && lane == 0) mbar_init(sl.mbar, 1);
+  __syncwarp();
   int* dsub = sl.dsub;
   const bool no_cull = (kp.flags & 1u) != 0;
   const int64_t n_run = dev_items ? *dev_items : n_items;
@@ -369,7 +372,25 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
         }
         const int nsc = sc1 - sc0;
         if (nsc == 0) break;   // unreachable, as above
-        stage_copy(sl.planes, g.planes + g.pieces[S.p0 + sc0].f0, P, lane);
+        if (us.stage_tma) {
+          // the chunk's planes (contiguous, 16 B each) in one bulk copy; the
+          // lanes' earlier reads of the slice precede it (syncwarp above)
+          if (lane == 0) {
+            fence_proxy_async_smem();
+            bulk_copy_g2s(sl.planes, g.planes + g.pieces[S.p0 + sc0].f0, 16u * (uint32_t)P,
+                          sl.mbar);
+          }
+          const bool ok = mbar_wait_bounded(sl.mbar, phase, us.wait_limit);
+          if (!ok) {
+            // record the timeout, let the copy land, and stop this warp
+            if (lane == 0 && status) atomicExch(status, (int)CCM_ERR_TIMEOUT);
+            mbar_wait_bounded(sl.mbar, phase, kDrainLimit);
+            return;
+          }
+          phase ^= 1u;
+        } else {
+          stage_copy(sl.planes, g.planes + g.pieces[S.p0 + sc0].f0, P, lane);
+        }
         __syncwarp();
 
         // gate the directions (fc, sc), 32 at a time, collecting live ones
@@ -451,10 +472,10 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   }
   if (L.counters)
     unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl);
+                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status);
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl);
+                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ struct FwdLaunch {
   int* sched;                     // optional work counter (device int), zeroed by the launch
   int grid;
   ContactList cl{};               // with `saved`: the contact list (cl.recs NULL: none)
+  int* status = nullptr;          // optional device word: CCM_ERR_TIMEOUT if a bounded wait ran out
 };
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);

@@ -79,6 +79,7 @@ struct Batch {
   DevBuf d_pair_order;           // pairs by decreasing cost (per-pair reverse pass)
   bool per_pair = false;         // every body has <= kHitS pieces
   DevBuf d_sched;                // [3] work counters: forward, gradient pass, H u pass
+  DevBuf d_status;               // [1] CCM_ERR_TIMEOUT once a bounded wait ran out
   BatchMaxima mx;
   ccm_tuning tuning{};
   UnitShape us{};

@@ -35,6 +35,8 @@ struct UnitShape {
   int32_t groups_b;       // groups per chunk of the reverse pass (<= groups)
   int32_t hit_words;      // hit words per group kept in shared memory:
                           // ceil(largest S body's pieces / 32) <= kHitWords
+  int32_t stage_tma;      // 1: stage the SDF body's planes with bulk copies (TMA)
+  int64_t wait_limit;     // iterations of a bounded wait for a bulk copy
 };
 
 constexpr int kGroupsPerChunk = 32;   // most groups of one F chunk (lane-indexed)
@@ -65,6 +67,7 @@ struct UnitSlice {
                       // edge cull, in phi's space)
   int* gcnt;          // [2 groups] contacts of non-zero weight per group (vertex,
                       // edge) found so far, for the contact list
+  uint64_t* mbar;     // [1] completion barrier of the warp's bulk copies
 };
 
 // Rounding allowance of the edge cull's plane bound (coordinates are O(1) in
@@ -90,6 +93,7 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += align16i(2 * u.item_e);               // elist
   b += align16i(u.item_v);                   // need
   b += align16i(8 * u.groups);               // gcnt
+  b += 16;                                   // mbar
   return b;
 }
 
@@ -115,7 +119,8 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
   s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
   s.need = reinterpret_cast<uint8_t*>(p);             p += align16i(u.item_v);
-  s.gcnt = reinterpret_cast<int*>(p);
+  s.gcnt = reinterpret_cast<int*>(p);               p += align16i(8 * u.groups);
+  s.mbar = reinterpret_cast<uint64_t*>(p);
   s.am = reinterpret_cast<uint16_t*>(s.phi);
   return s;
 }
