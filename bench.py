@@ -788,6 +788,55 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
             "latency": "arrival to completion as seen by the host (ms)", "sweep": results}
 
 
+def run_broadphase(args):
+    """Broad phase against d_max, shaped like the paper's Sec. 5.4 sweep: one
+    pair of 8-piece hull bodies, B translated along x through a batch of
+    offsets spanning overlap to separation, the forward timed at several
+    d_max with (a) the exact plane culls, (b) those plus the voxel grids
+    (Sec. 4.3) and (c) no culls at all (every feature through the narrow
+    phase), with the plane-evaluation counters of each."""
+    import torch
+    from paper_2604_17538_b300 import abi, api, build, scenes
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    base = scenes.hull_env_scene(seed=9, n_envs=1, workers=0)
+    V = base.geom.verts
+    ext = float((V.max(0) - V.min(0)).max())
+    n = args.bp_pairs
+    shift = np.linspace(0.1 * ext, 0.9 * ext, n)
+    pose_b = np.repeat(base.pose_b, n, axis=0).copy()
+    pose_b[:, 9] = base.pose_a[0, 9] + shift
+    sc = scenes.Scene(base.geom, np.zeros(n, np.int64), np.ones(n, np.int64),
+                      np.repeat(base.pose_a, n, axis=0), pose_b)
+    ctx = api.Context(local)
+    batch, pa, pb = api.scene_to_device(sc, ctx)
+    ctx.build_voxel_grids(args.bp_voxels)
+    rows = []
+    for d_max in (0.0, 0.01, 0.02, 0.05, 0.1):
+        row = {"d_max": d_max}
+        for name, flags in (("plane_culls", 0), ("plane_and_voxel_culls", 16), ("no_culls", 1)):
+            prm = {"d_max": d_max, "flags": flags}
+            cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
+            batch.contacts(pa, pb, params=prm, counters=cnt)
+            for _ in range(3):
+                batch.contacts(pa, pb, params=prm)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.steps):
+                batch.contacts(pa, pb, params=prm)
+            b.record()
+            b.synchronize()
+            row[name] = {"ms": a.elapsed_time(b) / args.steps,
+                         "counters": dict(zip(abi.COUNTER_NAMES, cnt.cpu().tolist()))}
+        rows.append(row)
+    batch.check()
+    return {"workload": f"{n} translations of one pair of 8-piece hull bodies along x, "
+                        f"0.1-0.9 x the scene's extent ({ext:.3f})",
+            "voxels": args.bp_voxels, "sweep": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -797,7 +846,10 @@ def main():
     ap.add_argument("--envs", type=int, default=N_ENVS)
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hull", choices=["hull", "uneven", "serve"])
+    ap.add_argument("--workload", default="hull", choices=["hull", "uneven", "serve",
+                                                            "broadphase"])
+    ap.add_argument("--bp-pairs", type=int, default=4096)
+    ap.add_argument("--bp-voxels", type=int, default=8)
     ap.add_argument("--pairs", type=int, default=65536)
     ap.add_argument("--tuning", default="",
                     help="uneven workload: a fixed launch shape (key=value,... of "
@@ -826,6 +878,11 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.workload == "broadphase":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "ms per forward", "broadphase":
+                              run_broadphase(args)}))
+        return
     if args.workload == "uneven":
         out, sc = run_uneven(args, rank, world)
         if rank == 0:

@@ -92,6 +92,12 @@ typedef enum {
  * ccm_attach_splines), and the contact normal is its normal spline; forward
  * only, like the two above, and not combined with BODY_UNION. */
 #define CCM_FLAG_SPLINE 8u
+/* VOXEL_CULL: the forward also culls with the voxel grids of
+ * ccm_build_voxel_grids (Sec. 4.3 broad phase: a vertex whose voxel's lower
+ * bound of the SDF is >= d_max, an edge whose corners' bounds minus its
+ * length are); culls are exact, so outputs equal those without the flag to
+ * float rounding.  Without grids the flag changes nothing. */
+#define CCM_FLAG_VOXEL_CULL 16u
 
 /* Method constants.  The paper fixes none of these values (Sec. 2-4). */
 typedef struct {
@@ -161,6 +167,16 @@ typedef struct {
  * the whole body.  Synchronous; allocates.  Errors: CCM_ERR_INVALID (bad
  * handle, sizes or non-finite values), CCM_ERR_OOM, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_attach_splines(ccm_ctx ctx, ccm_geom body, const ccm_spline_desc* desc);
+
+/* Builds the broad-phase voxel grids (Sec. 4.3) of every piece loaded so far,
+ * for CCM_FLAG_VOXEL_CULL: per piece a grid of cubic voxels over the
+ * bounding box of its vertices, `voxels` (1..64) along its longest side,
+ * each voxel holding a lower bound of the piece's SDF anywhere in it: the
+ * largest plane value at its centre minus its circumradius (the largest
+ * plane value is 1-Lipschitz and never above the smooth SDF).  Pieces loaded
+ * later have no grid until the next call.  Synchronous; allocates.
+ * Errors: CCM_ERR_INVALID, CCM_ERR_OOM, CCM_ERR_CUDA. */
+CCM_API ccm_status ccm_build_voxel_grids(ccm_ctx ctx, int voxels);
 
 /* Marks bodies as released: later calls reject their handles.  Batches that
  * were planned before keep working.  Device memory of released bodies is

@@ -111,6 +111,7 @@ _SIGS = {
     "ccm_serve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ccm_attach_splines": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
     "ccm_batch_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ccm_build_voxel_grids": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 _lib = None

@@ -75,6 +75,11 @@ class Context:
             check(lib().ccm_attach_splines(self.handle, C.c_uint64(int(handles[b])),
                                            C.byref(desc)))
 
+    def build_voxel_grids(self, voxels: int = 8):
+        """``ccm_build_voxel_grids``: broad-phase voxel grids of every loaded
+        piece (used by the forward with the CCM_FLAG_VOXEL_CULL flag)."""
+        check(lib().ccm_build_voxel_grids(self.handle, int(voxels)))
+
     def free_geometry(self, handles):
         h = np.ascontiguousarray(handles, np.uint64)
         check(lib().ccm_free_geometry(self.handle, ptr(h), len(h)))

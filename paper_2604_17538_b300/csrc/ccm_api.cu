@@ -68,6 +68,9 @@ DevGeom Context::dev_geom() const {
   g.verts = static_cast<const float4*>(d_verts.ptr);
   g.planes = static_cast<const float4*>(d_planes.ptr);
   g.edges = static_cast<const uint32_t*>(d_edges.ptr);
+  g.voxels = static_cast<const VoxelRec*>(d_voxels.ptr);
+  g.voxel_vals = static_cast<const float*>(d_voxel_vals.ptr);
+  g.n_voxels = (int32_t)n_voxels;
   return g;
 }
 
@@ -155,7 +158,62 @@ void ccm_destroy(ccm_ctx ctx) {
   c->d_edges.release();
   c->d_splines.release();
   c->d_spline_coef.release();
+  c->d_voxels.release();
+  c->d_voxel_vals.release();
   delete c;
+}
+
+ccm_status ccm_build_voxel_grids(ccm_ctx ctx, int voxels) {
+  if (!ctx || voxels < 1 || voxels > 64) return fail(CCM_ERR_INVALID, "voxels must be in [1, 64]");
+  Context* c = reinterpret_cast<Context*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  CCM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+  std::vector<VoxelRec> recs(c->pieces.size());
+  std::vector<float> vals;
+  for (size_t p = 0; p < c->pieces.size(); ++p) {
+    const PieceRec& pr = c->pieces[p];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < pr.nv; ++i) {
+      const float4 v = c->verts[pr.v0 + i];
+      const double xs[3] = {v.x, v.y, v.z};
+      for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], xs[a]); hi[a] = std::max(hi[a], xs[a]); }
+    }
+    double ext = 0;
+    for (int a = 0; a < 3; ++a) ext = std::max(ext, hi[a] - lo[a]);
+    const double h = std::max(ext, 1e-6) / voxels;
+    int dims[3];
+    for (int a = 0; a < 3; ++a)
+      dims[a] = std::max(1, (int)std::ceil((hi[a] - lo[a]) / h - 1e-9));
+    const double r = 0.5 * h * std::sqrt(3.0);
+    VoxelRec vr;
+    vr.grid = make_float4((float)lo[0], (float)lo[1], (float)lo[2], (float)h);
+    vr.dims = make_int4(dims[0], dims[1], dims[2], (int)vals.size());
+    // the grid as the kernels see it (float origin and size): a voxel's
+    // points lie within its circumradius (plus rounding) of its centre
+    const double fo[3] = {vr.grid.x, vr.grid.y, vr.grid.z}, fh = vr.grid.w;
+    for (int ix = 0; ix < dims[0]; ++ix)
+      for (int iy = 0; iy < dims[1]; ++iy)
+        for (int iz = 0; iz < dims[2]; ++iz) {
+          const double cx = fo[0] + (ix + 0.5) * fh, cy = fo[1] + (iy + 0.5) * fh,
+                       cz = fo[2] + (iz + 0.5) * fh;
+          double m = -INFINITY;
+          for (int k = 0; k < pr.nf; ++k) {
+            const float4 q = c->planes[pr.f0 + k];
+            m = std::max(m, q.x * cx + q.y * cy + q.z * cz + (double)q.w);
+          }
+          // the largest plane value is 1-Lipschitz and below the piece's SDF
+          vals.push_back((float)(m - r * (1.0 + 1e-6) - 1e-6));
+        }
+    recs[p] = vr;
+  }
+  if ((int64_t)vals.size() >= ((int64_t)1 << 31)) return fail(CCM_ERR_INVALID, "grids too large");
+  CCM_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  ccm_status s;
+  if ((s = upload(c->d_voxels, recs, "voxel grids")) != CCM_OK) return s;
+  if (vals.empty()) vals.push_back(0.f);
+  if ((s = upload(c->d_voxel_vals, vals, "voxel grids")) != CCM_OK) return s;
+  c->n_voxels = (int64_t)recs.size();
+  return CCM_OK;
 }
 
 ccm_status ccm_attach_splines(ccm_ctx ctx, ccm_geom body, const ccm_spline_desc* desc) {
@@ -204,6 +262,50 @@ ccm_status ccm_attach_splines(ccm_ctx ctx, ccm_geom body, const ccm_spline_desc*
   CCM_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
   if ((s = upload(c->d_splines, c->splines, "splines")) != CCM_OK) return s;
   return upload(c->d_spline_coef, c->spline_coef, "spline coefficients");
+}
+
+// Morton (Z-order) key of a point quantised to 10 bits per axis in a box
+static uint32_t zorder_key(const float* v, const float lo[3], const float inv[3]) {
+  uint32_t key = 0;
+  uint32_t q[3];
+  for (int a = 0; a < 3; ++a) {
+    const float t = (v[a] - lo[a]) * inv[a];
+    q[a] = (uint32_t)std::min(1023.0f, std::max(0.0f, t * 1023.0f));
+  }
+  for (int bit = 9; bit >= 0; --bit)
+    for (int a = 0; a < 3; ++a) key = (key << 1) | ((q[a] >> bit) & 1u);
+  return key;
+}
+
+// Sec. 4.3 serialisation: the order in which a piece's vertices and edges are
+// stored, along a Z-order curve through the piece's bounding box, so that
+// features with neighbouring indices are near each other and the lanes of a
+// warp that take them in order tend to agree on a cull.  perm_v[new] = old
+// vertex, perm_e[new] = old edge (ties keep the caller's order).
+static void serialise_piece(const float* verts, int nv, const int32_t* edges, int ne,
+                            std::vector<int>* perm_v, std::vector<int>* perm_e) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = 0; i < nv; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], verts[3 * i + a]);
+      hi[a] = std::max(hi[a], verts[3 * i + a]);
+    }
+  float inv[3];
+  for (int a = 0; a < 3; ++a) inv[a] = hi[a] > lo[a] ? 1.0f / (hi[a] - lo[a]) : 0.f;
+  std::vector<uint32_t> kv(nv), ke(ne);
+  for (int i = 0; i < nv; ++i) kv[i] = zorder_key(verts + 3 * i, lo, inv);
+  for (int j = 0; j < ne; ++j) {
+    const float* a = verts + 3 * edges[2 * j];
+    const float* b = verts + 3 * edges[2 * j + 1];
+    const float m[3] = {0.5f * (a[0] + b[0]), 0.5f * (a[1] + b[1]), 0.5f * (a[2] + b[2])};
+    ke[j] = zorder_key(m, lo, inv);
+  }
+  perm_v->resize(nv);
+  perm_e->resize(ne);
+  for (int i = 0; i < nv; ++i) (*perm_v)[i] = i;
+  for (int j = 0; j < ne; ++j) (*perm_e)[j] = j;
+  std::stable_sort(perm_v->begin(), perm_v->end(), [&](int x, int y) { return kv[x] < kv[y]; });
+  std::stable_sort(perm_e->begin(), perm_e->end(), [&](int x, int y) { return ke[x] < ke[y]; });
 }
 
 ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bodies,
@@ -262,9 +364,12 @@ ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bod
       pr.ne = ne;
       pr.body = (int32_t)c->bodies.size();
       pr.pad = 0;
+      std::vector<int> pv, pe, rank(nv);
+      serialise_piece(d.verts + 3 * vo, nv, d.edges + 2 * eo, ne, &pv, &pe);
+      for (int i = 0; i < nv; ++i) rank[pv[i]] = i;
       double cx = 0, cy = 0, cz = 0;
       for (int i = 0; i < nv; ++i) {
-        const float* v = d.verts + 3 * (vo + i);
+        const float* v = d.verts + 3 * (vo + pv[i]);
         c->verts.push_back(make_float4(v[0], v[1], v[2], 0.f));
         cx += v[0]; cy += v[1]; cz += v[2];
       }
@@ -283,7 +388,9 @@ ccm_status ccm_load_geometry(ccm_ctx ctx, const ccm_body_desc* bodies, int n_bod
         c->planes.push_back(make_float4(q[0], q[1], q[2], q[3]));
       }
       for (int j = 0; j < ne; ++j) {
-        const uint32_t i0 = (uint32_t)d.edges[2 * (eo + j)], i1 = (uint32_t)d.edges[2 * (eo + j) + 1];
+        const int o = pe[j];
+        const uint32_t i0 = (uint32_t)rank[d.edges[2 * (eo + o)]],
+                       i1 = (uint32_t)rank[d.edges[2 * (eo + o) + 1]];
         c->edges.push_back(i0 | (i1 << 16));
       }
       c->pieces.push_back(pr);

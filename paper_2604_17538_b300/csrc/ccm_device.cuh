@@ -35,13 +35,41 @@ struct WorkItem {
   uint16_t fc0, fc1;
 };
 
+// Voxel grid of a piece for the broad phase (Sec. 4.3): origin and voxel
+// size, voxel counts and the offset of its values; every value is a lower
+// bound of the piece's SDF anywhere in that voxel (the largest plane value at
+// the voxel's centre minus the voxel's circumradius).  dims.x = 0: no grid.
+struct VoxelRec {
+  float4 grid;
+  int4 dims;
+};
+
 struct DevGeom {
   const PieceRec* __restrict__ pieces;
   const BodyRec* __restrict__ bodies;
   const float4* __restrict__ verts;
   const float4* __restrict__ planes;
   const uint32_t* __restrict__ edges;
+  const VoxelRec* __restrict__ voxels = nullptr;    // [n_voxels] or NULL
+  const float* __restrict__ voxel_vals = nullptr;
+  int32_t n_voxels = 0;                             // pieces with a record
 };
+
+// the voxel grid's lower bound of piece p's SDF at x (piece / body frame),
+// -inf outside its grid or without one
+__device__ __forceinline__ float voxel_bound(const DevGeom& g, int p, float x, float y,
+                                             float z) {
+  if (!g.voxels || p >= g.n_voxels) return -INFINITY;
+  const VoxelRec v = g.voxels[p];
+  if (v.dims.x == 0) return -INFINITY;
+  const float ih = 1.0f / v.grid.w;
+  const float tx = (x - v.grid.x) * ih, ty = (y - v.grid.y) * ih, tz = (z - v.grid.z) * ih;
+  if (!(tx >= 0.f && ty >= 0.f && tz >= 0.f && tx < (float)v.dims.x && ty < (float)v.dims.y &&
+        tz < (float)v.dims.z))
+    return -INFINITY;
+  const int ix = (int)tx, iy = (int)ty, iz = (int)tz;
+  return __ldg(g.voxel_vals + v.dims.w + (ix * v.dims.y + iy) * v.dims.z + iz);
+}
 
 // Tricubic spline SDF of a piece (Sec. 3.2): grid origin and voxel size, and
 // the voxel counts with the first of its (nx+3)(ny+3)(nz+3) coefficient rows

@@ -66,10 +66,15 @@ struct FwdCounts {
 // Narrow phase of the live directions sl.dsub[0..nd) whose vertex / edge items
 // are numbered by the exclusive prefixes sl.pv / sl.pe (totals TV, TE).
 template <bool kCount>
-__device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, int TE, int sc0,
-                         const KParams& kp, bool no_cull, int lane, FwdCounts& cnt,
-                         const ContactList& cl, const ChunkRef& cr) {
+__device__ void run_list(const DevGeom& g, const UnitSlice& sl, const int* dsub, int nd, int TV,
+                         int TE, int sc0, const KParams& kp, bool no_cull, int lane,
+                         FwdCounts& cnt, const ContactList& cl, const ChunkRef& cr) {
   const bool project = (kp.flags & CCM_FLAG_PROJECT) != 0u;
+  const bool voxel = (kp.flags & CCM_FLAG_VOXEL_CULL) != 0u && !no_cull;
+  // Sec. 4.3 voxel-grid broad phase (with CCM_FLAG_VOXEL_CULL): a vertex whose
+  // voxel's lower bound of the SDF is >= d_max is culled without a plane
+  // scan; it keeps the one plane value below as its (valid, lower) max-plane
+  // bound for the edge cull and marks its plane index with kVoxCulled.
   // max-plane value of every (direction, vertex) item.  First one plane: the
   // plane attaining the max at the feature piece's centre (from the gate) is
   // far above d_max at the vertices on the far side of the piece, and its
@@ -90,9 +95,16 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       const float4 pj = sl.planes[s.x + j];
       const float vj = fmaf(pj.x, x.x, fmaf(pj.y, x.y, fmaf(pj.z, x.z, pj.w)));
       sl.need[t] = 0;
+      const float vb = voxel ? voxel_bound(g, cr.spiece + sc0 + (code & 0xffff), x.x, x.y, x.z)
+                             : -INFINITY;
+      sl.vb[t] = vb;
       if (!no_cull && vj >= kp.d_max) {
         sl.m[t] = vj;
         sl.am[t] = (uint16_t)j;
+        if (kCount) cnt.maxp += 1;
+      } else if (vb - kVoxTol >= kp.d_max) {
+        sl.m[t] = vj;
+        sl.am[t] = (uint16_t)(j | kVoxCulled);
         if (kCount) cnt.maxp += 1;
       } else {
         full = true;
@@ -131,9 +143,14 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       const int i0 = e & 0xffff, i1 = e >> 16;
       const int t0v = sl.pv[r] + i0, t1v = sl.pv[r] + i1;
       const float4 a = sl.xs[f.x + i0], b = sl.xs[f.x + i1];
-      const float lb = edge_plane_bound(sl.planes[s.x + sl.am[t0v]], sl.planes[s.x + sl.am[t1v]],
-                                        b.x - a.x, b.y - a.y, b.z - a.z, sl.m[t0v], sl.m[t1v]);
-      live = no_cull || lb - kEdgeTol < kp.d_max;
+      const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+      const float lb = edge_plane_bound(sl.planes[s.x + (sl.am[t0v] & kPlaneMask)],
+                                        sl.planes[s.x + (sl.am[t1v] & kPlaneMask)], dx, dy, dz,
+                                        sl.m[t0v], sl.m[t1v]);
+      // Sec. 4.3 voxel edge bound: min(phi_1, phi_2) - r - l (r inside vb)
+      const float vlb = fminf(sl.vb[t0v], sl.vb[t1v]) -
+                        sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      live = no_cull || (lb - kEdgeTol < kp.d_max && vlb - kVoxTol < kp.d_max);
       if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
     }
     const unsigned bal = __ballot_sync(kFull, live);
@@ -144,7 +161,15 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
   int n_v = 0;
   for (int t0 = 0; t0 < TV; t0 += 32) {
     const int t = t0 + lane;
-    const bool live = t < TV && (no_cull || sl.m[t] < kp.d_max || sl.need[t]);
+    bool live = false;
+    if (t < TV) {
+      if (sl.am[t] & kVoxCulled) {
+        // from here on m is only a lower bound (the SDF shift and the contact
+        // test): the voxel bound lifts it to >= d_max, so no contact is made
+        sl.m[t] = fmaxf(sl.m[t], sl.vb[t]);
+      }
+      live = no_cull || sl.m[t] < kp.d_max || sl.need[t];
+    }
     const unsigned bal = __ballot_sync(kFull, live);
     if (live) sl.vlist[n_v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
     n_v += __popc(bal);
@@ -167,17 +192,17 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
       feat = t - sl.pv[r];
       const float4 x = sl.xs[f.x + feat];
       const float m = sl.m[t];
-      const SdfGrad g = sdf_grad(sl.planes + s.x, s.y, x.x, x.y, x.z, m, kp);
-      sl.phi[t] = g.phi;
+      const SdfGrad sg = sdf_grad(sl.planes + s.x, s.y, x.x, x.y, x.z, m, kp);
+      sl.phi[t] = sg.phi;
       key = code >> 16;
       s_glob = cr.spiece + sc0 + (code & 0xffff);
       if (no_cull || m < kp.d_max) {
-        const float w = transition(g.phi, kp);
-        const float dc = fmaf(w, g.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
+        const float w = transition(sg.phi, kp);
+        const float dc = fmaf(w, sg.phi - kp.d_max, kp.d_max);   // f phi + (1 - f) d_max
         float3 p = make_float3(x.x, x.y, x.z);
-        if (project) p = make_float3(fmaf(-g.phi, g.gx, p.x), fmaf(-g.phi, g.gy, p.y),
-                                     fmaf(-g.phi, g.gz, p.z));   // Sec. 4.1 projection
-        part_from_contact(c, w, dc, v3(p.x, p.y, p.z), v3(g.gx, g.gy, g.gz), kp.c_blend);
+        if (project) p = make_float3(fmaf(-sg.phi, sg.gx, p.x), fmaf(-sg.phi, sg.gy, p.y),
+                                     fmaf(-sg.phi, sg.gz, p.z));   // Sec. 4.1 projection
+        part_from_contact(c, w, dc, v3(p.x, p.y, p.z), v3(sg.gx, sg.gy, sg.gz), kp.c_blend);
         mark_hit(sl.hit, sl.hw, code >> 16, sc0 + (code & 0xffff), w);
         contrib = w > 0.f;
         if (kCount) cnt.con += w > 0.f;
@@ -233,9 +258,9 @@ __device__ void run_list(const UnitSlice& sl, const int* dsub, int nd, int TV, i
 // Splits the pending directions sl.dir[0..np) into lists that fit the item
 // budgets and runs each.
 template <bool kCount>
-__device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, const UnitShape& us,
-                           const KParams& kp, bool no_cull, int lane, FwdCounts& cnt,
-                           const ContactList& cl, const ChunkRef& cr) {
+__device__ void run_pending(const DevGeom& g, const UnitSlice& sl, int* dsub, int np, int sc0,
+                           const UnitShape& us, const KParams& kp, bool no_cull, int lane,
+                           FwdCounts& cnt, const ContactList& cl, const ChunkRef& cr) {
   int start = 0;
   while (start < np) {
     const int r = start + lane;
@@ -264,7 +289,7 @@ __device__ void run_pending(const UnitSlice& sl, int* dsub, int np, int sc0, con
     }
     const int TV = __shfl_sync(kFull, iv, nd - 1), TE = __shfl_sync(kFull, ie, nd - 1);
     __syncwarp();
-    run_list<kCount>(sl, dsub, nd, TV, TE, sc0, kp, no_cull, lane, cnt, cl, cr);
+    run_list<kCount>(g, sl, dsub, nd, TV, TE, sc0, kp, no_cull, lane, cnt, cl, cr);
     start += nd;
   }
 }
@@ -412,7 +437,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           const unsigned bal = __ballot_sync(kFull, live);
           const int nl = __popc(bal);
           if (np + nl > kPending) {
-            run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
+            run_pending<kCount>(g, sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
             np = 0;
           }
           if (live) {
@@ -423,7 +448,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
           np += nl;
           __syncwarp();
         }
-        if (np > 0) run_pending<kCount>(sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
+        if (np > 0) run_pending<kCount>(g, sl, dsub, np, sc0, us, kp, no_cull, lane, cnt, cl, cr);
         sc0 = sc1;
       }
       __syncwarp();

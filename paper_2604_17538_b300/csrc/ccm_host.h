@@ -44,6 +44,10 @@ struct Context {
   std::vector<SplineRec> splines;
   std::vector<float4> spline_coef;
   DevBuf d_splines, d_spline_coef;
+  // broad-phase voxel grids (ccm_build_voxel_grids): one record per piece
+  // loaded when they were built
+  DevBuf d_voxels, d_voxel_vals;
+  int64_t n_voxels = 0;
   Serving* serving = nullptr;
 
   DevGeom dev_geom() const;

@@ -63,6 +63,7 @@ struct UnitSlice {
   uint16_t* vlist;    // [item_v] surviving vertex items
   uint16_t* elist;    // [item_e] surviving edge items
   uint8_t* need;      // [item_v]
+  float* vb;          // [item_v] voxel-grid lower bound of the SDF per (direction, vertex)
   uint16_t* am;       // [item_v] a plane attaining the max-plane value (until the
                       // edge cull, in phi's space)
   int* gcnt;          // [2 groups] contacts of non-zero weight per group (vertex,
@@ -73,6 +74,11 @@ struct UnitSlice {
 // Rounding allowance of the edge cull's plane bound (coordinates are O(1) in
 // the SDF frame, so float rounding of the bound is ~1e-7).
 constexpr float kEdgeTol = 1e-5f;
+// Voxel-grid culls: the same allowance, and the flag in a vertex item's
+// plane index that says the grid culled it (plane indices are < 1024).
+constexpr float kVoxTol = 1e-5f;
+constexpr uint16_t kVoxCulled = 0x8000;
+constexpr uint16_t kPlaneMask = 0x7fff;
 
 __host__ __device__ inline int align16i(int b) { return (b + 15) & ~15; }
 
@@ -92,6 +98,7 @@ __host__ __device__ inline int unit_slice_bytes(const UnitShape& u) {
   b += align16i(2 * u.item_v);               // vlist
   b += align16i(2 * u.item_e);               // elist
   b += align16i(u.item_v);                   // need
+  b += align16i(4 * u.item_v);               // vb
   b += align16i(8 * u.groups);               // gcnt
   b += 16;                                   // mbar
   return b;
@@ -119,6 +126,7 @@ __device__ inline UnitSlice unit_slice(unsigned char* p, const UnitShape& u) {
   s.vlist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_v);
   s.elist = reinterpret_cast<uint16_t*>(p);          p += align16i(2 * u.item_e);
   s.need = reinterpret_cast<uint8_t*>(p);             p += align16i(u.item_v);
+  s.vb = reinterpret_cast<float*>(p);                 p += align16i(4 * u.item_v);
   s.gcnt = reinterpret_cast<int*>(p);               p += align16i(8 * u.groups);
   s.mbar = reinterpret_cast<uint64_t*>(p);
   s.am = reinterpret_cast<uint16_t*>(s.phi);
