@@ -4,7 +4,8 @@ times, on sampled outputs the oracle recomputes pair by pair:
 * the 4096-environment step: 4096 pairs of two 8-piece bodies (seed 2), default
   launch shape, the forward keeping its record, then the gradient pass and the
   H u / J u pass running concurrently on two streams -- its derivatives also
-  against central differences (h = 1e-5, FP64) on 256 sampled environments;
+  against central differences (h = 1e-4, FP64) on the sampled environments
+  not flagged near a transition knot;
 * the uneven batch: 65,536 body pairs (seed 4), autotuned shape, forward and
   gradient from the record.
 
@@ -140,21 +141,39 @@ def _moved(sc, xi):
     return out
 
 
+def _knot_flags(oracle_lib, sub, hstep, d_max=D_MAX, eps=0.01):
+    """Per pair: True where some contact's SDF value lies within 3 h (lever
+    arm) of a knot of the transition (d_max - eps or d_max).  A step of h in
+    the twist chart moves a contact's SDF by at most h times the lever arm
+    (1 + the largest vertex norm + the distance between the bodies); within
+    that of a knot the loss's third derivative jumps and a central difference
+    of step h is not accurate to its own truncation order."""
+    flags = np.zeros(sub.n_pairs, bool)
+    vmax = float(np.linalg.norm(sub.geom.verts, axis=1).max())
+    for i in range(sub.n_pairs):
+        phi = oracle_lib.pair_contacts(sub, i)[:, 1]
+        lever = 1.0 + vmax + float(np.linalg.norm(sub.pose_a[i, 9:] - sub.pose_b[i, 9:]))
+        win = 3.0 * hstep * lever
+        flags[i] = bool(np.any(np.abs(phi - (d_max - eps)) < win) or
+                        np.any(np.abs(phi - d_max) < win))
+    return flags
+
+
 def test_hull_4096_derivatives_against_central_differences(oracle_lib, hull_step):
     """Gradient and H u of the bench step on 256 sampled environments against
-    central differences in FP64: of L = <ybar, y> along each twist coordinate
-    for the gradient, and of the fixed-chart gradient along +-h u for H u.
-
-    The step is h = 1e-5.  At h = 1e-4 the truncation error is not small next
-    to every pair's gradient: with softness 5e-3 a grazing pair's loss bends
-    on a scale below 1e-4, and there the difference misses even the FP64
-    oracle's analytic derivative by more than the derivative itself.  At
-    1e-5 it stays within 1e-4 (gradient) and 3e-4 (H u) of it on this sample,
-    so the bar adds a 1e-3 allowance to the oracle-parity bar."""
+    central differences in FP64 with the step the 4096-environment
+    differentiation workload names, h = 1e-4: of L = <ybar, y> along each
+    twist coordinate for the gradient, and of the fixed-chart gradient along
+    +-h u for H u.  Environments with a contact within 3 h (lever arm) of a
+    transition knot are flagged and left out; the others are held to the
+    parity bar itself, with no allowance for the differences."""
     sc, ybar, u = hull_step["sc"], hull_step["ybar"], hull_step["u"]
     g, h = hull_step["g"], hull_step["h"]
-    hstep = 1e-5
-    idx = np.sort(np.random.default_rng(23).choice(sc.n_pairs, 256, replace=False))
+    hstep = 1e-4
+    idx0 = np.sort(np.random.default_rng(23).choice(sc.n_pairs, 256, replace=False))
+    flags = _knot_flags(oracle_lib, sc.take(idx0), hstep)
+    idx = idx0[~flags]
+    assert len(idx) >= 64, int(flags.sum())
     sub = sc.take(idx)
     rows = _rows(sc.group_offsets(), idx)
     yb_s, u_s = ybar[rows].astype(np.float64), u[idx].astype(np.float64)
@@ -173,8 +192,10 @@ def test_hull_4096_derivatives_against_central_differences(oracle_lib, hull_step
     gm, _ = oracle_lib.gradient(sub, yb_s, xi=-hstep * u_s)
     fd_h = (gp - gm) / (2 * hstep)
     kg, kh = fp32_sensitivity(oracle_lib, sub, ybar[rows], u[idx])
-    _check_pairs(g[idx], fd_g, np.maximum(GRAD_RTOL, COND_FACTOR * kg) + 1e-3, "gradient vs FD")
-    _check_pairs(h[idx], fd_h, np.maximum(GRAD_RTOL, COND_FACTOR * kh) + 1e-3, "H u vs FD")
+    print(f"central differences at h = {hstep}: {int(flags.sum())} of {len(idx0)} "
+          "environments flagged near a transition knot")
+    _check_pairs(g[idx], fd_g, np.maximum(GRAD_RTOL, COND_FACTOR * kg), "gradient vs FD (h=1e-4)")
+    _check_pairs(h[idx], fd_h, np.maximum(GRAD_RTOL, COND_FACTOR * kh), "H u vs FD (h=1e-4)")
     assert np.abs(fd_g).max() > 0 and np.abs(fd_h).max() > 0
 
 
