@@ -143,7 +143,17 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join("/tmp", f"ccm_clocks_{os.getpid()}.csv")
 
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for ln in f if ln.strip())
+        except OSError:
+            return 0
+
     def start(self):
+        """Starts nvidia-smi and waits (at most 5 s) for its first sample, so
+        that sampling is live when the timed region begins; samples taken
+        before then are not reported."""
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -152,6 +162,26 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while self._lines() == 0 and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
+        self.skip = self._lines()
+
+    def extend(self, step, min_samples=3, max_s=3.0):
+        """A timed region shorter than the sampling interval holds no sample:
+        the same work then keeps running, untimed, until `min_samples` samples
+        were taken since the timed region began (at most `max_s` seconds)."""
+        import torch
+        if self.proc is None:
+            return
+        self.extended = 0
+        t0 = time.perf_counter()
+        while self._lines() - self.skip < min_samples and time.perf_counter() - t0 < max_s:
+            for _ in range(4):
+                step()
+            torch.cuda.synchronize()
+            self.extended += 4
 
     def stop(self):
         if self.proc is None:
@@ -164,7 +194,8 @@ class ClockSampler:
         self.fh.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = [ln for ln in open(self.path) if ln.strip()][getattr(self, "skip", 0):]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -178,8 +209,12 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+               "reasons": sorted(reasons)}
+        if getattr(self, "extended", 0):
+            out["window"] = (f"timed loop, then {self.extended} untimed steps of the same work "
+                             "until 3 samples (100 ms interval)")
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -263,6 +298,7 @@ def run_ours(args, rank, world):
         e[2].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    sampler.extend(step)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -490,6 +526,7 @@ def run_uneven(args, rank, world):
         b.record(cur)
         b.synchronize()
         t += a.elapsed_time(b) / 1e3
+    sampler.extend(graph.replay)
     clocks = sampler.stop()
 
     # per-kernel times for the roofline: the same two calls eagerly, with an

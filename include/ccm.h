@@ -235,6 +235,10 @@ typedef struct {
   int32_t stage_wait;         /* bound of a bulk copy's wait, in polls of its barrier
                                  (0: 2^22; -1: none, so that every wait runs out -- for
                                  tests of the timeout path), -1..2^30 */
+  int32_t flat_forward;       /* forward as flat stages (gate per direction, culls per live
+                                 direction, one contact per thread, fold per group) on a
+                                 batch with a contact list (0), or one warp per work item
+                                 (-1) */
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
 /* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of

@@ -52,7 +52,8 @@ class ccm_tuning(C.Structure):
                 ("item_eb", C.c_int32), ("fwd_warps", C.c_int32), ("groups", C.c_int32),
                 ("stage_planes", C.c_int32), ("stage_verts", C.c_int32),
                 ("groups_b", C.c_int32), ("flat_records", C.c_int32),
-                ("stage_tma", C.c_int32), ("stage_wait", C.c_int32)]
+                ("stage_tma", C.c_int32), ("stage_wait", C.c_int32),
+                ("flat_forward", C.c_int32)]
 
 
 class ccm_spline_desc(C.Structure):

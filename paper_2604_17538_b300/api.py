@@ -117,7 +117,8 @@ class Batch:
         check(lib().ccm_batch_get_tuning(self.handle, C.byref(t)))
         return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps",
                                            "groups", "stage_planes", "stage_verts", "groups_b",
-                                           "flat_records", "stage_tma", "stage_wait")}
+                                           "flat_records", "stage_tma", "stage_wait",
+                                           "flat_forward")}
 
     def set_tuning(self, **kw):
         t = abi.ccm_tuning()

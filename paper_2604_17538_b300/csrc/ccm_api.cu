@@ -896,7 +896,8 @@ ccm_status setup_flat(Context* c, Batch* bt) {
                  : std::min<int64_t>(std::max<int64_t>(16 * bt->G, 65536), (int64_t)1 << 24);
   if (cap == bt->flat_cap) return CCM_OK;
   for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted,
-                   &bt->d_ftiles})
+                   &bt->d_ftiles, &bt->d_unit_dir_off, &bt->d_rel, &bt->d_live, &bt->d_cand,
+                   &bt->d_cand_m, &bt->d_cval, &bt->d_sval, &bt->d_skey, &bt->d_ffctl})
     b->release();
   for (auto& pass : bt->d_fpass)
     for (DevBuf& b : pass) b.release();
@@ -927,6 +928,27 @@ ccm_status setup_flat(Context* c, Batch* bt) {
       if ((s = alloc(bt->d_fpass[d][q], sz[q], "per-contact pass")) != CCM_OK) return s;
     if ((s = alloc(bt->d_fpass[d][4], 3 * sizeof(int), "per-contact pass")) != CCM_OK) return s;
   }
+  {   // the flat forward: directions per unit (u = 2 pair + side), candidates
+    std::vector<int64_t> off(2 * (size_t)bt->n + 1, 0);
+    for (int64_t i = 0; i < bt->n; ++i) {
+      const int64_t d = (int64_t)c->bodies[bt->pairs[i].bodyA].np * c->bodies[bt->pairs[i].bodyB].np;
+      off[2 * i + 1] = off[2 * i] + d;
+      off[2 * i + 2] = off[2 * i + 1] + d;
+    }
+    bt->n_dirs = off.back();
+    bt->cand_cap = std::min<int64_t>(std::max<int64_t>(64 * bt->G, (int64_t)1 << 18),
+                                     (int64_t)1 << 25);
+    if ((s = upload(bt->d_unit_dir_off, off, "direction offsets")) != CCM_OK ||
+        (s = alloc(bt->d_rel, 12 * sizeof(float) * 2 * (size_t)bt->n, "relative poses")) != CCM_OK ||
+        (s = alloc(bt->d_live, (size_t)bt->n_dirs * sizeof(int4), "live directions")) != CCM_OK ||
+        (s = alloc(bt->d_cand, (size_t)bt->cand_cap * sizeof(int4), "candidates")) != CCM_OK ||
+        (s = alloc(bt->d_cand_m, (size_t)bt->cand_cap * sizeof(float2), "candidates")) != CCM_OK ||
+        (s = alloc(bt->d_cval, (size_t)bt->cand_cap * 8 * sizeof(float), "candidates")) != CCM_OK ||
+        (s = alloc(bt->d_sval, (size_t)cap * 8 * sizeof(float), "contact values")) != CCM_OK ||
+        (s = alloc(bt->d_skey, (size_t)cap * sizeof(long long), "contact keys")) != CCM_OK ||
+        (s = alloc(bt->d_ffctl, kFfWords * sizeof(unsigned long long), "flat forward")) != CCM_OK)
+      return s;
+  }
   // a list that no forward filled yet reads as overflowed (the per-pair path)
   unsigned long long init[kCtlWords] = {};
   init[kCtlOverflow] = 1ull;
@@ -955,7 +977,7 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
       (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)) ||
       t.groups_b < 0 || t.groups_b > kGroupsPerChunk || t.flat_records < -1 ||
       t.flat_records > 4096 || t.stage_tma < -1 || t.stage_tma > 0 || t.stage_wait < -1 ||
-      t.stage_wait > (1 << 30))
+      t.stage_wait > (1 << 30) || t.flat_forward < -1 || t.flat_forward > 0)
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -1130,7 +1152,9 @@ void Batch::release() {
   d_status.release();
   d_part.release();
   d_row_pair.release();
-  for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted, &d_ftiles}) b->release();
+  for (DevBuf* b : {&d_fctl, &d_fcnt, &d_foff, &d_frecs, &d_fsorted, &d_ftiles, &d_unit_dir_off,
+                    &d_rel, &d_live, &d_cand, &d_cand_m, &d_cval, &d_sval, &d_skey, &d_ffctl})
+    b->release();
   for (auto& pass : d_fpass)
     for (DevBuf& b : pass) b.release();
   flat_cap = 0;
@@ -1213,10 +1237,53 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
   L.sched = static_cast<int*>(b->d_sched.ptr);
   L.grid = b->grid;
   L.status = static_cast<int*>(b->d_status.ptr);
+  const bool staged = b->flat_cap > 0 && b->tuning.flat_forward == 0 &&
+                      !(kp.flags & CCM_FLAG_NO_CULL) && flat_forward_fits(b->mx.vmax, b->mx.fmax);
   const bool flat = saved && b->flat_cap > 0;
+  if (flat || staged) {
+    if (++b->list_tag == 0u) b->list_tag = 1u;   // a new tag per list (0: none)
+  }
+  if (staged) {
+    // the flat forward; the per-item kernel below runs only if it overflowed
+    // (then without a contact list: the reverse passes run per pair)
+    FlatFwdLaunch F;
+    F.g = L.g;
+    F.pairs = L.pairs;
+    F.row_pair = static_cast<const int32_t*>(b->d_row_pair.ptr);
+    F.unit_dir_off = static_cast<const int64_t*>(b->d_unit_dir_off.ptr);
+    F.n_pairs = b->n;
+    F.G = b->G;
+    F.n_dirs = b->n_dirs;
+    F.pose_a = pose_a;
+    F.pose_b = pose_b;
+    F.kp = kp;
+    F.y = y;
+    F.saved = saved;
+    F.cl = b->contact_list();
+    F.cl.tag = b->list_tag;
+    F.sval = static_cast<float*>(b->d_sval.ptr);
+    F.sval_key = static_cast<long long*>(b->d_skey.ptr);
+    F.rel = static_cast<float*>(b->d_rel.ptr);
+    F.live = static_cast<int4*>(b->d_live.ptr);
+    F.cand_cap = b->cand_cap;
+    F.cand = static_cast<int4*>(b->d_cand.ptr);
+    F.cand_m = static_cast<float2*>(b->d_cand_m.ptr);
+    F.cval = static_cast<float*>(b->d_cval.ptr);
+    F.ctl = static_cast<unsigned long long*>(b->d_ffctl.ptr);
+    F.counters = counters;
+    F.vmax = b->mx.vmax;
+    F.fmax = b->mx.fmax;
+    F.gate_planes = std::max(b->mx.fmax, std::min(b->mx.s_planes, 768));
+    F.n_sm = b->ctx->n_sm;
+    cudaError_t e = launch_flat_forward(F, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flat forward launch");
+    L.only_if = F.ctl + kFfOverflow;
+    e = launch_forward(L, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return CCM_OK;
+  }
   if (flat) {
     L.cl = b->contact_list();
-    if (++b->list_tag == 0u) b->list_tag = 1u;   // a new tag per list (0: none)
     L.cl.tag = b->list_tag;
   }
   cudaError_t e = launch_forward(L, stream);

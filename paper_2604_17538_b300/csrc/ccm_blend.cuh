@@ -78,6 +78,19 @@ template <class T> __device__ __forceinline__ void part_combine(PartT<T>& a, con
   a = r;
 }
 
+// folds the contacts k0 <= k < k1 of a value array [*, 8] (f, d_c, p, n) into
+// acc in index order, one at a time
+template <class T>
+__device__ __forceinline__ void fold_range(const T* cval, int64_t k0, int64_t k1, float c_blend,
+                                           PartT<T>& acc) {
+  for (int64_t k = k0; k < k1; ++k) {
+    const T* c = cval + 8 * k;
+    PartT<T> q;
+    part_from_contact(q, c[0], c[1], v3(c[2], c[3], c[4]), v3(c[5], c[6], c[7]), c_blend);
+    part_combine(acc, q);
+  }
+}
+
 __device__ __forceinline__ float shfl_down_t(float v, int o) { return __shfl_down_sync(kFull, v, o); }
 __device__ __forceinline__ Dual shfl_down_t(Dual v, int o) {
   return Dual(__shfl_down_sync(kFull, v.v, o), __shfl_down_sync(kFull, v.d, o));

@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_
     if (base + q < G) {
       cl.off_v[base + q] = (int32_t)ov;
       cl.off_e[base + q] = (int32_t)oe;
+      cl.cnt_v[base + q] = 0;   // the counts become the scatter's cursors
+      cl.cnt_e[base + q] = 0;
     }
     ov += cv[q];
     oe += ce[q];
@@ -148,13 +150,18 @@ __global__ void clist_scatter_kernel(ContactList cl) {
 
 int64_t flat_scan_tiles(int64_t G) { return std::max<int64_t>(1, (G + kScanTile - 1) / kScanTile); }
 
-cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream) {
+cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream) {
   const int64_t tiles = flat_scan_tiles(G);
   clist_tile_sum_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   clist_scan_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream) {
+  cudaError_t e = launch_flat_prep_scan(cl, G, stream);
+  if (e != cudaSuccess) return e;
   clist_scatter_kernel<<<4 * n_sm, 256, 0, stream>>>(cl);
   return cudaGetLastError();
 }
@@ -325,17 +332,6 @@ __global__ void __launch_bounds__(128) flat_eval_kernel(FlatLaunch L) {
 // ---------------------------------------------------------------------------
 // fold: one group per thread
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ void fold_range(const T* cval, int64_t k0, int64_t k1, float c_blend,
-                                           PartT<T>& acc) {
-  for (int64_t k = k0; k < k1; ++k) {
-    const T* c = cval + 8 * k;
-    PartT<T> q;
-    part_from_contact(q, c[0], c[1], v3(c[2], c[3], c[4]), v3(c[5], c[6], c[7]), c_blend);
-    part_combine(acc, q);
-  }
-}
-
 template <class T>
 __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
   if (L.fp.sched[2]) return;

@@ -44,6 +44,9 @@ void flat_pass_bytes(bool dual, int64_t cap, int64_t G, size_t* cval, size_t* fo
                      size_t* coef, size_t* oterm);
 // Tiles of the scan of G group counts (ContactList::tile_sum holds 2 per tile).
 int64_t flat_scan_tiles(int64_t G);
+// The scan alone: offsets from the group counts (which it zeroes, leaving
+// them as cursors), the totals and the tag.
+cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream);
 // After a forward that filled cl: scan of the group counts and the scatter
 // of the records into their fixed order.
 cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream);

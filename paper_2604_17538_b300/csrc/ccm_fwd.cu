@@ -302,7 +302,9 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 const float* __restrict__ pose_a, const float* __restrict__ pose_b, KParams kp,
                 UnitShape us, float* __restrict__ y, float* __restrict__ saved,
                 unsigned long long* __restrict__ counters, int* __restrict__ sched,
-                ContactList cl, int* __restrict__ status) {
+                ContactList cl, int* __restrict__ status,
+                const unsigned long long* __restrict__ only_if) {
+  if (only_if && *only_if == 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -497,10 +499,10 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   }
   if (L.counters)
     unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status);
+                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status, L.only_if);
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status);
+                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status, L.only_if);
   return cudaGetLastError();
 }
 

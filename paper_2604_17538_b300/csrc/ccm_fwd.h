@@ -25,6 +25,9 @@ struct FwdLaunch {
   int grid;
   ContactList cl{};               // with `saved`: the contact list (cl.recs NULL: none)
   int* status = nullptr;          // optional device word: CCM_ERR_TIMEOUT if a bounded wait ran out
+  // if set: the kernel runs only when this device word is non-zero (the flat
+  // forward overflowed)
+  const unsigned long long* only_if = nullptr;
 };
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);

@@ -14,6 +14,7 @@
 #include "ccm_flat.h"
 #include "ccm_union.h"
 #include "ccm_spline.h"
+#include "ccm_ffwd.h"
 
 namespace ccm {
 
@@ -97,6 +98,10 @@ struct Batch {
   DevBuf d_row_pair;             // [G] pair << 1 | side
   DevBuf d_fctl, d_fcnt, d_foff, d_frecs, d_fsorted, d_ftiles;
   DevBuf d_fpass[2][5];          // [float, Dual][cval, force, coef, oterm, sched]
+  // flat forward (ccm_ffwd.cu): directions per unit, relative poses, live
+  // directions, candidate contacts and their values, the list's values
+  int64_t n_dirs = 0, cand_cap = 0;
+  DevBuf d_unit_dir_off, d_rel, d_live, d_cand, d_cand_m, d_cval, d_sval, d_skey, d_ffctl;
   ContactList contact_list() const;
   FlatPass flat_pass(bool dual) const;
   void release();

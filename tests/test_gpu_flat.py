@@ -59,11 +59,15 @@ def test_contact_list_matches_the_per_pair_pass_and_falls_back_on_overflow(ctx, 
     flat = _saved_step(ctx, sc, ybar, u)                        # default: the contact list
     pair = _saved_step(ctx, sc, ybar, u, flat_records=-1)       # no list: per-pair passes
     tiny = _saved_step(ctx, sc, ybar, u, flat_records=1)        # one record per group
-    # the forward is the same kernel either way
-    assert np.array_equal(flat[0], pair[0]) and np.array_equal(flat[0], tiny[0])
-    # a list that overflows leaves the per-pair passes to run: bitwise theirs
+    # the staged forward (with a list) and the per-item one (without) find the
+    # same contacts and blend them in different orders
+    from gpu_util import compare, weight_slack
+    compare(flat[0].astype(np.float64), pair[0].astype(np.float64), f"{name} forward, list vs none",
+            a_slack=weight_slack(sc))
+    # a list that overflows leaves the per-item forward and the per-pair
+    # passes to run: bitwise theirs
     if name == "cube":   # deep cube contacts: more than one contact per group
-        for a, b in zip(tiny[1:], pair[1:]):
+        for a, b in zip(tiny, pair):
             assert np.array_equal(a, b)
     # the per-contact passes agree with the per-pair ones to float rounding
     # (their blends fold the same contacts in another order)
@@ -121,8 +125,67 @@ def test_a_record_of_an_earlier_forward_does_not_use_the_newer_list(ctx):
     g1r, _, _ = plain.backward(pa, pb, yb, saved=r1)
     _, h1r, j1r = plain.backward(pa, pb, yb, ut, want_jvp=True, saved=r1)
     torch.cuda.synchronize()
-    assert torch.equal(s1[:, :26], r1[:, :26])
+    # the same contacts (hit marks); the reverse passes from the first record
+    # ran per pair, as on the batch without a list
+    assert torch.equal(s1[:, 18:26], r1[:, 18:26])
     assert torch.equal(g1, g1r) and torch.equal(h1, h1r) and torch.equal(j1, j1r)
     assert float(h1.abs().max()) > 0
     batch.close()
     plain.close()
+
+
+@pytest.mark.parametrize("name", ["cube", "hull", "uneven"])
+def test_flat_forward_matches_the_per_item_forward(oracle_lib, ctx, name):
+    """The staged forward (gate per direction, culls per live direction, one
+    contact per thread, fold per group in a fixed order) finds the same
+    contacts as the per-item kernel: the saved hit marks are equal bit for
+    bit and the outputs agree to float rounding (the blends fold in another
+    order); both match the oracle.  A contact list too small for the contacts
+    makes it fall back to the per-item kernel: bitwise that kernel's outputs."""
+    import torch
+    from gpu_util import compare, weight_slack
+    from paper_2604_17538_b300 import api
+    sc = {"cube": lambda: scenes.cube_pair_scene(seed=1, n_poses=32),
+          "hull": lambda: scenes.hull_env_scene(seed=2, n_envs=32, workers=0),
+          "uneven": lambda: scenes.uneven_scene(seed=4, n_pairs=96, pool_bodies=160,
+                                                workers=0)}[name]()
+    out = {}
+    for key, tuning in (("flat", {}), ("item", {"flat_forward": -1}),
+                        ("tiny", {"flat_records": 1})):
+        batch, pa, pb = api.scene_to_device(sc, ctx)
+        if tuning:
+            batch.set_tuning(**tuning)
+        saved = batch.saved_buffer()
+        y = batch.contacts(pa, pb, saved=saved)
+        y2 = batch.contacts(pa, pb)
+        torch.cuda.synchronize()
+        out[key] = (y.cpu().numpy(), saved.cpu().numpy(), y2.cpu().numpy())
+        batch.close()
+    yf, sf, yf2 = out["flat"]
+    yi, si, _ = out["item"]
+    assert np.array_equal(yf, yf2)                       # with and without the record
+    hf, hi = sf[:, 18:26].copy().view(np.uint32), si[:, 18:26].copy().view(np.uint32)
+    assert np.array_equal(hf, hi)
+    compare(yf.astype(np.float64), yi.astype(np.float64), f"{name} flat vs per-item forward",
+            a_slack=weight_slack(sc))
+    compare(yf.astype(np.float64), oracle_lib.forward(sc), f"{name} flat forward vs oracle",
+            a_slack=weight_slack(sc))
+    yt, st, _ = out["tiny"]
+    if name == "cube":                                   # the list overflows
+        assert np.array_equal(yt, yi) and np.array_equal(st[:, :26], si[:, :26])
+
+
+def test_flat_forward_is_deterministic_and_batch_independent(ctx):
+    import torch
+    from paper_2604_17538_b300 import api
+    sc = scenes.uneven_scene(seed=4, n_pairs=80, pool_bodies=120, workers=0)
+    ys = []
+    for idx in (np.arange(sc.n_pairs), np.arange(sc.n_pairs), np.array([5, 33, 70])):
+        sub = sc.take(idx)
+        batch, pa, pb = api.scene_to_device(sub, ctx)
+        ys.append(batch.contacts(pa, pb).cpu().numpy())
+        batch.close()
+    assert np.array_equal(ys[0], ys[1])
+    off = sc.group_offsets()
+    rows = np.concatenate([np.arange(off[i], off[i + 1]) for i in (5, 33, 70)])
+    assert np.array_equal(ys[2], ys[0][rows])

@@ -4,8 +4,8 @@ times, on sampled outputs the oracle recomputes pair by pair:
 * the 4096-environment step: 4096 pairs of two 8-piece bodies (seed 2), default
   launch shape, the forward keeping its record, then the gradient pass and the
   H u / J u pass running concurrently on two streams -- its derivatives also
-  against central differences (h = 1e-4, FP64) on the sampled environments
-  not flagged near a transition knot;
+  against central differences (h = 1e-4 and h/2, FP64, Richardson-combined)
+  on the sampled environments not flagged near a transition knot;
 * the uneven batch: 65,536 body pairs (seed 4), autotuned shape, forward and
   gradient from the record.
 
@@ -162,11 +162,19 @@ def _knot_flags(oracle_lib, sub, hstep, d_max=D_MAX, eps=0.01):
 def test_hull_4096_derivatives_against_central_differences(oracle_lib, hull_step):
     """Gradient and H u of the bench step on 256 sampled environments against
     central differences in FP64 with the step the 4096-environment
-    differentiation workload names, h = 1e-4: of L = <ybar, y> along each
+    differentiation workload names, h = 1e-4, of L = <ybar, y> along each
     twist coordinate for the gradient, and of the fixed-chart gradient along
     +-h u for H u.  Environments with a contact within 3 h (lever arm) of a
-    transition knot are flagged and left out; the others are held to the
-    parity bar itself, with no allowance for the differences."""
+    transition knot are flagged and left out.
+
+    A central difference of step h is off by c h^2 + O(h^4): the mollifier's
+    curvature makes c large enough that at h = 1e-4 a few environments sit
+    above the 1e-3 bar on the truncation alone (the FP64 analytic gradient
+    misses them the same way).  So the differences at h and h/2 are combined
+    by Richardson extrapolation, (4 D(h/2) - D(h)) / 3, which cancels the h^2
+    term; that is held to the parity bar with no allowance.  The plain h = 1e-4
+    differences are held to the bar plus their own truncation estimate,
+    |D(h) - D(h/2)| 4/3, measured per environment."""
     sc, ybar, u = hull_step["sc"], hull_step["ybar"], hull_step["u"]
     g, h = hull_step["g"], hull_step["h"]
     hstep = 1e-4
@@ -183,20 +191,34 @@ def test_hull_4096_derivatives_against_central_differences(oracle_lib, hull_step
         y = oracle_lib.forward(s)
         return np.array([np.sum(y[soff[i]:soff[i + 1]] * yb_s[soff[i]:soff[i + 1]])
                          for i in range(s.n_pairs)])
-    fd_g = np.zeros((sub.n_pairs, 12))
-    for k in range(12):
-        xi = np.zeros((sub.n_pairs, 12))
-        xi[:, k] = hstep
-        fd_g[:, k] = (loss(_moved(sub, xi)) - loss(_moved(sub, -xi))) / (2 * hstep)
-    gp, _ = oracle_lib.gradient(sub, yb_s, xi=hstep * u_s)
-    gm, _ = oracle_lib.gradient(sub, yb_s, xi=-hstep * u_s)
-    fd_h = (gp - gm) / (2 * hstep)
+
+    def differences(step):
+        fd_g = np.zeros((sub.n_pairs, 12))
+        for k in range(12):
+            xi = np.zeros((sub.n_pairs, 12))
+            xi[:, k] = step
+            fd_g[:, k] = (loss(_moved(sub, xi)) - loss(_moved(sub, -xi))) / (2 * step)
+        gp, _ = oracle_lib.gradient(sub, yb_s, xi=step * u_s)
+        gm, _ = oracle_lib.gradient(sub, yb_s, xi=-step * u_s)
+        return fd_g, (gp - gm) / (2 * step)
+    g1, h1 = differences(hstep)
+    g2, h2 = differences(hstep / 2)
     kg, kh = fp32_sensitivity(oracle_lib, sub, ybar[rows], u[idx])
+    tol_g, tol_h = np.maximum(GRAD_RTOL, COND_FACTOR * kg), np.maximum(GRAD_RTOL, COND_FACTOR * kh)
     print(f"central differences at h = {hstep}: {int(flags.sum())} of {len(idx0)} "
           "environments flagged near a transition knot")
-    _check_pairs(g[idx], fd_g, np.maximum(GRAD_RTOL, COND_FACTOR * kg), "gradient vs FD (h=1e-4)")
-    _check_pairs(h[idx], fd_h, np.maximum(GRAD_RTOL, COND_FACTOR * kh), "H u vs FD (h=1e-4)")
-    assert np.abs(fd_g).max() > 0 and np.abs(fd_h).max() > 0
+    _check_pairs(g[idx], (4 * g2 - g1) / 3, tol_g, "gradient vs FD (h=1e-4, Richardson)")
+    _check_pairs(h[idx], (4 * h2 - h1) / 3, tol_h, "H u vs FD (h=1e-4, Richardson)")
+    for got, d1, d2, tol, what in ((g[idx], g1, g2, tol_g, "gradient"), (h[idx], h1, h2, tol_h, "H u")):
+        trunc = np.abs(d1 - d2).max(1) * 4 / 3
+        err = np.abs(got - d1).max(1)
+        scale = np.abs(d1).max(1)
+        over = err > tol * scale + 1e-6
+        print(f"{what} vs plain FD (h=1e-4): {int(over.sum())} of {len(idx)} environments above "
+              f"the bar, largest truncation estimate "
+              f"{float((trunc / np.maximum(scale, 1e-30)).max()):.2e} relative")
+        assert np.all(err <= tol * scale + 1.5 * trunc + 1e-6), what
+    assert np.abs(g1).max() > 0 and np.abs(h1).max() > 0
 
 
 def test_uneven_65536_autotuned_sampled_against_oracle(oracle_lib, ctx):
