@@ -230,8 +230,9 @@ typedef struct {
                                  for the per-contact reverse passes, in records per output
                                  group (0: 16, and at least 65,536 in all; -1: no list, the
                                  reverse passes re-gate per pair), -1..4096 */
-  int32_t stage_tma;          /* forward: stage the SDF body's planes into shared memory
-                                 with bulk (TMA) copies (0) or plain loads (-1) */
+  int32_t stage_tma;          /* forward (per-item kernel and flat stages): stage the SDF
+                                 planes into shared memory with bulk (TMA) copies (0) or
+                                 plain loads (-1) */
   int32_t stage_wait;         /* bound of a bulk copy's wait, in polls of its barrier
                                  (0: 2^22; -1: none, so that every wait runs out -- for
                                  tests of the timeout path), -1..2^30 */
@@ -239,6 +240,9 @@ typedef struct {
                                  direction, one contact per thread, fold per group) on a
                                  batch with a contact list (0), or one warp per work item
                                  (-1) */
+  int32_t pdl;                /* flat stages launched with programmatic dependent launch,
+                                 each stage scheduled while the previous one drains (0), or
+                                 as ordinary launches (-1) */
 } ccm_tuning;
 CCM_API ccm_status ccm_batch_get_tuning(ccm_batch batch, ccm_tuning* out);
 /* Synchronous (sets kernel attributes).  Errors: CCM_ERR_INVALID (out of
@@ -250,6 +254,12 @@ CCM_API ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t);
  * are then incomplete), clearing the flag.  Synchronous.
  * Errors: CCM_ERR_INVALID, CCM_ERR_TIMEOUT, CCM_ERR_CUDA. */
 CCM_API ccm_status ccm_batch_check(ccm_batch batch, ccm_stream stream);
+
+/* Number of kernels the library has launched in this process (every context
+ * and stream), counted on the host as they are issued; the kernels of a CUDA
+ * graph captured from the library's calls count once, at capture, however
+ * often it is replayed.  For measurement.  Errors: CCM_ERR_INVALID (NULL). */
+CCM_API ccm_status ccm_kernel_launches(int64_t* n);
 
 /* Forward pass (Sec. 4.2-4.4).  pose_a, pose_b: device [n,12] float32; y:
  * device [G,8] float32, fully overwritten.  Asynchronous on `stream`.
@@ -305,23 +315,24 @@ CCM_API ccm_status ccm_contacts_backward_saved(ccm_batch batch, const float* pos
 /* One step from host memory, for callers whose poses and cotangents live on
  * the host: copies pose_a, pose_b (host [n,12]) and, if given, ybar (host
  * [G,8]) and dir (host [n,12]) into device buffers the batch owns, runs
- * ccm_contacts_save, then (with dir) the H dir / J dir pass and (with ybar)
- * the gradient pass of ccm_contacts_backward_saved (on a per-pair batch,
- * every body <= 256 pieces, the two passes run concurrently on two
- * streams), and copies back y (host
+ * ccm_contacts_save, then (with ybar) one pass of ccm_contacts_backward_saved:
+ * with dir the forward-over-reverse pass, whose gradient (the primal part of
+ * its dual numbers) is grad and whose tangents are hvp and jvp, without dir
+ * the gradient pass; and copies back y (host
  * [G,8]), grad (host [n,12]; required with ybar) and, with dir, hvp (host
  * [n,12]; required) and jvp (host [G,8]; optional).  Results are those of
- * the device calls on the same data.  The ybar / dir copies run on a second
- * stream during the forward kernel (after the pose copy, which the forward
- * waits for), and y, hvp and jvp are copied back on a third stream while the
- * next pass runs; only the pose copy and the copy of the last pass's output
- * (grad, or y for a forward alone) are not hidden behind a kernel.  Host
+ * the device calls on the same data (with dir: grad is that call's grad).
+ * The ybar / dir copies run on a second stream during the forward (after the
+ * pose copy, which the forward waits for), and y is copied back on a third
+ * stream while the reverse pass runs; only the pose copy and the copies of
+ * the reverse pass's outputs (or y for a forward alone) are not hidden
+ * behind a kernel.  Host
  * buffers should be pinned (cudaHostAlloc, torch pin_memory) so that the
  * copies are asynchronous.  Asynchronous on `stream`: the outputs are
  * complete once the work queued on `stream` up to this call is (synchronize
  * it before reading them); later work on `stream` waits for every copy.  The
  * first call allocates the device buffers (the poses, y, the record, ybar,
- * two gradients, hvp, dir and jvp: 52 n + (8 + CCM_SAVED_FLOATS + 8) G
+ * the gradient, hvp, dir and jvp: 52 n + (8 + CCM_SAVED_FLOATS + 8) G
  * floats) and two streams, kept until ccm_batch_destroy; later calls
  * allocate nothing.  Calls on one batch must be ordered on one stream.
  * Errors: CCM_ERR_INVALID (NULL pointer a mode needs, dir without ybar),

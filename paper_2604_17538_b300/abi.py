@@ -53,7 +53,7 @@ class ccm_tuning(C.Structure):
                 ("stage_planes", C.c_int32), ("stage_verts", C.c_int32),
                 ("groups_b", C.c_int32), ("flat_records", C.c_int32),
                 ("stage_tma", C.c_int32), ("stage_wait", C.c_int32),
-                ("flat_forward", C.c_int32)]
+                ("flat_forward", C.c_int32), ("pdl", C.c_int32)]
 
 
 class ccm_spline_desc(C.Structure):
@@ -113,7 +113,15 @@ _SIGS = {
     "ccm_attach_splines": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
     "ccm_batch_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ccm_build_voxel_grids": (C.c_int, [C.c_void_p, C.c_int]),
+    "ccm_kernel_launches": (C.c_int, [C.c_void_p]),
 }
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (host-side count)."""
+    n = C.c_int64()
+    check(lib().ccm_kernel_launches(C.byref(n)))
+    return n.value
 
 _lib = None
 

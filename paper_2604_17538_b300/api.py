@@ -118,7 +118,7 @@ class Batch:
         return {k: getattr(t, k) for k in ("item_v", "item_e", "item_vb", "item_eb", "fwd_warps",
                                            "groups", "stage_planes", "stage_verts", "groups_b",
                                            "flat_records", "stage_tma", "stage_wait",
-                                           "flat_forward")}
+                                           "flat_forward", "pdl")}
 
     def set_tuning(self, **kw):
         t = abi.ccm_tuning()

@@ -14,8 +14,12 @@
 #include "../../include/ccm.h"
 #include "ccm_device.cuh"
 #include "ccm_host.h"
+#include "ccm_launch.h"
 
 namespace ccm {
+
+std::atomic<long long> g_kernel_launches{0};
+
 
 // ---------------------------------------------------------------------------
 // errors
@@ -492,6 +496,12 @@ ccm_status ccm_batch_set_tuning(ccm_batch batch, const ccm_tuning* t) {
   return setup_flat(b->ctx, b);
 }
 
+ccm_status ccm_kernel_launches(int64_t* n) {
+  if (!n) return fail(CCM_ERR_INVALID, "n is NULL");
+  *n = g_kernel_launches.load(std::memory_order_relaxed);
+  return CCM_OK;
+}
+
 ccm_status ccm_batch_check(ccm_batch batch, ccm_stream stream) {
   Batch* b = reinterpret_cast<Batch*>(batch);
   if (!b) return fail(CCM_ERR_INVALID, "batch is NULL");
@@ -617,35 +627,21 @@ ccm_status ccm_contacts_step_host(ccm_batch batch, const float* pose_a, const fl
   CCM_CUDA(cudaEventRecord(h.ev[2], st), "event");
   CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[2], 0), "wait");
   CCM_CUDA(cudaMemcpyAsync(y, yd, G8, out, h.cout), "output copy");
-  // With dir on a per-pair batch the gradient pass runs on the input-copy
-  // stream, concurrently with the H u pass (they count their work on separate
-  // words; the per-item path shares its slots, so there both stay in order on
-  // `stream`, the H u pass first so that its larger outputs copy back during
-  // the gradient pass).
-  const bool conc = ybar && dir && b->per_pair;
+  // With dir, one forward-over-reverse pass gives the gradient (its primal
+  // part) with H u and J u (its tangents); without, the gradient pass.
   if (ybar) {
     CCM_CUDA(cudaStreamWaitEvent(st, h.ev[1], 0), "wait");
-    if (conc) CCM_CUDA(cudaStreamWaitEvent(h.cin, h.ev[2], 0), "wait");
-    if (dir) {
-      float* hd = static_cast<float*>(h.hvp.ptr);
-      float* jd = jvp ? static_cast<float*>(h.jvp.ptr) : nullptr;
-      if ((s = run_backward(b, pa, pb, prm, sv, yb, static_cast<const float*>(h.dir.ptr),
-                            static_cast<float*>(h.grad2.ptr), hd, jd, nullptr, st)) != CCM_OK)
-        return s;
-      CCM_CUDA(cudaEventRecord(h.ev[3], st), "event");
-      CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[3], 0), "wait");
-      CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, h.cout), "hvp copy");
-      if (jvp) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, h.cout), "jvp copy");
-    }
-    cudaStream_t gs = conc ? h.cin : st;
-    if ((s = run_backward(b, pa, pb, prm, sv, yb, nullptr, gd, nullptr, nullptr, nullptr, gs)) !=
-        CCM_OK)
+    float* hd = dir ? static_cast<float*>(h.hvp.ptr) : nullptr;
+    float* jd = dir && jvp ? static_cast<float*>(h.jvp.ptr) : nullptr;
+    if ((s = run_backward(b, pa, pb, prm, sv, yb,
+                          dir ? static_cast<const float*>(h.dir.ptr) : nullptr, gd, hd, jd,
+                          nullptr, st)) != CCM_OK)
       return s;
-    CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, gs), "gradient copy");
-    if (conc) {
-      CCM_CUDA(cudaEventRecord(h.ev[4], h.cin), "event");
-      CCM_CUDA(cudaStreamWaitEvent(st, h.ev[4], 0), "wait");
-    }
+    CCM_CUDA(cudaEventRecord(h.ev[3], st), "event");
+    CCM_CUDA(cudaStreamWaitEvent(h.cout, h.ev[3], 0), "wait");
+    CCM_CUDA(cudaMemcpyAsync(grad, gd, P, out, h.cout), "gradient copy");
+    if (dir) CCM_CUDA(cudaMemcpyAsync(hvp, hd, P, out, h.cout), "hvp copy");
+    if (jd) CCM_CUDA(cudaMemcpyAsync(jvp, jd, G8, out, h.cout), "jvp copy");
   }
   // later work on `stream` waits for the copies of the side streams
   CCM_CUDA(cudaEventRecord(h.ev[0], h.cout), "event");
@@ -873,6 +869,7 @@ ContactList Batch::contact_list() const {
   cl.cnt_e = cl.cnt_v + G;
   cl.off_v = static_cast<int32_t*>(d_foff.ptr);
   cl.off_e = cl.off_v + (G + 1);
+  cl.live_g = cl.off_e + (G + 1);
   cl.tile_sum = static_cast<long long*>(d_ftiles.ptr);
   return cl;
 }
@@ -897,7 +894,8 @@ ccm_status setup_flat(Context* c, Batch* bt) {
   if (cap == bt->flat_cap) return CCM_OK;
   for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted,
                    &bt->d_ftiles, &bt->d_unit_dir_off, &bt->d_rel, &bt->d_live, &bt->d_cand,
-                   &bt->d_cand_m, &bt->d_cval, &bt->d_sval, &bt->d_skey, &bt->d_ffctl})
+                   &bt->d_cand_m, &bt->d_cval, &bt->d_sval, &bt->d_skey, &bt->d_ffctl,
+                   &bt->d_ffhits})
     b->release();
   for (auto& pass : bt->d_fpass)
     for (DevBuf& b : pass) b.release();
@@ -915,7 +913,7 @@ ccm_status setup_flat(Context* c, Batch* bt) {
   ccm_status s;
   if ((s = alloc(bt->d_fctl, kCtlWords * sizeof(unsigned long long), "contact list")) != CCM_OK ||
       (s = alloc(bt->d_fcnt, 2 * G * sizeof(int32_t), "contact counts")) != CCM_OK ||
-      (s = alloc(bt->d_foff, 2 * (G + 1) * sizeof(int32_t), "contact offsets")) != CCM_OK ||
+      (s = alloc(bt->d_foff, (3 * G + 2) * sizeof(int32_t), "contact offsets")) != CCM_OK ||
       (s = alloc(bt->d_frecs, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK ||
       (s = alloc(bt->d_fsorted, (size_t)cap * sizeof(int4), "contact list")) != CCM_OK ||
       (s = alloc(bt->d_ftiles, 2 * (size_t)flat_scan_tiles(bt->G) * sizeof(long long),
@@ -946,7 +944,8 @@ ccm_status setup_flat(Context* c, Batch* bt) {
         (s = alloc(bt->d_cval, (size_t)bt->cand_cap * 8 * sizeof(float), "candidates")) != CCM_OK ||
         (s = alloc(bt->d_sval, (size_t)cap * 8 * sizeof(float), "contact values")) != CCM_OK ||
         (s = alloc(bt->d_skey, (size_t)cap * sizeof(long long), "contact keys")) != CCM_OK ||
-        (s = alloc(bt->d_ffctl, kFfWords * sizeof(unsigned long long), "flat forward")) != CCM_OK)
+        (s = alloc(bt->d_ffctl, kFfWords * sizeof(unsigned long long), "flat forward")) != CCM_OK ||
+        (s = alloc(bt->d_ffhits, (size_t)bt->G * kHitWords * sizeof(uint32_t), "hit words")) != CCM_OK)
       return s;
   }
   // a list that no forward filled yet reads as overflowed (the per-pair path)
@@ -977,7 +976,8 @@ ccm_status apply_tuning(Context* c, Batch* bt, const ccm_tuning& t) {
       (t.stage_verts != 0 && (t.stage_verts < 16 || t.stage_verts > 4096)) ||
       t.groups_b < 0 || t.groups_b > kGroupsPerChunk || t.flat_records < -1 ||
       t.flat_records > 4096 || t.stage_tma < -1 || t.stage_tma > 0 || t.stage_wait < -1 ||
-      t.stage_wait > (1 << 30) || t.flat_forward < -1 || t.flat_forward > 0)
+      t.stage_wait > (1 << 30) || t.flat_forward < -1 || t.flat_forward > 0 || t.pdl < -1 ||
+      t.pdl > 0)
     return fail(CCM_ERR_INVALID, "tuning out of range");
   const BatchMaxima& mx = bt->mx;
   UnitShape us{};
@@ -1119,6 +1119,7 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
     F.jvp = dir ? jvp : nullptr;
     F.counters = counters;
     F.n_sm = b->ctx->n_sm;
+    F.pdl = b->tuning.pdl == 0 ? 1 : 0;
     cudaError_t e = launch_flat_backward(F, stream);
     if (e != cudaSuccess) return cuda_fail(e, "per-contact backward launch");
     L.only_if = F.fp.sched + 2;
@@ -1259,6 +1260,7 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
     F.kp = kp;
     F.y = y;
     F.saved = saved;
+    F.hits = static_cast<uint32_t*>(b->d_ffhits.ptr);
     F.cl = b->contact_list();
     F.cl.tag = b->list_tag;
     F.sval = static_cast<float*>(b->d_sval.ptr);
@@ -1273,8 +1275,12 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
     F.counters = counters;
     F.vmax = b->mx.vmax;
     F.fmax = b->mx.fmax;
-    F.gate_planes = std::max(b->mx.fmax, std::min(b->mx.s_planes, 768));
+    F.gate_planes = std::max(b->mx.fmax, std::min(b->mx.s_planes, 760));   // 4 warps in 48 KB
+    F.stage_tma = b->us.stage_tma;
+    F.wait_limit = b->us.wait_limit;
+    F.status = static_cast<int*>(b->d_status.ptr);
     F.n_sm = b->ctx->n_sm;
+    F.pdl = b->tuning.pdl == 0 ? 1 : 0;
     cudaError_t e = launch_flat_forward(F, stream);
     if (e != cudaSuccess) return cuda_fail(e, "flat forward launch");
     L.only_if = F.ctl + kFfOverflow;

@@ -79,16 +79,31 @@ template <class T> __device__ __forceinline__ void part_combine(PartT<T>& a, con
 }
 
 // folds the contacts k0 <= k < k1 of a value array [*, 8] (f, d_c, p, n) into
-// acc in index order, one at a time
+// acc in index order, one at a time; the values of kBatch contacts are loaded
+// before the first of them is folded, so that a long group waits on one load
+// latency per batch instead of one per contact (the order of the arithmetic,
+// hence the result, is that of the plain loop)
+template <class T>
+__device__ __forceinline__ void fold_one(const T* c, float c_blend, PartT<T>& acc) {
+  PartT<T> q;
+  part_from_contact(q, c[0], c[1], v3(c[2], c[3], c[4]), v3(c[5], c[6], c[7]), c_blend);
+  part_combine(acc, q);
+}
 template <class T>
 __device__ __forceinline__ void fold_range(const T* cval, int64_t k0, int64_t k1, float c_blend,
                                            PartT<T>& acc) {
-  for (int64_t k = k0; k < k1; ++k) {
-    const T* c = cval + 8 * k;
-    PartT<T> q;
-    part_from_contact(q, c[0], c[1], v3(c[2], c[3], c[4]), v3(c[5], c[6], c[7]), c_blend);
-    part_combine(acc, q);
+  constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
+  int64_t k = k0;
+  for (; k + kBatch <= k1; k += kBatch) {
+    T v[kBatch][8];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[b][q] = cval[8 * (k + b) + q];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) fold_one(v[b], c_blend, acc);
   }
+  for (; k < k1; ++k) fold_one(cval + 8 * k, c_blend, acc);
 }
 
 __device__ __forceinline__ float shfl_down_t(float v, int o) { return __shfl_down_sync(kFull, v, o); }

@@ -23,6 +23,7 @@
 #include "ccm_adjoint.cuh"
 #include "ccm_unit.cuh"
 #include "ccm_bwd.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -1047,6 +1048,7 @@ static void launch_pair(const BwdLaunch& L, cudaStream_t stream) {
     bwd_pair_kernel<T, kK, false><<<L.pair_grid, 32, smem, stream>>>(
         L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
         L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, nullptr, L.sched, L.only_if);
+  count_launch();
 }
 
 template <class T, int kK>
@@ -1060,6 +1062,7 @@ static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
     bwd_unit_kernel<T, kK, false><<<L.grid, 32, smem, stream>>>(
         L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a, L.pose_b, L.ybar, L.dir,
         L.saved, L.kp, L.us, L.part, L.jvp, nullptr, L.sched);
+  count_launch();
 }
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
@@ -1093,6 +1096,7 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   const int blocks = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (n + 255) / 256));
   bwd_reduce_kernel<<<blocks, 256, 0, stream>>>(L.part, L.item_off, L.n_pairs, L.dev_pairs, L.grad,
                                                 L.dir ? L.hvp : nullptr);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -40,9 +40,13 @@ struct ContactList {
   int32_t* cnt_e;           // [G] edge contacts per group
   int32_t* off_v;           // [G + 1] exclusive prefix of cnt_v
   int32_t* off_e;           // [G + 1] exclusive prefix of cnt_e
+  int32_t* live_g;          // [G] the groups with at least one contact, in index order
   long long* tile_sum;      // [2 tiles] scratch of the scan (flat_scan_tiles)
 };
 
-enum { kCtlCursor = 0, kCtlOverflow = 1, kCtlNV = 2, kCtlNE = 3, kCtlTag = 4, kCtlWords = 8 };
+// ctl words: appended records, overflow flag, vertex contacts NV, edge
+// contacts NE, the list's tag, groups with contacts NG
+enum { kCtlCursor = 0, kCtlOverflow = 1, kCtlNV = 2, kCtlNE = 3, kCtlTag = 4, kCtlNG = 5,
+       kCtlWords = 8 };
 
 }  // namespace ccm

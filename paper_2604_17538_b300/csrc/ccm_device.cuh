@@ -317,6 +317,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 constexpr long long kDrainLimit = 1ll << 28;
 
+// Waits, in a kernel launched with programmatic dependent launch, until the
+// previous kernel of the stream has completed and its writes are visible
+// (ccm_launch.h); returns at once in a kernel launched without it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Copies n elements from global to shared memory, four loads in flight per
 // lane (the staging of a work item's geometry is latency-bound otherwise).
 template <class U>

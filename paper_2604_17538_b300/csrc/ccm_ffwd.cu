@@ -17,10 +17,11 @@
 //   scan     the counts to offsets (ccm_flat.cu), then scatter: the contacts
 //            of non-zero weight to their group's segment of the contact list;
 //   rank     one contact per thread: its place in the segment's (SDF piece,
-//            feature) order, where it and its values are written;
-//   fold     one output group per thread: its vertex contacts, then its edge
-//            contacts, blended in list order (online softmax, Sec. 4.4) into
-//            the group's outputs and saved record.
+//            feature) order, where it and its values are written; and every
+//            group's outputs and record written as if it had no contact;
+//   fold     one group with contacts per thread: its vertex contacts, then
+//            its edge contacts, blended in list order (online softmax,
+//            Sec. 4.4) into the group's outputs and saved record.
 // The contact list it leaves is the one the per-contact reverse passes read
 // (ccm_flat.cu).  The fixed order of the fold makes a pair's outputs depend
 // on the pair alone.  Culls are those of the per-item kernel, so the set of
@@ -32,6 +33,7 @@
 #include "ccm_narrow.cuh"
 #include "ccm_unit.cuh"
 #include "ccm_ffwd.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -39,6 +41,7 @@ namespace ccm {
 // setup: relative poses per unit; counters, group counts and hit words zeroed
 // ---------------------------------------------------------------------------
 __global__ void ff_setup_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid < kFfWords) L.ctl[tid] = 0ull;
@@ -46,10 +49,10 @@ __global__ void ff_setup_kernel(FlatFwdLaunch L) {
   for (int64_t i = tid; i < L.G; i += stride) {
     L.cl.cnt_v[i] = 0;
     L.cl.cnt_e[i] = 0;
-    if (L.saved) {
-      uint32_t* h = reinterpret_cast<uint32_t*>(L.saved + (int64_t)kSavedFloats * i + 18);
-      for (int q = 0; q < kHitWords; ++q) h[q] = 0u;
-    }
+  }
+  if (L.saved) {
+    uint4* h = reinterpret_cast<uint4*>(L.hits);
+    for (int64_t i = tid; i < L.G * (kHitWords / 4); i += stride) h[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int64_t u = tid; u < 2 * L.n_pairs; u += stride) {
     const int64_t p = u >> 1;
@@ -95,6 +98,30 @@ __device__ __forceinline__ int64_t ff_slot(unsigned long long* counter, bool wan
   return want ? (int64_t)(base + __popc(m & ((1u << lane) - 1u))) : -1;
 }
 
+// Copies n planes to a warp's shared memory: one bulk copy completed on the
+// warp's mbarrier, or the lanes' loads.  A bulk copy whose wait runs out
+// records CCM_ERR_TIMEOUT, waits (bounded) for the copy to land and returns
+// false: the warp then stops.  The caller's syncwarp before the call orders
+// the lanes' earlier reads of dst before the copy.
+__device__ __forceinline__ bool ff_stage(const FlatFwdLaunch& L, float4* dst, const float4* src,
+                                         int n, uint64_t* bar, uint32_t& phase, int lane) {
+  if (!L.stage_tma) {
+    stage_copy(dst, src, n, lane);
+    return true;
+  }
+  if (lane == 0) {
+    fence_proxy_async_smem();
+    bulk_copy_g2s(dst, src, 16u * (uint32_t)n, bar);
+  }
+  const bool ok = __all_sync(kFull, mbar_wait_bounded(bar, phase, L.wait_limit));
+  if (!ok) {
+    if (lane == 0 && L.status) atomicExch(L.status, (int)CCM_ERR_TIMEOUT);
+    mbar_wait_bounded(bar, phase, kDrainLimit);
+  }
+  phase ^= 1u;
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
 // gate: one unit per warp, lanes over its directions (f, s); the SDF body's
 // planes staged in the warp's shared memory, a chunk of pieces at a time
@@ -103,9 +130,15 @@ constexpr int kGateWarps = 4;
 
 template <bool kCount>
 __global__ void __launch_bounds__(128) ff_gate_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* pl_s = reinterpret_cast<float4*>(smem_raw) + (size_t)warp * L.gate_planes;
+  __shared__ uint64_t bar_s[kGateWarps];
+  uint64_t* bar = bar_s + warp;
+  if (L.stage_tma && lane == 0) mbar_init(bar, 1);
+  __syncwarp();
+  uint32_t phase = 0;
   const bool no_cull = (L.kp.flags & CCM_FLAG_NO_CULL) != 0u;
   const int64_t nu = 2 * L.n_pairs;
   unsigned long long c_dirs = 0, c_gate = 0;
@@ -121,39 +154,46 @@ __global__ void __launch_bounds__(128) ff_gate_kernel(FlatFwdLaunch L) {
     const float margin = 1e-6f * (1.0f + fabsf(tr[0]) + fabsf(tr[1]) + fabsf(tr[2]));
     const int f_base = L.g.pieces[S.p0].f0;   // a body's planes are contiguous
     for (int s0 = 0; s0 < S.np;) {
-      // the chunk [s0, s1): whole pieces whose planes fit the warp's budget
-      int s1 = s0, P = 0;
-      while (s1 < S.np) {
-        const int nf = L.g.pieces[S.p0 + s1].nf;
-        if (P + nf > L.gate_planes && s1 > s0) break;
-        P += nf;
-        ++s1;
+      // the chunk [s0, s1): whole pieces (at most 32) whose planes fit the
+      // warp's budget, from a prefix sum of the pieces' plane counts
+      const PieceRec mine = s0 + lane < S.np ? L.g.pieces[S.p0 + s0 + lane] : PieceRec{};
+      int pre = s0 + lane < S.np ? mine.nf : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += t;
       }
-      const int p0 = L.g.pieces[S.p0 + s0].f0 - f_base;
+      const unsigned fit = __ballot_sync(kFull, s0 + lane < S.np && pre <= L.gate_planes);
+      const int ns = max(1, __popc(fit));            // the prefix sums grow with the lane
+      const int P = __shfl_sync(kFull, pre, ns - 1);
+      const int p0 = __shfl_sync(kFull, mine.f0, 0) - f_base;
       __syncwarp();   // the previous chunk is no longer read
-      stage_copy(pl_s, L.g.planes + f_base + p0, P, lane);
+      if (!ff_stage(L, pl_s, L.g.planes + f_base + p0, P, bar, phase, lane)) return;
       __syncwarp();
-      const int ns = s1 - s0, nd = F.np * ns;
+      // directions f fastest: lanes that share an SDF piece read the same
+      // plane (a broadcast) and run the same number of steps
+      const int nd = F.np * ns;
       for (int d0 = 0; d0 < nd; d0 += 32) {
         const int d = d0 + lane;
+        const int s = d / F.np, f = d - s * F.np;
+        const int sf0 = __shfl_sync(kFull, mine.f0, min(s, 31));
+        const int snf = __shfl_sync(kFull, mine.nf, min(s, 31));
         bool live = false;
         int4 rec = make_int4(0, 0, 0, 0);
         if (d < nd) {
-          const int f = d / ns, s = s0 + (d - f * ns);
           const float4 sph = L.g.pieces[F.p0 + f].sphere;
           const float3 c = xform(R, tr, sph);
-          const PieceRec sp = L.g.pieces[S.p0 + s];
           int pl = 0;
-          const float mc = max_plane_arg(pl_s + (sp.f0 - f_base - p0), sp.nf, c.x, c.y, c.z, pl);
+          const float mc = max_plane_arg(pl_s + (sf0 - f_base - p0), snf, c.x, c.y, c.z, pl);
           live = no_cull || mc - sph.w - margin < L.kp.d_max;
           // (output row, F piece, S piece, a plane attaining the max at the centre)
-          rec = make_int4((int)(row0 + f), F.p0 + f, S.p0 + s, pl);
-          if (kCount) { c_dirs += 1; c_gate += sp.nf; }
+          rec = make_int4((int)(row0 + f), F.p0 + f, S.p0 + s0 + s, pl);
+          if (kCount) { c_dirs += 1; c_gate += snf; }
         }
         const int64_t at = ff_slot(L.ctl + kFfLive, live, lane);
         if (live) L.live[at] = rec;   // capacity: every direction
       }
-      s0 = s1;
+      s0 += ns;
     }
   }
   if (kCount && L.counters) {
@@ -174,25 +214,37 @@ __host__ __device__ inline size_t ff_feature_warp_bytes(int vmax, int fmax) {
          (size_t)16 * fmax;
 }
 
+// dynamic shared memory of a block: the default 48 KB less the static
+// mbarrier words of the gate and feature kernels
+constexpr int kDynSmem = 48 * 1024 - 256;
+
 bool flat_forward_fits(int vmax, int fmax) {
-  return 16 * fmax <= 48 * 1024 && ff_feature_warp_bytes(vmax, fmax) <= 48 * 1024;
+  return 16 * fmax <= kDynSmem && ff_feature_warp_bytes(vmax, fmax) <= (size_t)kDynSmem;
 }
 
 size_t flat_forward_feature_smem(int vmax, int fmax, int* warps_per_block) {
   const size_t per_warp = ff_feature_warp_bytes(vmax, fmax);
   int w = 4;
-  while (w > 1 && (size_t)w * per_warp > 48 * 1024) --w;
+  while (w > 1 && (size_t)w * per_warp > (size_t)kDynSmem) --w;
   *warps_per_block = w;
   return (size_t)w * per_warp;
 }
 
+// candidate index of the t-th candidate of the eval order: the nv vertex
+// candidates, then the edge candidates from the middle of the arrays
+__device__ __forceinline__ int64_t ff_cand_index(const FlatFwdLaunch& L, int64_t t, int64_t nv) {
+  return t < nv ? t : L.cand_cap / 2 + (t - nv);
+}
+
 __device__ __forceinline__ void ff_push(const FlatFwdLaunch& L, bool want, int4 rec, float2 mm,
-                                        int lane) {
-  const int64_t at = ff_slot(L.ctl + kFfCand, want, lane);
+                                        int lane, bool edge) {
+  const int64_t at = ff_slot(L.ctl + (edge ? kFfCandE : kFfCand), want, lane);
   if (want) {
-    if (at < L.cand_cap) {
-      L.cand[at] = rec;
-      L.cand_m[at] = mm;
+    const int64_t half = L.cand_cap / 2;
+    if (at < half) {
+      const int64_t k = edge ? half + at : at;
+      L.cand[k] = rec;
+      L.cand_m[k] = mm;
     } else {
       L.ctl[kFfOverflow] = 1ull;
     }
@@ -200,7 +252,8 @@ __device__ __forceinline__ void ff_push(const FlatFwdLaunch& L, bool want, int4 
 }
 
 template <bool kCount>
-__global__ void ff_feature_kernel(FlatFwdLaunch L) {
+__global__ void __launch_bounds__(128, 8) ff_feature_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int vmax = L.vmax;
@@ -211,6 +264,11 @@ __global__ void ff_feature_kernel(FlatFwdLaunch L) {
   uint16_t* am = reinterpret_cast<uint16_t*>(base + align16i(16 * vmax) + 2 * align16i(4 * vmax));
   float4* planes = reinterpret_cast<float4*>(base + align16i(16 * vmax) + 2 * align16i(4 * vmax) +
                                              align16i(2 * vmax));
+  __shared__ uint64_t bar_s[4];
+  uint64_t* bar = bar_s + warp;
+  if (L.stage_tma && lane == 0) mbar_init(bar, 1);
+  __syncwarp();
+  uint32_t phase = 0;
   const bool no_cull = (L.kp.flags & CCM_FLAG_NO_CULL) != 0u;
   const bool voxel = (L.kp.flags & CCM_FLAG_VOXEL_CULL) != 0u && !no_cull;
   const float d_max = L.kp.d_max;
@@ -224,32 +282,62 @@ __global__ void ff_feature_kernel(FlatFwdLaunch L) {
     const PieceRec fp = L.g.pieces[f_glob], sp = L.g.pieces[s_glob];
     // the SDF piece's planes in the warp's shared memory (the previous
     // direction's are no longer read: syncwarp at the end of the loop)
-    stage_copy(planes, L.g.planes + sp.f0, sp.nf, lane);
     float R[9], tr[3];
     load_rel(L.rel + 12 * u, R, tr);
+    if (!ff_stage(L, planes, L.g.planes + sp.f0, sp.nf, bar, phase, lane)) return;
     __syncwarp();
     if (kCount && lane == 0) { c_live += 1; c_feat += fp.nv + fp.ne; }
     // vertices: exact max-plane value (or a one-plane / voxel cull)
     const float4 pj = planes[pl];
-    for (int i = lane; i < fp.nv; i += 32) {
-      const float3 x = xform(R, tr, L.g.verts[fp.v0 + i]);
-      xs[i] = make_float4(x.x, x.y, x.z, 0.f);
-      const float vj = fmaf(pj.x, x.x, fmaf(pj.y, x.y, fmaf(pj.z, x.z, pj.w)));
-      const float b = voxel ? voxel_bound(L.g, s_glob, x.x, x.y, x.z) : -INFINITY;
-      vb[i] = b;
-      if (!no_cull && vj >= d_max) {
-        m[i] = vj;
-        am[i] = (uint16_t)pl;
-        if (kCount) c_maxp += 1;
-      } else if (b - kVoxTol >= d_max) {
-        m[i] = vj;
-        am[i] = (uint16_t)(pl | kVoxCulled);
-        if (kCount) c_maxp += 1;
-      } else {
-        int arg;
-        m[i] = max_plane_arg(planes, sp.nf, x.x, x.y, x.z, arg);
-        am[i] = (uint16_t)arg;
-        if (kCount) c_maxp += sp.nf;
+    for (int i0 = 0; i0 < fp.nv; i0 += 32) {
+      const int i = i0 + lane;
+      bool scan = false;
+      float3 x = make_float3(0.f, 0.f, 0.f);
+      if (i < fp.nv) {
+        x = xform(R, tr, L.g.verts[fp.v0 + i]);
+        xs[i] = make_float4(x.x, x.y, x.z, 0.f);
+        const float vj = fmaf(pj.x, x.x, fmaf(pj.y, x.y, fmaf(pj.z, x.z, pj.w)));
+        const float b = voxel ? voxel_bound(L.g, s_glob, x.x, x.y, x.z) : -INFINITY;
+        vb[i] = b;
+        if (!no_cull && vj >= d_max) {
+          m[i] = vj;
+          am[i] = (uint16_t)pl;
+          if (kCount) c_maxp += 1;
+        } else if (b - kVoxTol >= d_max) {
+          m[i] = vj;
+          am[i] = (uint16_t)(pl | kVoxCulled);
+          if (kCount) c_maxp += 1;
+        } else {
+          scan = true;
+          if (kCount) c_maxp += sp.nf;
+        }
+      }
+      // the exact maxima of the few vertices left, one at a time with the
+      // planes over the lanes (the lowest index attaining the maximum, as a
+      // serial scan would keep)
+      unsigned todo = __ballot_sync(kFull, scan);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float px = __shfl_sync(kFull, x.x, src), py = __shfl_sync(kFull, x.y, src),
+                    pz = __shfl_sync(kFull, x.z, src);
+        float best = -INFINITY;
+        int barg = 0x7fffffff;
+        for (int k = lane; k < sp.nf; k += 32) {
+          const float4 p = planes[k];
+          const float v = fmaf(p.x, px, fmaf(p.y, py, fmaf(p.z, pz, p.w)));
+          if (v > best) { best = v; barg = k; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(kFull, best, o);
+          const int oa = __shfl_xor_sync(kFull, barg, o);
+          if (ov > best || (ov == best && oa < barg)) { best = ov; barg = oa; }
+        }
+        if (lane == src) {
+          m[i] = best;
+          am[i] = (uint16_t)barg;
+        }
       }
     }
     __syncwarp();
@@ -272,14 +360,14 @@ __global__ void ff_feature_kernel(FlatFwdLaunch L) {
         rec = make_int4(row, s_glob, f_glob, (int)((1u << 31) | (uint32_t)k));
         mm = make_float2(m[i0], m[i1]);
       }
-      ff_push(L, live, rec, mm, lane);
+      ff_push(L, live, rec, mm, lane, true);
     }
     // vertices below d_max (not culled by a voxel)
     for (int i0 = 0; i0 < fp.nv; i0 += 32) {
       const int i = i0 + lane;
       const bool live = i < fp.nv && (no_cull || (m[i] < d_max && !(am[i] & kVoxCulled)));
       ff_push(L, live, make_int4(row, s_glob, f_glob, i), make_float2(i < fp.nv ? m[i] : 0.f, 0.f),
-              lane);
+              lane, false);
     }
     __syncwarp();   // the next direction overwrites the slice
   }
@@ -299,14 +387,19 @@ __global__ void ff_feature_kernel(FlatFwdLaunch L) {
 // ---------------------------------------------------------------------------
 template <bool kCount>
 __global__ void __launch_bounds__(128) ff_eval_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   if (L.ctl[kFfOverflow]) return;
   const int lane = threadIdx.x & 31;
   const KParams& kp = L.kp;
   const bool project = (kp.flags & CCM_FLAG_PROJECT) != 0u;
-  const int64_t n = (int64_t)L.ctl[kFfCand];
+  // (an overflow stops this stage above; the clamps keep every index in range)
+  const int64_t half = L.cand_cap / 2;
+  const int64_t nv = min((int64_t)L.ctl[kFfCand], half);
+  const int64_t n = nv + min((int64_t)L.ctl[kFfCandE], half);
   unsigned long long c_eg = 0, c_ev = 0, c_con = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = ff_cand_index(L, t, nv);
     const int4 rec = L.cand[k];
     const float2 mm = L.cand_m[k];
     const int row = rec.x;
@@ -356,8 +449,7 @@ __global__ void __launch_bounds__(128) ff_eval_kernel(FlatFwdLaunch L) {
         const int sp0 = L.g.bodies[(rp & 1) == 0 ? pr.bodyB : pr.bodyA].p0;
         const int sl = rec.y - sp0;
         if (sl < kHitS)
-          atomicOr(reinterpret_cast<uint32_t*>(L.saved + (int64_t)kSavedFloats * row + 18) + (sl >> 5),
-                   1u << (sl & 31));
+          atomicOr(L.hits + (int64_t)kHitWords * row + (sl >> 5), 1u << (sl & 31));
       }
       if (kCount) c_con += 1;
     }
@@ -377,15 +469,20 @@ __global__ void __launch_bounds__(128) ff_eval_kernel(FlatFwdLaunch L) {
 // scatter: contacts of non-zero weight to their group's segment
 // ---------------------------------------------------------------------------
 __global__ void ff_scatter_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   if (L.ctl[kFfOverflow]) return;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NE = (int64_t)L.cl.ctl[kCtlNE];
   if (NV + NE > L.cl.cap) {          // the contact list cannot hold them
     if (blockIdx.x == 0 && threadIdx.x == 0) L.ctl[kFfOverflow] = 1ull;
     return;
   }
-  const int64_t n = (int64_t)L.ctl[kFfCand];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  // (an overflow stops this stage above; the clamps keep every index in range)
+  const int64_t half = L.cand_cap / 2;
+  const int64_t nv = min((int64_t)L.ctl[kFfCand], half);
+  const int64_t n = nv + min((int64_t)L.ctl[kFfCandE], half);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = ff_cand_index(L, t, nv);
     const float* c = L.cval + 8 * k;
     if (!(c[0] > 0.f)) continue;
     const int4 rec = L.cand[k];
@@ -405,7 +502,8 @@ __global__ void ff_scatter_kernel(FlatFwdLaunch L) {
 // ---------------------------------------------------------------------------
 constexpr int64_t kRankCap = 4096;   // longer segments: the per-item forward runs instead
 
-__global__ void ff_rank_kernel(FlatFwdLaunch L) {
+__global__ void __launch_bounds__(256) ff_rank_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   if (L.ctl[kFfOverflow]) return;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NE = (int64_t)L.cl.ctl[kCtlNE];
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < NV + NE;
@@ -429,34 +527,77 @@ __global__ void ff_rank_kernel(FlatFwdLaunch L) {
     o[0] = c[0];
     o[1] = c[1];
   }
+  // every group's outputs and record as if it had no contact (the fold
+  // then rewrites the groups that have some), 32 groups per warp staged in
+  // shared memory and written as contiguous float4 rows
+  __shared__ __align__(16) float y_s[8][32 * 8];
+  __shared__ __align__(16) float r_s[8][32 * kSavedFloats];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32; g0 < L.G;
+       g0 += warps * 32) {
+    const int64_t g = g0 + lane;
+    const int n_here = (int)(L.G - g0 < 32 ? L.G - g0 : 32);
+    if (g < L.G) {
+      write_empty(y_s[warp] + 8 * lane, L.kp);
+      if (L.saved) {
+        PartT<float> z;
+        part_zero(z);
+        float* o = r_s[warp] + kSavedFloats * lane;
+        o[0] = z.M;
+        for (int q = 1; q < 18; ++q) o[q] = 0.f;
+        const uint4* hs = reinterpret_cast<const uint4*>(L.hits + (int64_t)kHitWords * g);
+        uint32_t* h = reinterpret_cast<uint32_t*>(o + 18);
+#pragma unroll
+        for (int q = 0; q < kHitWords / 4; ++q) {
+          const uint4 w = hs[q];
+          h[4 * q] = w.x; h[4 * q + 1] = w.y; h[4 * q + 2] = w.z; h[4 * q + 3] = w.w;
+        }
+        h[kHitWords] = L.cl.tag;
+        h[kHitWords + 1] = 0u;
+      }
+    }
+    __syncwarp();
+    {
+      const float4* src = reinterpret_cast<const float4*>(y_s[warp]);
+      float4* dst = reinterpret_cast<float4*>(L.y + 8 * g0);
+      for (int i = lane; i < 2 * n_here; i += 32) dst[i] = src[i];
+    }
+    if (L.saved) {
+      const float4* src = reinterpret_cast<const float4*>(r_s[warp]);
+      float4* dst = reinterpret_cast<float4*>(L.saved + (int64_t)kSavedFloats * g0);
+      for (int i = lane; i < (kSavedFloats / 4) * n_here; i += 32) dst[i] = src[i];
+    }
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
-// fold: one output group per thread, its vertex contacts then its edge
-// contacts in list order, one at a time -- the order and arithmetic of the
-// per-contact reverse passes' own fold (ccm_flat.cu) over the same list
+// fold: one group with contacts per thread (the list of such groups from the
+// scan), its vertex contacts then its edge contacts in list order -- the
+// order and arithmetic of the per-contact reverse passes' own fold
+// (ccm_flat.cu) over the same list
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) ff_fold_kernel(FlatFwdLaunch L) {
+  pdl_wait();
   if (L.ctl[kFfOverflow]) return;
-  const int64_t NV = (int64_t)L.cl.ctl[kCtlNV];
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.G;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v0 = L.cl.off_v[g], v1 = L.cl.off_v[g + 1];
-    const int64_t e0 = L.cl.off_e[g], e1 = L.cl.off_e[g + 1];
+  const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NG = (int64_t)L.cl.ctl[kCtlNG];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < NG;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = L.cl.live_g[i];
+    const int rp = L.row_pair[g];   // the pose's loads overlap the folds
+    float RS[9], tS[3];
+    load_pose(((rp & 1) == 0 ? L.pose_b : L.pose_a) + 12 * (int64_t)(rp >> 1), RS, tS);
     PartT<float> A;
     part_zero(A);
-    float* yo = L.y + 8 * g;
-    if (v0 == v1 && e0 == e1) {
-      write_empty(yo, L.kp);
-    } else {
-      fold_range(L.sval, v0, v1, L.kp.c_blend, A);
-      fold_range(L.sval, NV + e0, NV + e1, L.kp.c_blend, A);
-      const int rp = L.row_pair[g];
-      float RS[9], tS[3];
-      load_pose(((rp & 1) == 0 ? L.pose_b : L.pose_a) + 12 * (int64_t)(rp >> 1), RS, tS);
-      write_group(yo, A, RS, tS, L.kp);
-    }
-    if (L.saved) {   // the partial and the list's tag (hit words set by eval)
+    fold_range(L.sval, L.cl.off_v[g], L.cl.off_v[g + 1], L.kp.c_blend, A);
+    fold_range(L.sval, NV + L.cl.off_e[g], NV + L.cl.off_e[g + 1], L.kp.c_blend, A);
+    float yo[8];
+    write_group(yo, A, RS, tS, L.kp);
+    float4* yd = reinterpret_cast<float4*>(L.y + 8 * g);
+    yd[0] = make_float4(yo[0], yo[1], yo[2], yo[3]);
+    yd[1] = make_float4(yo[4], yo[5], yo[6], yo[7]);
+    if (L.saved) {   // the partial (hit words and tag are in place)
       float* o = L.saved + (int64_t)kSavedFloats * g;
       o[0] = A.M; o[1] = A.U; o[2] = A.rd; o[3] = A.rf;
       o[4] = A.rp.x; o[5] = A.rp.y; o[6] = A.rp.z;
@@ -464,9 +605,6 @@ __global__ void __launch_bounds__(128) ff_fold_kernel(FlatFwdLaunch L) {
       o[10] = A.Dd; o[11] = A.Da;
       o[12] = A.Dp.x; o[13] = A.Dp.y; o[14] = A.Dp.z;
       o[15] = A.Dn.x; o[16] = A.Dn.y; o[17] = A.Dn.z;
-      uint32_t* h = reinterpret_cast<uint32_t*>(o + 18);
-      h[kHitWords] = L.cl.tag;
-      h[kHitWords + 1] = 0u;
     }
   }
 }
@@ -474,35 +612,33 @@ __global__ void __launch_bounds__(128) ff_fold_kernel(FlatFwdLaunch L) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_flat_forward(const FlatFwdLaunch& L, cudaStream_t stream) {
   cudaError_t e;
+  const bool pdl = L.pdl != 0;
   const int sb = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(L.G, 2 * L.n_pairs) + 255) / 256,
                                                              8 * L.n_sm));
-  ff_setup_kernel<<<sb, 256, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int gw = std::max(1, std::min(kGateWarps, (48 * 1024) / (16 * L.gate_planes)));
+  if ((e = launch_k(pdl, ff_setup_kernel, sb, 256, 0, stream, L)) != cudaSuccess) return e;
+  const int gw = std::max(1, std::min(kGateWarps, kDynSmem / (16 * L.gate_planes)));
   const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.n_pairs + gw - 1) / gw,
                                                              32 * L.n_sm));
   const size_t gsm = (size_t)gw * 16 * L.gate_planes;
-  if (L.counters) ff_gate_kernel<true><<<gb, 32 * gw, gsm, stream>>>(L);
-  else ff_gate_kernel<false><<<gb, 32 * gw, gsm, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_k(pdl, L.counters ? ff_gate_kernel<true> : ff_gate_kernel<false>, gb, 32 * gw, gsm,
+               stream, L);
+  if (e != cudaSuccess) return e;
   int wpb = 1;
   const size_t smem = flat_forward_feature_smem(L.vmax, L.fmax, &wpb);
   const int fb = 64 * L.n_sm;
-  if (L.counters) ff_feature_kernel<true><<<fb, 32 * wpb, smem, stream>>>(L);
-  else ff_feature_kernel<false><<<fb, 32 * wpb, smem, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_k(pdl, L.counters ? ff_feature_kernel<true> : ff_feature_kernel<false>, fb, 32 * wpb,
+               smem, stream, L);
+  if (e != cudaSuccess) return e;
   const int eb = 32 * L.n_sm;
-  if (L.counters) ff_eval_kernel<true><<<eb, 128, 0, stream>>>(L);
-  else ff_eval_kernel<false><<<eb, 128, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_flat_prep_scan(L.cl, L.G, stream)) != cudaSuccess) return e;
-  ff_scatter_kernel<<<8 * L.n_sm, 256, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ff_rank_kernel<<<8 * L.n_sm, 256, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int fo = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 64 * L.n_sm));
-  ff_fold_kernel<<<fo, 128, 0, stream>>>(L);
-  return cudaGetLastError();
+  e = launch_k(pdl, L.counters ? ff_eval_kernel<true> : ff_eval_kernel<false>, eb, 128, 0, stream,
+               L);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_flat_prep_scan(L.cl, L.G, stream, pdl)) != cudaSuccess) return e;
+  if ((e = launch_k(pdl, ff_scatter_kernel, 8 * L.n_sm, 256, 0, stream, L)) != cudaSuccess) return e;
+  if ((e = launch_k(pdl, ff_rank_kernel, 8 * L.n_sm, 256, 0, stream, L)) != cudaSuccess) return e;
+  // groups with contacts: at most G, and one thread each
+  const int fo = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 8 * L.n_sm));
+  return launch_k(pdl, ff_fold_kernel, fo, 128, 0, stream, L);
 }
 
 }  // namespace ccm

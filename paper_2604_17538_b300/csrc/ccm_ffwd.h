@@ -7,7 +7,10 @@
 
 namespace ccm {
 
-enum { kFfLive = 0, kFfCand = 1, kFfOverflow = 2, kFfSched = 3, kFfWords = 8 };
+// control words: live directions, vertex and edge candidates (vertices fill
+// the first half of the candidate arrays, edges the second, so that a warp of
+// the eval stage takes contacts of one kind), overflow flag
+enum { kFfLive = 0, kFfCand = 1, kFfOverflow = 2, kFfSched = 3, kFfCandE = 4, kFfWords = 8 };
 
 struct FlatFwdLaunch {
   DevGeom g;
@@ -20,6 +23,7 @@ struct FlatFwdLaunch {
   KParams kp;
   float* y;                       // [G, 8]
   float* saved;                   // [G, kSavedFloats] or NULL
+  uint32_t* hits;                 // [G, kHitWords] hit words while the forward runs
   ContactList cl;                 // the contact list it fills (sorted, counts, offsets)
   float* sval;                    // [cl.cap, 8] contact values, in list order
   long long* sval_key;            // [cl.cap] (SDF piece, feature) keys, in arrival order
@@ -34,6 +38,10 @@ struct FlatFwdLaunch {
   int vmax;                       // most vertices of a feature piece in the batch
   int fmax;                       // most planes of a piece in the batch
   int gate_planes;                // planes staged per gate warp (>= fmax)
+  int stage_tma;                  // stage planes with bulk copies on an mbarrier (1) or loads
+  long long wait_limit;           // polls of a bulk copy's barrier before giving up
+  int* status;                    // CCM_ERR_TIMEOUT when a wait gave up
+  int pdl;                        // launch the stages with programmatic dependent launch
   int n_sm;
 };
 

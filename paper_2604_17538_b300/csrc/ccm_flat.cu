@@ -9,7 +9,7 @@
 //   eval     recomputes each contact (SDF, sphere trace, mollifier) on T;
 //   fold     blends each group's contacts in their fixed order (online
 //            softmax, Sec. 4.4) and forms its adjoint coefficients, J u row
-//            and output-transform terms;
+//            and output-transform terms (one thread per group with contacts);
 //   adjoint  recomputes each contact with its group's coefficients and
 //            back-propagates into its feature points: a force and a torque;
 //   reduce   sums a pair's forces, torques and output terms (one warp per
@@ -22,6 +22,7 @@
 #include "ccm_adjoint.cuh"
 #include "ccm_clist.cuh"
 #include "ccm_flat.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -59,34 +60,43 @@ __device__ __forceinline__ void block_scan2(long long& v, long long& e, long lon
   if (w > 0) { v += wv[w - 1]; e += we[w - 1]; }
 }
 
+// Counts of a tile: the vertex and edge contacts packed into one word (low
+// and high 32 bits; a list's counts fit 31 bits, so the low half never
+// carries) and the number of groups with contacts.
 __global__ void __launch_bounds__(1024) clist_tile_sum_kernel(ContactList cl, int64_t G,
                                                               long long* tile_sum) {
+  pdl_wait();
   __shared__ long long wv[32], we[32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
-  long long sv = 0, se = 0;
+  long long sp = 0, sl = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    if (base + q < G) { sv += cl.cnt_v[base + q]; se += cl.cnt_e[base + q]; }
-  block_scan2(sv, se, wv, we);
+    if (base + q < G) {
+      const long long v = cl.cnt_v[base + q], e = cl.cnt_e[base + q];
+      sp += v | (e << 32);
+      sl += (v + e) > 0;
+    }
+  block_scan2(sp, sl, wv, we);
   if (threadIdx.x == 1023) {
-    tile_sum[2 * blockIdx.x] = sv;
-    tile_sum[2 * blockIdx.x + 1] = se;
+    tile_sum[2 * blockIdx.x] = sp;
+    tile_sum[2 * blockIdx.x + 1] = sl;
   }
 }
 
 __global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_t G,
                                                           const long long* tile_sum) {
+  pdl_wait();
   __shared__ long long wv[32], we[32], pre[2];
   const int t = threadIdx.x;
   // totals of the tiles before this one
-  long long pv = 0, pe = 0;
-  for (int b = t; b < (int)blockIdx.x; b += 1024) { pv += tile_sum[2 * b]; pe += tile_sum[2 * b + 1]; }
+  long long pp = 0, pl = 0;
+  for (int b = t; b < (int)blockIdx.x; b += 1024) { pp += tile_sum[2 * b]; pl += tile_sum[2 * b + 1]; }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    pv += __shfl_xor_sync(kFull, pv, o);
-    pe += __shfl_xor_sync(kFull, pe, o);
+    pp += __shfl_xor_sync(kFull, pp, o);
+    pl += __shfl_xor_sync(kFull, pl, o);
   }
-  if ((t & 31) == 0) { wv[t >> 5] = pv; we[t >> 5] = pe; }
+  if ((t & 31) == 0) { wv[t >> 5] = pp; we[t >> 5] = pl; }
   __syncthreads();
   if (t == 0) {
     long long a = 0, b = 0;
@@ -95,21 +105,22 @@ __global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_
     pre[1] = b;
   }
   __syncthreads();
-  const long long p0v = pre[0], p0e = pre[1];
+  const long long p0 = pre[0], p0l = pre[1];
   __syncthreads();   // wv / we are reused by the scan
   const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * t;
   int cv[4], ce[4];
-  long long sv = 0, se = 0;
+  long long sp = 0, sl = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     cv[q] = base + q < G ? cl.cnt_v[base + q] : 0;
     ce[q] = base + q < G ? cl.cnt_e[base + q] : 0;
-    sv += cv[q];
-    se += ce[q];
+    sp += (long long)cv[q] | ((long long)ce[q] << 32);
+    sl += (cv[q] + ce[q]) > 0;
   }
-  long long iv = sv, ie = se;
-  block_scan2(iv, ie, wv, we);
-  long long ov = p0v + iv - sv, oe = p0e + ie - se;
+  long long ip = sp, il = sl;
+  block_scan2(ip, il, wv, we);
+  const long long op = p0 + ip - sp;
+  long long ov = op & 0xffffffffll, oe = op >> 32, ol = p0l + il - sl;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (base + q < G) {
@@ -117,15 +128,18 @@ __global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_
       cl.off_e[base + q] = (int32_t)oe;
       cl.cnt_v[base + q] = 0;   // the counts become the scatter's cursors
       cl.cnt_e[base + q] = 0;
+      if (cv[q] + ce[q] > 0) cl.live_g[ol++] = (int32_t)(base + q);
     }
     ov += cv[q];
     oe += ce[q];
   }
   if (blockIdx.x == gridDim.x - 1 && t == 1023) {
-    cl.off_v[G] = (int32_t)(p0v + iv);
-    cl.off_e[G] = (int32_t)(p0e + ie);
-    cl.ctl[kCtlNV] = (unsigned long long)(p0v + iv);
-    cl.ctl[kCtlNE] = (unsigned long long)(p0e + ie);
+    const long long tp = p0 + ip;
+    cl.off_v[G] = (int32_t)(tp & 0xffffffffll);
+    cl.off_e[G] = (int32_t)(tp >> 32);
+    cl.ctl[kCtlNV] = (unsigned long long)(tp & 0xffffffffll);
+    cl.ctl[kCtlNE] = (unsigned long long)(tp >> 32);
+    cl.ctl[kCtlNG] = (unsigned long long)(p0l + il);
     cl.ctl[kCtlTag] = cl.tag;
   }
 }
@@ -133,6 +147,7 @@ __global__ void __launch_bounds__(1024) clist_scan_kernel(ContactList cl, int64_
 // Every record to its place: vertex contacts in [0, NV) by group and rank,
 // then edge contacts in [NV, NV + NE).
 __global__ void clist_scatter_kernel(ContactList cl) {
+  pdl_wait();
   if (cl.ctl[kCtlOverflow]) return;
   const int64_t n = (int64_t)cl.ctl[kCtlCursor];
   const int64_t NV = (int64_t)cl.ctl[kCtlNV];
@@ -150,19 +165,20 @@ __global__ void clist_scatter_kernel(ContactList cl) {
 
 int64_t flat_scan_tiles(int64_t G) { return std::max<int64_t>(1, (G + kScanTile - 1) / kScanTile); }
 
-cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream) {
+cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream,
+                                  bool pdl) {
   const int64_t tiles = flat_scan_tiles(G);
-  clist_tile_sum_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(pdl, clist_tile_sum_kernel, (int)tiles, 1024, 0, stream, cl, G,
+                           cl.tile_sum);
   if (e != cudaSuccess) return e;
-  clist_scan_kernel<<<(int)tiles, 1024, 0, stream>>>(cl, G, cl.tile_sum);
-  return cudaGetLastError();
+  return launch_k(pdl, clist_scan_kernel, (int)tiles, 1024, 0, stream, cl, G, cl.tile_sum);
 }
 
 cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream) {
   cudaError_t e = launch_flat_prep_scan(cl, G, stream);
   if (e != cudaSuccess) return e;
   clist_scatter_kernel<<<4 * n_sm, 256, 0, stream>>>(cl);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -269,6 +285,7 @@ __device__ __forceinline__ void flush_counts(const FlatCounts& c, unsigned long 
 // ---------------------------------------------------------------------------
 template <class T, bool kCount>
 __global__ void __launch_bounds__(128) flat_eval_kernel(FlatLaunch L) {
+  pdl_wait();
   if (L.fp.sched[2]) return;
   const int lane = threadIdx.x & 31;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NE = (int64_t)L.cl.ctl[kCtlNE];
@@ -330,40 +347,36 @@ __global__ void __launch_bounds__(128) flat_eval_kernel(FlatLaunch L) {
 }
 
 // ---------------------------------------------------------------------------
-// fold: one group per thread
+// fold: one group with contacts per thread (the scan's list of them); the
+// groups without contacts have no adjoint, and the reduce kernel gives them
+// zero output terms and tangent rows
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
+  pdl_wait();
   if (L.fp.sched[2]) return;
-  const int64_t NV = (int64_t)L.cl.ctl[kCtlNV];
+  const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NG = (int64_t)L.cl.ctl[kCtlNG];
   const T* cval = static_cast<const T*>(L.fp.cval);
   Coef<T>* coef = static_cast<Coef<T>*>(L.fp.coef);
   T* ot = static_cast<T*>(L.fp.oterm);
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.G;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    T* o = ot + 6 * g;
-    const int64_t v0 = L.cl.off_v[g], v1 = L.cl.off_v[g + 1];
-    const int64_t e0 = L.cl.off_e[g], e1 = L.cl.off_e[g + 1];
-    if (v0 == v1 && e0 == e1) {   // no contact: no adjoint, zero output terms and tangents
-      for (int q = 0; q < 6; ++q) o[q] = T(0.f);
-      if (L.jvp)
-        for (int q = 0; q < 8; ++q) L.jvp[8 * g + q] = 0.f;
-      continue;
-    }
-    PartT<T> acc;
-    part_zero(acc);
-    fold_range(cval, v0, v1, L.kp.c_blend, acc);
-    fold_range(cval, NV + e0, NV + e1, L.kp.c_blend, acc);
-    const int rp = L.row_pair[g];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < NG;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = L.cl.live_g[i];
+    const int rp = L.row_pair[g];   // the pose's loads overlap the folds
     const int64_t pair = rp >> 1;
     const int side = rp & 1;
     PoseT<T> PS;
     load_pose_t((side == 0 ? L.pose_b : L.pose_a) + 12 * pair,
                 L.dir ? L.dir + 12 * pair + (side == 0 ? 6 : 0) : nullptr, PS);
+    PartT<T> acc;
+    part_zero(acc);
+    fold_range(cval, L.cl.off_v[g], L.cl.off_v[g + 1], L.kp.c_blend, acc);
+    fold_range(cval, NV + L.cl.off_e[g], NV + L.cl.off_e[g + 1], L.kp.c_blend, acc);
     Coef<T> cf;
     V3T<T> ow, ov;
     form_coef(acc, L.ybar + 8 * g, PS, L.jvp ? L.jvp + 8 * g : nullptr, cf, ow, ov);
     coef[g] = cf;
+    T* o = ot + 6 * g;
     o[0] = ow.x; o[1] = ow.y; o[2] = ow.z;
     o[3] = ov.x; o[4] = ov.y; o[5] = ov.z;
   }
@@ -374,6 +387,7 @@ __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
 // ---------------------------------------------------------------------------
 template <class T, bool kCount>
 __global__ void __launch_bounds__(128) flat_adjoint_kernel(FlatLaunch L) {
+  pdl_wait();
   if (L.fp.sched[2]) return;
   const int lane = threadIdx.x & 31;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NE = (int64_t)L.cl.ctl[kCtlNE];
@@ -444,6 +458,7 @@ template <class T> __device__ __forceinline__ V3T<T> warp_sum3(V3T<T> a) {
 
 template <class T>
 __global__ void __launch_bounds__(128) flat_reduce_kernel(FlatLaunch L) {
+  pdl_wait();
   if (L.fp.sched[2]) return;
   const int lane = threadIdx.x & 31;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV];
@@ -465,7 +480,14 @@ __global__ void __launch_bounds__(128) flat_reduce_kernel(FlatLaunch L) {
       add3(M, force + 6 * k + 3);
     }
     for (int64_t g = g0 + lane; g < g1; g += 32) {
-      if (g - g0 < npA) {   // side 0: the SDF body is B
+      if (L.cl.off_v[g + 1] == L.cl.off_v[g] && L.cl.off_e[g + 1] == L.cl.off_e[g]) {
+        // no contact: no output terms, a zero tangent row
+        if (L.jvp) {
+          float4* jr = reinterpret_cast<float4*>(L.jvp + 8 * g);
+          jr[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+          jr[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      } else if (g - g0 < npA) {   // side 0: the SDF body is B
         add3(oBw, ot + 6 * g);
         add3(oBv, ot + 6 * g + 3);
       } else {
@@ -507,6 +529,7 @@ void flat_pass_bytes(bool dual, int64_t cap, int64_t G, size_t* cval, size_t* fo
 // The pass uses the list only if it did not overflow and the saved record
 // carries its tag (the record and the list come from the same forward).
 __global__ void flat_gate_kernel(ContactList cl, const float* __restrict__ saved, int* sched) {
+  pdl_wait();
   const uint32_t tag = reinterpret_cast<const uint32_t*>(saved)[kSavedTag];
   sched[0] = 0;
   sched[1] = 0;
@@ -516,26 +539,21 @@ __global__ void flat_gate_kernel(ContactList cl, const float* __restrict__ saved
 
 template <class T>
 static cudaError_t launch_flat_t(const FlatLaunch& L, cudaStream_t stream) {
-  flat_gate_kernel<<<1, 1, 0, stream>>>(L.cl, L.saved, L.fp.sched);
-  cudaError_t e = cudaGetLastError();
+  const bool pdl = L.pdl != 0;
+  cudaError_t e = launch_k(pdl, flat_gate_kernel, 1, 1, 0, stream, L.cl, L.saved, L.fp.sched);
   if (e != cudaSuccess) return e;
   const int rec_blocks = 16 * L.n_sm;   // persistent: warps draw 32 contacts at a time
-  if (L.counters)
-    flat_eval_kernel<T, true><<<rec_blocks, 128, 0, stream>>>(L);
-  else
-    flat_eval_kernel<T, false><<<rec_blocks, 128, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 64 * L.n_sm));
-  flat_fold_kernel<T><<<gb, 128, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (L.counters)
-    flat_adjoint_kernel<T, true><<<rec_blocks, 128, 0, stream>>>(L);
-  else
-    flat_adjoint_kernel<T, false><<<rec_blocks, 128, 0, stream>>>(L);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_k(pdl, L.counters ? flat_eval_kernel<T, true> : flat_eval_kernel<T, false>,
+               rec_blocks, 128, 0, stream, L);
+  if (e != cudaSuccess) return e;
+  // groups with contacts: at most G, and one thread each
+  const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 8 * L.n_sm));
+  if ((e = launch_k(pdl, flat_fold_kernel<T>, gb, 128, 0, stream, L)) != cudaSuccess) return e;
+  e = launch_k(pdl, L.counters ? flat_adjoint_kernel<T, true> : flat_adjoint_kernel<T, false>,
+               rec_blocks, 128, 0, stream, L);
+  if (e != cudaSuccess) return e;
   const int pb = (int)std::max<int64_t>(1, std::min<int64_t>((L.n_pairs + 3) / 4, 64 * L.n_sm));
-  flat_reduce_kernel<T><<<pb, 128, 0, stream>>>(L);
-  return cudaGetLastError();
+  return launch_k(pdl, flat_reduce_kernel<T>, pb, 128, 0, stream, L);
 }
 
 cudaError_t launch_flat_backward(const FlatLaunch& L, cudaStream_t stream) {

@@ -37,6 +37,7 @@ struct FlatLaunch {
   float* jvp;                // [G, 8] or NULL
   unsigned long long* counters;   // optional work counters (CCM_BWD_CNT_*)
   int n_sm;
+  int pdl;                   // launch the stages with programmatic dependent launch
 };
 
 // Bytes of one pass's scratch (FlatPass) for capacity cap and G groups.
@@ -46,7 +47,8 @@ void flat_pass_bytes(bool dual, int64_t cap, int64_t G, size_t* cval, size_t* fo
 int64_t flat_scan_tiles(int64_t G);
 // The scan alone: offsets from the group counts (which it zeroes, leaving
 // them as cursors), the totals and the tag.
-cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream);
+cudaError_t launch_flat_prep_scan(const ContactList& cl, int64_t G, cudaStream_t stream,
+                                  bool pdl = false);
 // After a forward that filled cl: scan of the group counts and the scatter
 // of the records into their fixed order.
 cudaError_t launch_flat_prep(const ContactList& cl, int64_t G, int n_sm, cudaStream_t stream);

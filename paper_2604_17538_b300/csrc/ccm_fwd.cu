@@ -15,6 +15,7 @@
 #include "ccm_narrow.cuh"
 #include "ccm_unit.cuh"
 #include "ccm_fwd.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -407,7 +408,9 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
             bulk_copy_g2s(sl.planes, g.planes + g.pieces[S.p0 + sc0].f0, 16u * (uint32_t)P,
                           sl.mbar);
           }
-          const bool ok = mbar_wait_bounded(sl.mbar, phase, us.wait_limit);
+          // the whole warp gives up together (a lane may see the phase
+          // complete on the poll after another lane's last one)
+          const bool ok = __all_sync(kFull, mbar_wait_bounded(sl.mbar, phase, us.wait_limit));
           if (!ok) {
             // record the timeout, let the copy land, and stop this warp
             if (lane == 0 && status) atomicExch(status, (int)CCM_ERR_TIMEOUT);
@@ -503,6 +506,7 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
   else
     unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
                                                               L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status, L.only_if);
+  count_launch();
   return cudaGetLastError();
 }
 

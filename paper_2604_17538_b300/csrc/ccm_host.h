@@ -101,7 +101,8 @@ struct Batch {
   // flat forward (ccm_ffwd.cu): directions per unit, relative poses, live
   // directions, candidate contacts and their values, the list's values
   int64_t n_dirs = 0, cand_cap = 0;
-  DevBuf d_unit_dir_off, d_rel, d_live, d_cand, d_cand_m, d_cval, d_sval, d_skey, d_ffctl;
+  DevBuf d_unit_dir_off, d_rel, d_live, d_cand, d_cand_m, d_cval, d_sval, d_skey, d_ffctl,
+      d_ffhits;
   ContactList contact_list() const;
   FlatPass flat_pass(bool dual) const;
   void release();

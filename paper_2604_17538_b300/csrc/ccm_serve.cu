@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "ccm_host.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -231,6 +232,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   serve_gather<<<sv->ctx->n_sm * 4, 256, 0, s.stream>>>(
       reqs, wc, static_cast<float*>(s.d_pose_a.ptr), static_cast<float*>(s.d_pose_b.ptr),
       static_cast<float*>(s.d_ybar.ptr));
+  count_launch();
   FwdLaunch F;
   F.g = sv->ctx->dev_geom();
   F.pairs = static_cast<const PairRec*>(s.d_pairs.ptr);
@@ -277,6 +279,7 @@ static void launch_wave_graph(Serving* sv, WaveSet& s, bool reverse) {
   if (reverse) launch_backward(B, s.stream);
   serve_scatter<<<sv->ctx->n_sm * 4, 256, 0, s.stream>>>(
       reqs, wc, static_cast<const float*>(s.d_y.ptr), static_cast<const float*>(s.d_grad.ptr));
+  count_launch();
 }
 
 static ccm_status setup_set(Serving* sv, WaveSet& s) {

@@ -18,6 +18,7 @@
 
 #include "ccm_narrow.cuh"
 #include "ccm_spline.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -168,6 +169,7 @@ cudaError_t launch_spline_forward(const SplineLaunch& L, cudaStream_t stream) {
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((L.G + 3) / 4, 64 * L.n_sm));
   spline_fwd_kernel<<<(int)blocks, 128, 0, stream>>>(L.g, L.splines, L.coef, L.pairs, L.row_pair,
                                                       L.G, L.pose_a, L.pose_b, L.kp, L.y);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 
 #include "ccm_narrow.cuh"
 #include "ccm_union.h"
+#include "ccm_launch.h"
 
 namespace ccm {
 
@@ -167,6 +168,7 @@ cudaError_t launch_union_forward(const UnionLaunch& L, cudaStream_t stream) {
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((L.G + 3) / 4, 64 * L.n_sm));
   union_fwd_kernel<<<(int)blocks, 128, 0, stream>>>(L.g, L.pairs, L.row_pair, L.G, L.pose_a,
                                                      L.pose_b, L.kp, L.y);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 overlapped with the kernels on side streams, returns exactly what the device
 calls (ccm_contacts_save, ccm_contacts_backward_saved with and without a
 direction) return on the same data -- same kernels, same inputs -- in every
-mode (forward only, + gradient, + H u / J u), across repeated calls whose
-buffers are reused, and it rejects the mode errors."""
+mode (forward only, + gradient, + H u / J u; with a direction the gradient is
+that of the forward-over-reverse pass), across repeated calls whose buffers
+are reused, and it rejects the mode errors."""
 import numpy as np
 import pytest
 
@@ -31,9 +32,9 @@ def _device_step(batch, pa, pb, yb, u):
     saved = batch.saved_buffer()
     y = batch.contacts(pa, pb, saved=saved)
     g, _, _ = batch.backward(pa, pb, yb, saved=saved)
-    _, h, j = batch.backward(pa, pb, yb, u, want_jvp=True, saved=saved)
+    g2, h, j = batch.backward(pa, pb, yb, u, want_jvp=True, saved=saved)
     torch.cuda.synchronize()
-    return [t.cpu().numpy() for t in (y, g, h, j)]
+    return [t.cpu().numpy() for t in (y, g, h, j, g2)]
 
 
 def _host_inputs(sc, seed):
@@ -55,7 +56,7 @@ def test_step_host_equals_device_calls(ctx, scene):
         ref = _device_step(batch, pa_h.cuda(), pb_h.cuda(), yb_h.cuda(), u_h.cuda())
         y, g, h, j = batch.step_host(pa_h, pb_h, yb_h, u_h, want_jvp=True)
         torch.cuda.synchronize()
-        for name, a, b in zip("yghj", (y, g, h, j), ref):
+        for name, a, b in zip("yghj", (y, g, h, j), (ref[0], ref[4], ref[2], ref[3])):
             assert np.array_equal(a.numpy(), b), (seed, name, np.abs(a.numpy() - b).max())
         assert np.isfinite(g.numpy()).all() and np.abs(g.numpy()).max() > 0
 
