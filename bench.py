@@ -709,7 +709,13 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
     def per_request(P):
         """Plain per-request launches, in arrival order on one stream."""
         arr = P["arr"]
-        batches = [ctx.batch(P["A"][k], P["B"][k]) for k in range(n_req)]
+        # one small batch per request; the per-item kernels (no contact list),
+        # so that thousands of planned batches do not each hold list buffers
+        batches = []
+        for k in range(n_req):
+            b = ctx.batch(P["A"][k], P["B"][k])
+            b.set_tuning(flat_records=-1)
+            batches.append(b)
         prm = C.byref(api._params(None))
         stream = torch.cuda.current_stream()
         sh = stream.cuda_stream

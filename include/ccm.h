@@ -94,9 +94,10 @@ typedef enum {
 #define CCM_FLAG_SPLINE 8u
 /* VOXEL_CULL: the forward also culls with the voxel grids of
  * ccm_build_voxel_grids (Sec. 4.3 broad phase: a vertex whose voxel's lower
- * bound of the SDF is >= d_max, an edge whose corners' bounds minus its
- * length are); culls are exact, so outputs equal those without the flag to
- * float rounding.  Without grids the flag changes nothing. */
+ * bound b of the SDF is >= d_max, an edge whose corners' bounds give
+ * (b_I + b_II - length) / 2 >= d_max); culls are exact, so outputs equal
+ * those without the flag to float rounding.  Without grids the flag changes
+ * nothing. */
 #define CCM_FLAG_VOXEL_CULL 16u
 
 /* Method constants.  The paper fixes none of these values (Sec. 2-4). */
@@ -228,8 +229,9 @@ typedef struct {
                                  groups), 0..32 */
   int32_t flat_records;       /* capacity of the contact list that ccm_contacts_save keeps
                                  for the per-contact reverse passes, in records per output
-                                 group (0: 16, and at least 65,536 in all; -1: no list, the
-                                 reverse passes re-gate per pair), -1..4096 */
+                                 group (0: 16, and at least 4,096 in all; -1: no list, the
+                                 reverse passes re-gate per pair and the forward runs per
+                                 item), -1..4096 */
   int32_t stage_tma;          /* forward (per-item kernel and flat stages): stage the SDF
                                  planes into shared memory with bulk (TMA) copies (0) or
                                  plain loads (-1) */

@@ -70,7 +70,7 @@ __device__ SdfT<Dual> sdf_dual(const float4* __restrict__ pl, int nf, V3T<Dual> 
     S = Gx = Gy = Gz = Pd = Dx = Dy = Dz = 0.f;
     Ax = Ay = Az = Bx = By = Bz = Cx = Cy = Cz = 0.f;
     float mx = -INFINITY;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nf; ++k) {
       const float4 p = pl[k];
       const float ph = fmaf(p.x, xv, fmaf(p.y, yv, fmaf(p.z, zv, p.w)));
@@ -137,7 +137,7 @@ __device__ SdfT<T> sdf_t(const float4* __restrict__ pl, int nf, V3T<T> x, float 
     const float sc = s * kp.c_sdf;
     T S(0.f), gx(0.f), gy(0.f), gz(0.f), hx(0.f), hy(0.f), hz(0.f);
     float mx = -INFINITY;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nf; ++k) {
       const float4 p = pl[k];
       const T ph = fma_t(p.x, x.x, fma_t(p.y, x.y, fma_t(p.z, x.z, T(p.w))));
@@ -192,7 +192,7 @@ __device__ void sdf_dual2(const float4* __restrict__ pl, int nf, V3T<Dual> xa, f
     Sa = Gxa = Gya = Gza = Pda = Dxa = Dya = Dza = 0.f;
     Sb = Gxb = Gyb = Gzb = Pdb = Dxb = Dyb = Dzb = 0.f;
     float mxa = -INFINITY, mxb = -INFINITY;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nf; ++k) {
       const float4 p = pl[k];
       const float pha = fmaf(p.x, xav, fmaf(p.y, yav, fmaf(p.z, zav, p.w)));
@@ -249,7 +249,7 @@ __device__ void sdf_t2(const float4* __restrict__ pl, int nf, V3T<T> xa, float s
       const float sca = sa * kp.c_sdf, scb = sb * kp.c_sdf;
       T Sa(0.f), gxa(0.f), gya(0.f), gza(0.f), Sb(0.f), gxb(0.f), gyb(0.f), gzb(0.f);
       float mxa = -INFINITY, mxb = -INFINITY;
-#pragma unroll 2
+#pragma unroll 4
       for (int k = 0; k < nf; ++k) {
         const float4 p = pl[k];
         const T pha = fma_t(p.x, xa.x, fma_t(p.y, xa.y, fma_t(p.z, xa.z, T(p.w))));

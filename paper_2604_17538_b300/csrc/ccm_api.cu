@@ -890,7 +890,7 @@ ccm_status setup_flat(Context* c, Batch* bt) {
   int64_t cap = 0;
   if (bt->per_pair && bt->G > 0 && fr >= 0)
     cap = fr > 0 ? fr * bt->G
-                 : std::min<int64_t>(std::max<int64_t>(16 * bt->G, 65536), (int64_t)1 << 24);
+                 : std::min<int64_t>(std::max<int64_t>(16 * bt->G, 4096), (int64_t)1 << 24);
   if (cap == bt->flat_cap) return CCM_OK;
   for (DevBuf* b : {&bt->d_fctl, &bt->d_fcnt, &bt->d_foff, &bt->d_frecs, &bt->d_fsorted,
                    &bt->d_ftiles, &bt->d_unit_dir_off, &bt->d_rel, &bt->d_live, &bt->d_cand,
@@ -934,7 +934,7 @@ ccm_status setup_flat(Context* c, Batch* bt) {
       off[2 * i + 2] = off[2 * i + 1] + d;
     }
     bt->n_dirs = off.back();
-    bt->cand_cap = std::min<int64_t>(std::max<int64_t>(64 * bt->G, (int64_t)1 << 18),
+    bt->cand_cap = std::min<int64_t>(std::max<int64_t>(64 * bt->G, (int64_t)1 << 14),
                                      (int64_t)1 << 25);
     if ((s = upload(bt->d_unit_dir_off, off, "direction offsets")) != CCM_OK ||
         (s = alloc(bt->d_rel, 12 * sizeof(float) * 2 * (size_t)bt->n, "relative poses")) != CCM_OK ||

@@ -355,7 +355,9 @@ __global__ void __launch_bounds__(128, 8) ff_feature_kernel(FlatFwdLaunch L) {
         const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
         const float lb = edge_plane_bound(planes[am[i0] & kPlaneMask], planes[am[i1] & kPlaneMask],
                                           dx, dy, dz, m[i0], m[i1]);
-        const float vlb = fminf(vb[i0], vb[i1]) - sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        // the max-plane value is 1-Lipschitz: along the edge it stays above
+        // (b_I + b_II - L) / 2 for lower bounds b at the corners
+        const float vlb = 0.5f * (vb[i0] + vb[i1] - sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
         live = no_cull || (lb - kEdgeTol < d_max && vlb - kVoxTol < d_max);
         rec = make_int4(row, s_glob, f_glob, (int)((1u << 31) | (uint32_t)k));
         mm = make_float2(m[i0], m[i1]);

@@ -149,8 +149,8 @@ __device__ void run_list(const DevGeom& g, const UnitSlice& sl, const int* dsub,
                                         sl.planes[s.x + (sl.am[t1v] & kPlaneMask)], dx, dy, dz,
                                         sl.m[t0v], sl.m[t1v]);
       // Sec. 4.3 voxel edge bound: min(phi_1, phi_2) - r - l (r inside vb)
-      const float vlb = fminf(sl.vb[t0v], sl.vb[t1v]) -
-                        sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      // 1-Lipschitz max-plane value: above (b_I + b_II - L) / 2 along the edge
+      const float vlb = 0.5f * (sl.vb[t0v] + sl.vb[t1v] - sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
       live = no_cull || (lb - kEdgeTol < kp.d_max && vlb - kVoxTol < kp.d_max);
       if (live) { sl.need[t0v] = 1; sl.need[t1v] = 1; }
     }
