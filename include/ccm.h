@@ -235,9 +235,9 @@ typedef struct {
   int32_t stage_tma;          /* forward (per-item kernel and flat stages): stage the SDF
                                  planes into shared memory with bulk (TMA) copies (0) or
                                  plain loads (-1) */
-  int32_t stage_wait;         /* bound of a bulk copy's wait, in polls of its barrier
-                                 (0: 2^22; -1: none, so that every wait runs out -- for
-                                 tests of the timeout path), -1..2^30 */
+  int32_t stage_wait;         /* bound of a bulk copy's wait, in polls of its barrier, each
+                                 suspending at most 1 us (0: 2^22; -1: none, so that every
+                                 wait runs out -- for tests of the timeout path), -1..2^30 */
   int32_t flat_forward;       /* forward as flat stages (gate per direction, culls per live
                                  direction, one contact per thread, fold per group) on a
                                  batch with a contact list (0), or one warp per work item

@@ -296,13 +296,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// One poll: returns when the phase completes or after a suspend of at most
+// kPollHintNs (the hint keeps a waiting warp from spinning through issue
+// slots while a copy is in flight).
+constexpr uint32_t kPollHintNs = 1000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kPollHintNs)
       : "memory");
   return ok != 0u;
 }
@@ -315,7 +319,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
-constexpr long long kDrainLimit = 1ll << 28;
+constexpr long long kDrainLimit = 1ll << 24;
 
 // Waits, in a kernel launched with programmatic dependent launch, until the
 // previous kernel of the stream has completed and its writes are visible

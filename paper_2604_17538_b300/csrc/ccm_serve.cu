@@ -747,7 +747,12 @@ ccm_status ccm_submit(ccm_ctx ctx, const ccm_request* req, ccm_ticket* out) {
   *out = p.ticket;
   sv->queued_pairs += p.d.n;
   sv->queue.push_back(std::move(p));
-  sv->cv.notify_one();
+  // Wake the scheduler when it has something new to decide: a queue that was
+  // empty (an idle loop launches at once) or one that now fills half a wave
+  // (a second wave may go out).  Otherwise it wakes on a wave's completion or
+  // its own 100 us re-check; waking it on every submission made the
+  // submitting thread and the scheduler trade the lock at the arrival rate.
+  if (sv->queue.size() == 1 || 2 * sv->queued_pairs >= sv->cap_pairs) sv->cv.notify_one();
   return CCM_OK;
 }
 
