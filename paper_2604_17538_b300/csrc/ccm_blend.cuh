@@ -133,6 +133,61 @@ template <class T> __device__ __forceinline__ PartT<T> part_shfl_down(const Part
   return r;
 }
 
+template <class T> __device__ __forceinline__ V3T<T> shfl_xor3(V3T<T> x, int o) {
+  return v3(shfl_xor_t(x.x, o), shfl_xor_t(x.y, o), shfl_xor_t(x.z, o));
+}
+template <class T> __device__ __forceinline__ PartT<T> part_shfl_xor(const PartT<T>& c, int o) {
+  PartT<T> r;
+  r.M = shfl_xor_t(c.M, o); r.U = shfl_xor_t(c.U, o);
+  r.rd = shfl_xor_t(c.rd, o); r.rf = shfl_xor_t(c.rf, o);
+  r.rp = shfl_xor3(c.rp, o); r.rn = shfl_xor3(c.rn, o);
+  r.Dd = shfl_xor_t(c.Dd, o); r.Da = shfl_xor_t(c.Da, o);
+  r.Dp = shfl_xor3(c.Dp, o); r.Dn = shfl_xor3(c.Dn, o);
+  return r;
+}
+
+// Folds one group's vertex contacts [v0, v1) and then its edge contacts
+// [e0, e1) over kSplit consecutive lanes (an aligned lane group): lane `sub`
+// folds every kSplit-th contact of that sequence, in order, with kBatch
+// contacts' values loaded at a time; the lanes' partials are then combined
+// pairwise in lane order ((0 with 1), (2 with 3), then the pairs), the same
+// operations on every lane of the group, so all of them end with the same
+// partial.  The chain of dependent blends of a long group is kSplit times
+// shorter than one lane's fold.  Every lane of the warp calls it (an empty
+// range gives an empty partial).
+template <class T, int kSplit>
+__device__ void fold_split(const T* cval, int64_t v0, int64_t v1, int64_t e0, int64_t e1,
+                           float c_blend, int sub, PartT<T>& acc) {
+  constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
+  part_zero(acc);
+  const int64_t nv = v1 - v0, n = nv + (e1 - e0);
+  auto at = [&](int64_t t) { return t < nv ? v0 + t : e0 + (t - nv); };
+  int64_t t = sub;
+  for (; t + (kBatch - 1) * kSplit < n; t += kBatch * kSplit) {
+    T v[kBatch][8];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const T* c = cval + 8 * at(t + b * kSplit);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[b][q] = c[q];
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) fold_one(v[b], c_blend, acc);
+  }
+  for (; t < n; t += kSplit) fold_one(cval + 8 * at(t), c_blend, acc);
+#pragma unroll
+  for (int o = 1; o < kSplit; o <<= 1) {
+    const PartT<T> other = part_shfl_xor(acc, o);
+    if (sub & o) {   // the lower lanes' partial first
+      PartT<T> lo = other;
+      part_combine(lo, acc);
+      acc = lo;
+    } else {
+      part_combine(acc, other);
+    }
+  }
+}
+
 // segmented fold of lane contacts sorted by key into the group table
 template <class T>
 __device__ void fold_t(PartT<T> c, int key, PartT<T>* acc, int lane) {

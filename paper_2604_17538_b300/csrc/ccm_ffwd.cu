@@ -19,9 +19,9 @@
 //   rank     one contact per thread: its place in the segment's (SDF piece,
 //            feature) order, where it and its values are written; and every
 //            group's outputs and record written as if it had no contact;
-//   fold     one group with contacts per thread: its vertex contacts, then
-//            its edge contacts, blended in list order (online softmax,
-//            Sec. 4.4) into the group's outputs and saved record.
+//   fold     one group with contacts per four lanes: its vertex contacts,
+//            then its edge contacts, blended (online softmax, Sec. 4.4) in a
+//            fixed order into the group's outputs and saved record.
 // The contact list it leaves is the one the per-contact reverse passes read
 // (ccm_flat.cu).  The fixed order of the fold makes a pair's outputs depend
 // on the pair alone.  Culls are those of the per-item kernel, so the set of
@@ -575,38 +575,52 @@ __global__ void __launch_bounds__(256) ff_rank_kernel(FlatFwdLaunch L) {
 }
 
 // ---------------------------------------------------------------------------
-// fold: one group with contacts per thread (the list of such groups from the
-// scan), its vertex contacts then its edge contacts in list order -- the
-// order and arithmetic of the per-contact reverse passes' own fold
-// (ccm_flat.cu) over the same list
+// fold: one group with contacts (the list of such groups from the scan) per
+// four lanes, its vertex contacts then its edge contacts in list order split
+// over the lanes (fold_split) -- the order and arithmetic of the per-contact
+// reverse passes' own fold (ccm_flat.cu) over the same list
 // ---------------------------------------------------------------------------
+constexpr int kFoldSplit = 4;   // lanes per group in the fold
+
 __global__ void __launch_bounds__(128) ff_fold_kernel(FlatFwdLaunch L) {
   pdl_wait();
   if (L.ctl[kFfOverflow]) return;
   const int64_t NV = (int64_t)L.cl.ctl[kCtlNV], NG = (int64_t)L.cl.ctl[kCtlNG];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < NG;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = L.cl.live_g[i];
-    const int rp = L.row_pair[g];   // the pose's loads overlap the folds
+  const int sub = threadIdx.x & (kFoldSplit - 1);
+  const int64_t per_block = blockDim.x / kFoldSplit;
+  // block-uniform loop: every lane takes part in the fold's shuffles
+  for (int64_t base = (int64_t)blockIdx.x * per_block; base < NG;
+       base += (int64_t)gridDim.x * per_block) {
+    const int64_t i = base + threadIdx.x / kFoldSplit;
+    const bool valid = i < NG;
+    const int64_t g = valid ? L.cl.live_g[i] : 0;
+    int64_t v0 = 0, v1 = 0, e0 = 0, e1 = 0;
     float RS[9], tS[3];
-    load_pose(((rp & 1) == 0 ? L.pose_b : L.pose_a) + 12 * (int64_t)(rp >> 1), RS, tS);
+    if (valid) {
+      v0 = L.cl.off_v[g]; v1 = L.cl.off_v[g + 1];
+      e0 = NV + L.cl.off_e[g]; e1 = NV + L.cl.off_e[g + 1];
+      if (sub == 0) {   // the pose's loads overlap the fold
+        const int rp = L.row_pair[g];
+        load_pose(((rp & 1) == 0 ? L.pose_b : L.pose_a) + 12 * (int64_t)(rp >> 1), RS, tS);
+      }
+    }
     PartT<float> A;
-    part_zero(A);
-    fold_range(L.sval, L.cl.off_v[g], L.cl.off_v[g + 1], L.kp.c_blend, A);
-    fold_range(L.sval, NV + L.cl.off_e[g], NV + L.cl.off_e[g + 1], L.kp.c_blend, A);
-    float yo[8];
-    write_group(yo, A, RS, tS, L.kp);
-    float4* yd = reinterpret_cast<float4*>(L.y + 8 * g);
-    yd[0] = make_float4(yo[0], yo[1], yo[2], yo[3]);
-    yd[1] = make_float4(yo[4], yo[5], yo[6], yo[7]);
-    if (L.saved) {   // the partial (hit words and tag are in place)
-      float* o = L.saved + (int64_t)kSavedFloats * g;
-      o[0] = A.M; o[1] = A.U; o[2] = A.rd; o[3] = A.rf;
-      o[4] = A.rp.x; o[5] = A.rp.y; o[6] = A.rp.z;
-      o[7] = A.rn.x; o[8] = A.rn.y; o[9] = A.rn.z;
-      o[10] = A.Dd; o[11] = A.Da;
-      o[12] = A.Dp.x; o[13] = A.Dp.y; o[14] = A.Dp.z;
-      o[15] = A.Dn.x; o[16] = A.Dn.y; o[17] = A.Dn.z;
+    fold_split<float, kFoldSplit>(L.sval, v0, v1, e0, e1, L.kp.c_blend, sub, A);
+    if (valid && sub == 0) {
+      float yo[8];
+      write_group(yo, A, RS, tS, L.kp);
+      float4* yd = reinterpret_cast<float4*>(L.y + 8 * g);
+      yd[0] = make_float4(yo[0], yo[1], yo[2], yo[3]);
+      yd[1] = make_float4(yo[4], yo[5], yo[6], yo[7]);
+      if (L.saved) {   // the partial (hit words and tag are in place)
+        float* o = L.saved + (int64_t)kSavedFloats * g;
+        o[0] = A.M; o[1] = A.U; o[2] = A.rd; o[3] = A.rf;
+        o[4] = A.rp.x; o[5] = A.rp.y; o[6] = A.rp.z;
+        o[7] = A.rn.x; o[8] = A.rn.y; o[9] = A.rn.z;
+        o[10] = A.Dd; o[11] = A.Da;
+        o[12] = A.Dp.x; o[13] = A.Dp.y; o[14] = A.Dp.z;
+        o[15] = A.Dn.x; o[16] = A.Dn.y; o[17] = A.Dn.z;
+      }
     }
   }
 }
@@ -638,8 +652,9 @@ cudaError_t launch_flat_forward(const FlatFwdLaunch& L, cudaStream_t stream) {
   if ((e = launch_flat_prep_scan(L.cl, L.G, stream, pdl)) != cudaSuccess) return e;
   if ((e = launch_k(pdl, ff_scatter_kernel, 8 * L.n_sm, 256, 0, stream, L)) != cudaSuccess) return e;
   if ((e = launch_k(pdl, ff_rank_kernel, 8 * L.n_sm, 256, 0, stream, L)) != cudaSuccess) return e;
-  // groups with contacts: at most G, and one thread each
-  const int fo = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 8 * L.n_sm));
+  // groups with contacts: at most G, kFoldSplit lanes each
+  const int fo = (int)std::max<int64_t>(
+      1, std::min<int64_t>((kFoldSplit * L.G + 127) / 128, 16 * L.n_sm));
   return launch_k(pdl, ff_fold_kernel, fo, 128, 0, stream, L);
 }
 

@@ -9,7 +9,7 @@
 //   eval     recomputes each contact (SDF, sphere trace, mollifier) on T;
 //   fold     blends each group's contacts in their fixed order (online
 //            softmax, Sec. 4.4) and forms its adjoint coefficients, J u row
-//            and output-transform terms (one thread per group with contacts);
+//            and output-transform terms (four lanes per group with contacts);
 //   adjoint  recomputes each contact with its group's coefficients and
 //            back-propagates into its feature points: a force and a torque;
 //   reduce   sums a pair's forces, torques and output terms (one warp per
@@ -347,10 +347,12 @@ __global__ void __launch_bounds__(128) flat_eval_kernel(FlatLaunch L) {
 }
 
 // ---------------------------------------------------------------------------
-// fold: one group with contacts per thread (the scan's list of them); the
-// groups without contacts have no adjoint, and the reduce kernel gives them
-// zero output terms and tangent rows
+// fold: one group with contacts per kFoldSplit lanes (the scan's list of
+// them; fold_split); the groups without contacts have no adjoint, and the
+// reduce kernel gives them zero output terms and tangent rows
 // ---------------------------------------------------------------------------
+constexpr int kFoldSplit = 4;   // lanes per group in the folds
+
 template <class T>
 __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
   pdl_wait();
@@ -359,26 +361,38 @@ __global__ void __launch_bounds__(128) flat_fold_kernel(FlatLaunch L) {
   const T* cval = static_cast<const T*>(L.fp.cval);
   Coef<T>* coef = static_cast<Coef<T>*>(L.fp.coef);
   T* ot = static_cast<T*>(L.fp.oterm);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < NG;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = L.cl.live_g[i];
-    const int rp = L.row_pair[g];   // the pose's loads overlap the folds
-    const int64_t pair = rp >> 1;
-    const int side = rp & 1;
+  const int sub = threadIdx.x & (kFoldSplit - 1);
+  const int64_t per_block = blockDim.x / kFoldSplit;
+  // block-uniform loop: every lane takes part in the fold's shuffles
+  for (int64_t base = (int64_t)blockIdx.x * per_block; base < NG;
+       base += (int64_t)gridDim.x * per_block) {
+    const int64_t i = base + threadIdx.x / kFoldSplit;
+    const bool valid = i < NG;
+    const int64_t g = valid ? L.cl.live_g[i] : 0;
+    int64_t v0 = 0, v1 = 0, e0 = 0, e1 = 0;
     PoseT<T> PS;
-    load_pose_t((side == 0 ? L.pose_b : L.pose_a) + 12 * pair,
-                L.dir ? L.dir + 12 * pair + (side == 0 ? 6 : 0) : nullptr, PS);
+    if (valid) {
+      v0 = L.cl.off_v[g]; v1 = L.cl.off_v[g + 1];
+      e0 = NV + L.cl.off_e[g]; e1 = NV + L.cl.off_e[g + 1];
+      if (sub == 0) {   // the pose's loads overlap the fold
+        const int rp = L.row_pair[g];
+        const int64_t pair = rp >> 1;
+        const int side = rp & 1;
+        load_pose_t((side == 0 ? L.pose_b : L.pose_a) + 12 * pair,
+                    L.dir ? L.dir + 12 * pair + (side == 0 ? 6 : 0) : nullptr, PS);
+      }
+    }
     PartT<T> acc;
-    part_zero(acc);
-    fold_range(cval, L.cl.off_v[g], L.cl.off_v[g + 1], L.kp.c_blend, acc);
-    fold_range(cval, NV + L.cl.off_e[g], NV + L.cl.off_e[g + 1], L.kp.c_blend, acc);
-    Coef<T> cf;
-    V3T<T> ow, ov;
-    form_coef(acc, L.ybar + 8 * g, PS, L.jvp ? L.jvp + 8 * g : nullptr, cf, ow, ov);
-    coef[g] = cf;
-    T* o = ot + 6 * g;
-    o[0] = ow.x; o[1] = ow.y; o[2] = ow.z;
-    o[3] = ov.x; o[4] = ov.y; o[5] = ov.z;
+    fold_split<T, kFoldSplit>(cval, v0, v1, e0, e1, L.kp.c_blend, sub, acc);
+    if (valid && sub == 0) {
+      Coef<T> cf;
+      V3T<T> ow, ov;
+      form_coef(acc, L.ybar + 8 * g, PS, L.jvp ? L.jvp + 8 * g : nullptr, cf, ow, ov);
+      coef[g] = cf;
+      T* o = ot + 6 * g;
+      o[0] = ow.x; o[1] = ow.y; o[2] = ow.z;
+      o[3] = ov.x; o[4] = ov.y; o[5] = ov.z;
+    }
   }
 }
 
@@ -546,8 +560,9 @@ static cudaError_t launch_flat_t(const FlatLaunch& L, cudaStream_t stream) {
   e = launch_k(pdl, L.counters ? flat_eval_kernel<T, true> : flat_eval_kernel<T, false>,
                rec_blocks, 128, 0, stream, L);
   if (e != cudaSuccess) return e;
-  // groups with contacts: at most G, and one thread each
-  const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((L.G + 127) / 128, 8 * L.n_sm));
+  // groups with contacts: at most G, kFoldSplit lanes each
+  const int gb = (int)std::max<int64_t>(
+      1, std::min<int64_t>((kFoldSplit * L.G + 127) / 128, 16 * L.n_sm));
   if ((e = launch_k(pdl, flat_fold_kernel<T>, gb, 128, 0, stream, L)) != cudaSuccess) return e;
   e = launch_k(pdl, L.counters ? flat_adjoint_kernel<T, true> : flat_adjoint_kernel<T, false>,
                rec_blocks, 128, 0, stream, L);
