@@ -554,6 +554,9 @@ def run_uneven(args, rank, world):
     # exact work counters of both passes (after the timed loops)
     cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
     batch.contacts(pa, pb, counters=cnt)
+    # a fresh record and contact list for the counted reverse pass (the counted
+    # forward keeps none), so that it counts the per-contact pass the step runs
+    batch.contacts(pa, pb, out=y, saved=saved)
     cnt_v = torch.zeros(8, dtype=torch.int64, device="cuda")
     batch.backward(pa, pb, ybar, saved=saved, counters=cnt_v)
     counters = dict(zip(abi.COUNTER_NAMES, cnt.cpu().tolist()))

@@ -221,8 +221,9 @@ typedef struct {
   int32_t item_vb, item_eb;   /* reverse pass: vertex / edge items per list */
   int32_t fwd_warps;          /* forward warps per block, 1..4 */
   int32_t groups;             /* feature pieces per work item, 1..32 */
-  int32_t stage_planes;       /* most SDF-body planes staged at once (0: 1024; at least
-                                 the largest piece's), 0 or 16..4096 */
+  int32_t stage_planes;       /* most SDF-body planes staged at once (0: 1024 per work item,
+                                 512 per warp in the flat gate, which takes at most 760;
+                                 at least the largest piece's), 0 or 16..4096 */
   int32_t stage_verts;        /* most feature-piece vertices staged at once, edges
                                  3x that (0: 512; at least the largest piece's), 0 or 16..4096 */
   int32_t groups_b;           /* reverse pass: feature pieces per chunk (0: 4; at most

@@ -1275,7 +1275,15 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
     F.counters = counters;
     F.vmax = b->mx.vmax;
     F.fmax = b->mx.fmax;
-    F.gate_planes = std::max(b->mx.fmax, std::min(b->mx.s_planes, 760));   // 4 warps in 48 KB
+    // the gate stages the SDF body's planes per chunk (4 warps in 48 KB) unless a
+    // piece is so large that a warp's chunk would hold few directions' planes
+    // for a lot of shared memory; then it reads them from global memory
+    // (tuning stage_planes bounds the chunk, as for the per-item kernel)
+    // (512 by default: on the uneven batch 2.37 ms against 2.51 ms with 760)
+    const int gate_cap = b->tuning.stage_planes ? std::min(b->tuning.stage_planes, 760) : 512;
+    F.gate_planes = b->mx.fmax > kGateStageMaxPlanes
+                        ? 0
+                        : std::max(b->mx.fmax, std::min(b->mx.s_planes, gate_cap));
     F.stage_tma = b->us.stage_tma;
     F.wait_limit = b->us.wait_limit;
     F.status = static_cast<int*>(b->d_status.ptr);

@@ -163,13 +163,16 @@ __global__ void __launch_bounds__(128) ff_gate_kernel(FlatFwdLaunch L) {
         const int t = __shfl_up_sync(kFull, pre, o);
         if (lane >= o) pre += t;
       }
-      const unsigned fit = __ballot_sync(kFull, s0 + lane < S.np && pre <= L.gate_planes);
+      const unsigned fit = __ballot_sync(
+          kFull, s0 + lane < S.np && (L.gate_planes == 0 || pre <= L.gate_planes));
       const int ns = max(1, __popc(fit));            // the prefix sums grow with the lane
       const int P = __shfl_sync(kFull, pre, ns - 1);
       const int p0 = __shfl_sync(kFull, mine.f0, 0) - f_base;
-      __syncwarp();   // the previous chunk is no longer read
-      if (!ff_stage(L, pl_s, L.g.planes + f_base + p0, P, bar, phase, lane)) return;
-      __syncwarp();
+      if (L.gate_planes > 0) {
+        __syncwarp();   // the previous chunk is no longer read
+        if (!ff_stage(L, pl_s, L.g.planes + f_base + p0, P, bar, phase, lane)) return;
+        __syncwarp();
+      }
       // directions f fastest: lanes that share an SDF piece read the same
       // plane (a broadcast) and run the same number of steps
       const int nd = F.np * ns;
@@ -184,7 +187,10 @@ __global__ void __launch_bounds__(128) ff_gate_kernel(FlatFwdLaunch L) {
           const float4 sph = L.g.pieces[F.p0 + f].sphere;
           const float3 c = xform(R, tr, sph);
           int pl = 0;
-          const float mc = max_plane_arg(pl_s + (sf0 - f_base - p0), snf, c.x, c.y, c.z, pl);
+          // staged planes, or (gate_planes = 0, pieces too large to stage
+          // without starving the SM of warps) the planes in global memory
+          const float4* spl = L.gate_planes > 0 ? pl_s + (sf0 - f_base - p0) : L.g.planes + sf0;
+          const float mc = max_plane_arg(spl, snf, c.x, c.y, c.z, pl);
           live = no_cull || mc - sph.w - margin < L.kp.d_max;
           // (output row, F piece, S piece, a plane attaining the max at the centre)
           rec = make_int4((int)(row0 + f), F.p0 + f, S.p0 + s0 + s, pl);
@@ -275,8 +281,13 @@ __global__ void __launch_bounds__(128, 8) ff_feature_kernel(FlatFwdLaunch L) {
   const int64_t n_live = (int64_t)L.ctl[kFfLive];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long c_live = 0, c_maxp = 0, c_feat = 0;
-  for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; d < n_live; d += warps) {
-    const int4 lv = L.live[d];
+  // a persistent grid: each warp takes every warps-th live direction, and the
+  // next one's record is loaded while the current one is processed
+  int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  int4 lv_next = d < n_live ? L.live[d] : make_int4(0, 0, 0, 0);
+  for (; d < n_live; d += warps) {
+    const int4 lv = lv_next;
+    if (d + warps < n_live) lv_next = L.live[d + warps];
     const int row = lv.x, f_glob = lv.y, s_glob = lv.z, pl = lv.w;
     const int64_t u = L.row_pair[row];   // unit = 2 pair + side
     const PieceRec fp = L.g.pieces[f_glob], sp = L.g.pieces[s_glob];
@@ -632,7 +643,9 @@ cudaError_t launch_flat_forward(const FlatFwdLaunch& L, cudaStream_t stream) {
   const int sb = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(L.G, 2 * L.n_pairs) + 255) / 256,
                                                              8 * L.n_sm));
   if ((e = launch_k(pdl, ff_setup_kernel, sb, 256, 0, stream, L)) != cudaSuccess) return e;
-  const int gw = std::max(1, std::min(kGateWarps, kDynSmem / (16 * L.gate_planes)));
+  const int gw = L.gate_planes > 0
+                     ? std::max(1, std::min(kGateWarps, kDynSmem / (16 * L.gate_planes)))
+                     : kGateWarps;
   const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.n_pairs + gw - 1) / gw,
                                                              32 * L.n_sm));
   const size_t gsm = (size_t)gw * 16 * L.gate_planes;
@@ -641,7 +654,8 @@ cudaError_t launch_flat_forward(const FlatFwdLaunch& L, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   int wpb = 1;
   const size_t smem = flat_forward_feature_smem(L.vmax, L.fmax, &wpb);
-  const int fb = 64 * L.n_sm;
+  // persistent: the blocks that stay resident (64 registers: 8 blocks of 4 warps per SM)
+  const int fb = std::max(1, (8 * 4 / wpb)) * L.n_sm;
   e = launch_k(pdl, L.counters ? ff_feature_kernel<true> : ff_feature_kernel<false>, fb, 32 * wpb,
                smem, stream, L);
   if (e != cudaSuccess) return e;

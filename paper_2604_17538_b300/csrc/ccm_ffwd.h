@@ -12,6 +12,10 @@ namespace ccm {
 // the eval stage takes contacts of one kind), overflow flag
 enum { kFfLive = 0, kFfCand = 1, kFfOverflow = 2, kFfSched = 3, kFfCandE = 4, kFfWords = 8 };
 
+// largest piece (in planes) for which the gate stages the SDF body's planes
+// in shared memory; a batch with larger pieces gates from global memory
+constexpr int kGateStageMaxPlanes = 256;
+
 struct FlatFwdLaunch {
   DevGeom g;
   const PairRec* pairs;
@@ -37,7 +41,8 @@ struct FlatFwdLaunch {
   unsigned long long* counters;   // optional CCM_CNT_* work counters
   int vmax;                       // most vertices of a feature piece in the batch
   int fmax;                       // most planes of a piece in the batch
-  int gate_planes;                // planes staged per gate warp (>= fmax)
+  int gate_planes;                // planes staged per gate warp (>= fmax), or 0: the gate
+                                  // reads the planes from global memory
   int stage_tma;                  // stage planes with bulk copies on an mbarrier (1) or loads
   long long wait_limit;           // polls of a bulk copy's barrier before giving up
   int* status;                    // CCM_ERR_TIMEOUT when a wait gave up
