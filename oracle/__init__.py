@@ -16,6 +16,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                           and support, interpolation at the nodes, exact
                           reproduction of linear fields, convergence to a
                           sphere's SDF, and the stacked-cube closed form.
+  * FLAG_UNGATED       -- separated bodies (every contact at d_max: uniform
+                          weights, the mean of the contact points), a fully
+                          immersed body (every f = 1: equal to the gated
+                          blend), the tau_blend -> infinity mean and the
+                          tau_blend -> 0 argmin over every contact.
   * ``sdf``            -- brute-force polytope distance, LSE bounds, tau -> 0 limit.
   * ``edge_point``     -- Cyrus-Beck chord midpoint (many iterations, small tau),
                           inside-edge midpoint, one-step convergence on a face.
@@ -75,6 +80,9 @@ FLAG_PROJECT = 4
 # every SDF piece as its tricubic spline SDF with normal splines (Sec. 3.2);
 # needs a geometry with splines (scenes.attach_splines)
 FLAG_SPLINE = 8
+# the literal "softmax on {d_c}" blend over every contact of a group, f = 0
+# ones included (Sec. 4.4), for comparison with the gated blend
+FLAG_UNGATED = 16
 
 _lib = None
 

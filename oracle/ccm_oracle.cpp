@@ -43,6 +43,11 @@
 //     the paper's basis u (support [-2, 2]); the contact normal is the normal
 //     spline, not the SDF's gradient.  Outside the grid box the SDF continues
 //     as the spline at the nearest box point plus the distance to the box.
+//   * kFlagUngated: the literal reading of "softmax on {d_c}" in Sec. 4.4,
+//     for comparison with the gated blend above: w_c = exp(-d_c/tau_blend) /
+//     sum exp(-d/tau_blend) over EVERY contact of the group, including those
+//     with f_c = 0 (whose mollified depth is exactly d_max); the outputs are
+//     the same sums with these weights, so no group is ever empty.
 //
 // Derivatives: the same templated code runs on forward-mode dual numbers.
 // Dual<double,12> gives the exact gradient with respect to the 12 twist
@@ -211,7 +216,7 @@ struct ccmo_params {
   double d_max;       // distance threshold (Sec. 4.3)
   double gate_width;  // transition bandwidth epsilon (Sec. 4.3)
   int32_t trace_iters;  // sphere-trace iterations (three in Sec. 4.2)
-  int32_t flags;      // kFlagBodyUnion | kFlagProject (forward variants)
+  int32_t flags;      // kFlagBodyUnion | kFlagProject | kFlagSpline | kFlagUngated
 };
 struct ccmo_geom {
   const int64_t* body_piece_off;
@@ -308,6 +313,7 @@ struct PieceSdf {
 constexpr int32_t kFlagBodyUnion = 2;
 constexpr int32_t kFlagProject = 4;
 constexpr int32_t kFlagSpline = 8;
+constexpr int32_t kFlagUngated = 16;
 
 // --------------------------------------------------------------------------
 // Sec. 3.2: cubic spline basis u(t) = 4 - 6|t|^2 + 3|t|^3 on |t| <= 1,
@@ -490,10 +496,13 @@ template <class T>
 Group<T> blend(const std::vector<Contact<T>>& cs, const std::vector<V3<T>>& pw,
                const std::vector<V3<T>>& nw, const ccmo_params& prm) {
   Group<T> g;
-  // logits l_c = -d_c / tau_blend over contacts with f_c > 0, max-shifted
+  // logits l_c = -d_c / tau_blend over contacts with f_c > 0 (every contact
+  // for the ungated reading), max-shifted
+  const bool gated = !(prm.flags & kFlagUngated);
   int cmax = -1;
   for (size_t c = 0; c < cs.size(); ++c)
-    if (val(cs[c].f) > 0.0 && (cmax < 0 || val(cs[c].dc) < val(cs[cmax].dc))) cmax = (int)c;
+    if ((!gated || val(cs[c].f) > 0.0) && (cmax < 0 || val(cs[c].dc) < val(cs[cmax].dc)))
+      cmax = (int)c;
   if (cmax < 0) {  // no active contact
     g.d = T(prm.d_max); g.a = T(0.0); g.p = zero3<T>(); g.n = zero3<T>();
     return g;
@@ -502,8 +511,9 @@ Group<T> blend(const std::vector<Contact<T>>& cs, const std::vector<V3<T>>& pw,
   T U(0.0), D(0.0), A(0.0);
   V3<T> P = zero3<T>(), N = zero3<T>();
   for (size_t c = 0; c < cs.size(); ++c) {
-    if (!(val(cs[c].f) > 0.0)) continue;
-    T u = cs[c].f * exp(-cs[c].dc / prm.tau_blend - M);
+    if (gated && !(val(cs[c].f) > 0.0)) continue;
+    T u = exp(-cs[c].dc / prm.tau_blend - M);
+    if (gated) u = cs[c].f * u;
     U = U + u;
     D = D + u * cs[c].dc;
     A = A + u * cs[c].f;
