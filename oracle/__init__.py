@@ -31,8 +31,16 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                           contact (vertex plane maxima, edge chord midpoints).
   * ``gradient``/``hvp`` -- central finite differences in FP64, rigid-motion
                           null directions, Hessian symmetry.
-  * random-hull blended values at the default softness beyond those
-    invariants and limits: parity unpinned (the paper prints no worked example).
+  * ``pair_contacts`` / ``forward`` on random hulls at the default softness
+                       -- every contact's SDF value and normal against scipy's
+                          logsumexp / softmax of the plane values, vertex
+                          contacts at their vertex, edge contacts strictly
+                          inside their edge, the mollified depth against the
+                          quintic smoothstep, each group against the softmax
+                          average of its contacts.
+  * where the soft sphere trace places an edge's contact along the edge at the
+    default softness (between the limits above): parity unpinned (the paper
+    prints no worked example).
 """
 from __future__ import annotations
 
