@@ -61,6 +61,27 @@ def test_step_host_equals_device_calls(ctx, scene):
         assert np.isfinite(g.numpy()).all() and np.abs(g.numpy()).max() > 0
 
 
+def test_step_host_on_an_overflowing_contact_list(ctx):
+    """With a contact list too small for the cube contacts, the per-item
+    forward and the per-pair reverse pass write the outputs, the gradient,
+    H u and J u instead of the flat stages; the host step, whose copies wait
+    on events around the passes, still returns exactly what the device calls
+    return."""
+    import torch
+    from paper_2604_17538_b300 import api
+    sc = scenes.cube_pair_scene(seed=1, n_poses=16)
+    batch, _, _ = api.scene_to_device(sc, ctx)
+    batch.set_tuning(flat_records=1)
+    pa_h, pb_h, yb_h, u_h = _host_inputs(sc, 3)
+    ref = _device_step(batch, pa_h.cuda(), pb_h.cuda(), yb_h.cuda(), u_h.cuda())
+    y, g, h, j = batch.step_host(pa_h, pb_h, yb_h, u_h, want_jvp=True)
+    torch.cuda.synchronize()
+    for name, a, b in zip("yghj", (y, g, h, j), (ref[0], ref[4], ref[2], ref[3])):
+        assert np.array_equal(a.numpy(), b), (name, np.abs(a.numpy() - b).max())
+    assert np.abs(j.numpy()).max() > 0
+    batch.close()
+
+
 def test_step_host_modes(ctx, scene):
     import torch
     from paper_2604_17538_b300 import api
