@@ -1120,9 +1120,11 @@ ccm_status run_backward(Batch* b, const float* pose_a, const float* pose_b, cons
     F.counters = counters;
     F.n_sm = b->ctx->n_sm;
     F.pdl = b->tuning.pdl == 0 ? 1 : 0;
+    F.fallback_sched = L.sched;
     cudaError_t e = launch_flat_backward(F, stream);
     if (e != cudaSuccess) return cuda_fail(e, "per-contact backward launch");
     L.only_if = F.fp.sched + 2;
+    L.after_chain = F.pdl != 0;
   }
   cudaError_t e = launch_backward(L, stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
@@ -1289,9 +1291,11 @@ ccm_status run_forward(Batch* b, const float* pose_a, const float* pose_b, const
     F.status = static_cast<int*>(b->d_status.ptr);
     F.n_sm = b->ctx->n_sm;
     F.pdl = b->tuning.pdl == 0 ? 1 : 0;
+    F.fallback_sched = L.sched;
     cudaError_t e = launch_flat_forward(F, stream);
     if (e != cudaSuccess) return cuda_fail(e, "flat forward launch");
     L.only_if = F.ctl + kFfOverflow;
+    L.after_chain = F.pdl != 0;   // then launched behind the chain, which zeroed its counter
     e = launch_forward(L, stream);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     return CCM_OK;

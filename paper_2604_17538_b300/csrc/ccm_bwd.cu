@@ -832,6 +832,7 @@ bwd_pair_kernel(DevGeom g, const PairRec* __restrict__ pairs, const int32_t* __r
                 float* __restrict__ grad, float* __restrict__ hvp, float* __restrict__ jvp,
                 unsigned long long* __restrict__ counters, int* __restrict__ sched,
                 const int* __restrict__ only_if) {
+  pdl_wait();   // launched behind the per-contact pass: its flag and buffers first
   if (only_if && *only_if == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -1040,15 +1041,11 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ part,
 template <class T, int kK>
 static void launch_pair(const BwdLaunch& L, cudaStream_t stream) {
   const int smem = bwd_slice_bytes<T>(L.us);
-  if (L.counters)
-    bwd_pair_kernel<T, kK, true><<<L.pair_grid, 32, smem, stream>>>(
-        L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
-        L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, L.counters, L.sched, L.only_if);
-  else
-    bwd_pair_kernel<T, kK, false><<<L.pair_grid, 32, smem, stream>>>(
-        L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs, L.pose_a, L.pose_b, L.ybar, L.dir,
-        L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp, nullptr, L.sched, L.only_if);
-  count_launch();
+  // (a launch error surfaces through cudaGetLastError in launch_backward)
+  launch_k(L.after_chain, L.counters ? bwd_pair_kernel<T, kK, true> : bwd_pair_kernel<T, kK, false>,
+           L.pair_grid, 32, smem, stream, L.g, L.pairs, L.pair_order, L.n_pairs, L.dev_pairs,
+           L.pose_a, L.pose_b, L.ybar, L.dir, L.saved, L.kp, L.us, L.grad, L.hvp, L.jvp,
+           L.counters, L.sched, L.only_if);
 }
 
 template <class T, int kK>
@@ -1067,7 +1064,7 @@ static void launch_unit(const BwdLaunch& L, cudaStream_t stream) {
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t stream) {
   const bool small_k = L.kp.trace_iters == 3;   // the paper's three steps: unrolled
-  if (L.sched) {
+  if (L.sched && !L.after_chain) {
     const cudaError_t e = cudaMemsetAsync(L.sched, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
   }

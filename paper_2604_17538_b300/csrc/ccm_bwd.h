@@ -49,6 +49,10 @@ struct BwdLaunch {
   // if set: the per-pair kernel runs only when this device word is non-zero
   // (the per-contact kernels did not run: see FlatPass::sched)
   const int* only_if = nullptr;
+  // behind the per-contact pass: the per-pair kernel is launched with
+  // programmatic dependent launch (it waits for the pass before it reads
+  // only_if), and `sched` was zeroed by the pass (no memset)
+  bool after_chain = false;
 };
 
 // Resident one-warp blocks per SM of the reverse kernels that launch_backward

@@ -38,7 +38,8 @@
 namespace ccm {
 
 // ---------------------------------------------------------------------------
-// setup: relative poses per unit; counters, group counts and hit words zeroed
+// setup: relative poses per unit; counters (the per-item fallback's too),
+// group counts and hit words zeroed
 // ---------------------------------------------------------------------------
 __global__ void ff_setup_kernel(FlatFwdLaunch L) {
   pdl_wait();
@@ -46,6 +47,7 @@ __global__ void ff_setup_kernel(FlatFwdLaunch L) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid < kFfWords) L.ctl[tid] = 0ull;
   if (tid < kCtlWords) L.cl.ctl[tid] = 0ull;
+  if (tid == 0 && L.fallback_sched) *L.fallback_sched = 0;
   for (int64_t i = tid; i < L.G; i += stride) {
     L.cl.cnt_v[i] = 0;
     L.cl.cnt_e[i] = 0;

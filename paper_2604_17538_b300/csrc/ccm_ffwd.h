@@ -48,6 +48,8 @@ struct FlatFwdLaunch {
   int* status;                    // CCM_ERR_TIMEOUT when a wait gave up
   int pdl;                        // launch the stages with programmatic dependent launch
   int n_sm;
+  int* fallback_sched = nullptr;  // optional: the per-item kernel's work counter, zeroed
+                                  // by the setup stage (that kernel runs behind the chain)
 };
 
 // Runs the flat forward.  When its candidate or contact list overflows, its

@@ -542,11 +542,13 @@ void flat_pass_bytes(bool dual, int64_t cap, int64_t G, size_t* cval, size_t* fo
 
 // The pass uses the list only if it did not overflow and the saved record
 // carries its tag (the record and the list come from the same forward).
-__global__ void flat_gate_kernel(ContactList cl, const float* __restrict__ saved, int* sched) {
+__global__ void flat_gate_kernel(ContactList cl, const float* __restrict__ saved, int* sched,
+                                 int* fallback_sched) {
   pdl_wait();
   const uint32_t tag = reinterpret_cast<const uint32_t*>(saved)[kSavedTag];
   sched[0] = 0;
   sched[1] = 0;
+  if (fallback_sched) *fallback_sched = 0;
   sched[2] = (cl.ctl[kCtlOverflow] != 0ull || tag == 0u ||
               (unsigned long long)tag != cl.ctl[kCtlTag]) ? 1 : 0;
 }
@@ -554,7 +556,8 @@ __global__ void flat_gate_kernel(ContactList cl, const float* __restrict__ saved
 template <class T>
 static cudaError_t launch_flat_t(const FlatLaunch& L, cudaStream_t stream) {
   const bool pdl = L.pdl != 0;
-  cudaError_t e = launch_k(pdl, flat_gate_kernel, 1, 1, 0, stream, L.cl, L.saved, L.fp.sched);
+  cudaError_t e = launch_k(pdl, flat_gate_kernel, 1, 1, 0, stream, L.cl, L.saved, L.fp.sched,
+                           L.fallback_sched);
   if (e != cudaSuccess) return e;
   const int rec_blocks = 16 * L.n_sm;   // persistent: warps draw 32 contacts at a time
   e = launch_k(pdl, L.counters ? flat_eval_kernel<T, true> : flat_eval_kernel<T, false>,

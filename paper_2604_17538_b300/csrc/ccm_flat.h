@@ -38,6 +38,8 @@ struct FlatLaunch {
   unsigned long long* counters;   // optional work counters (CCM_BWD_CNT_*)
   int n_sm;
   int pdl;                   // launch the stages with programmatic dependent launch
+  int* fallback_sched = nullptr;   // optional: the per-pair kernel's work counter, zeroed
+                                   // by the gate kernel (that kernel runs behind the pass)
 };
 
 // Bytes of one pass's scratch (FlatPass) for capacity cap and G groups.

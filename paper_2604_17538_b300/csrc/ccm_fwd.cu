@@ -305,6 +305,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
                 unsigned long long* __restrict__ counters, int* __restrict__ sched,
                 ContactList cl, int* __restrict__ status,
                 const unsigned long long* __restrict__ only_if) {
+  pdl_wait();   // launched behind the flat chain: its flag and buffers first
   if (only_if && *only_if == 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -488,7 +489,7 @@ unit_fwd_kernel(DevGeom g, const PairRec* __restrict__ pairs,
 }
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
-  if (L.sched) {
+  if (L.sched && !L.after_chain) {
     const cudaError_t e = cudaMemsetAsync(L.sched, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
   }
@@ -500,14 +501,11 @@ cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream) {
     const cudaError_t e = cudaMemsetAsync(cl.ctl, 0, kCtlWords * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
   }
-  if (L.counters)
-    unit_fwd_kernel<true><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                             L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status, L.only_if);
-  else
-    unit_fwd_kernel<false><<<L.grid, threads, smem, stream>>>(L.g, L.pairs, L.items, L.order, L.n_items, L.dev_items, L.pose_a,
-                                                              L.pose_b, L.kp, L.us, L.y, L.saved, L.counters, L.sched, cl, L.status, L.only_if);
-  count_launch();
-  return cudaGetLastError();
+  const cudaError_t e = launch_k(L.after_chain, L.counters ? unit_fwd_kernel<true> : unit_fwd_kernel<false>,
+                                 L.grid, threads, smem, stream, L.g, L.pairs, L.items, L.order,
+                                 L.n_items, L.dev_items, L.pose_a, L.pose_b, L.kp, L.us, L.y,
+                                 L.saved, L.counters, L.sched, cl, L.status, L.only_if);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t configure_forward(const UnitShape& us, int smem_limit, int* blocks_per_sm) {

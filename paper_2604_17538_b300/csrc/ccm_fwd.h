@@ -28,6 +28,10 @@ struct FwdLaunch {
   // if set: the kernel runs only when this device word is non-zero (the flat
   // forward overflowed)
   const unsigned long long* only_if = nullptr;
+  // behind the flat forward's chain: launched with programmatic dependent
+  // launch (the kernel waits for the chain before it reads only_if), and
+  // `sched` was zeroed by the chain (no memset)
+  bool after_chain = false;
 };
 
 cudaError_t launch_forward(const FwdLaunch& L, cudaStream_t stream);
