@@ -189,3 +189,22 @@ def test_flat_forward_is_deterministic_and_batch_independent(ctx):
     off = sc.group_offsets()
     rows = np.concatenate([np.arange(off[i], off[i + 1]) for i in (5, 33, 70)])
     assert np.array_equal(ys[2], ys[0][rows])
+
+
+@pytest.mark.parametrize("name", ["cube", "hull"])
+def test_chains_without_programmatic_dependent_launch_give_the_same_results(ctx, name):
+    """Tuning pdl = -1 launches every stage (and the gated fallback kernels
+    behind each chain) as an ordinary launch, the fallbacks' work counters
+    reset by a memset: the same kernels in the same order, so every output of
+    the forward and of both reverse passes is bitwise that of the default
+    chained launches -- also when the contact list overflows (the cube scene
+    with one record per group runs the fallbacks)."""
+    sc = (scenes.cube_pair_scene(seed=1, n_poses=16) if name == "cube"
+          else scenes.hull_env_scene(seed=2, n_envs=24, workers=0))
+    ybar, u = _inputs(sc, seed=4)
+    for extra in ({}, {"flat_records": 1}) if name == "cube" else ({},):
+        on = _saved_step(ctx, sc, ybar, u, **extra)
+        off = _saved_step(ctx, sc, ybar, u, pdl=-1, **extra)
+        for a, b, what in zip(on, off, ("y", "gradient", "gradient (dual pass)", "H u", "J u")):
+            assert np.array_equal(a, b), (name, extra, what, float(np.abs(a - b).max()))
+        assert np.abs(on[3]).max() > 0
