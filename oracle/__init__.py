@@ -15,7 +15,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   * ``spline_u`` / ``spline_sdf`` / FLAG_SPLINE -- basis partition of unity
                           and support, interpolation at the nodes, exact
                           reproduction of linear fields, convergence to a
-                          sphere's SDF, and the stacked-cube closed form.
+                          sphere's SDF, the stacked-cube closed form, and the
+                          64-coefficient window against the brute-force sum
+                          over every coefficient of the grid.
   * FLAG_UNGATED       -- separated bodies (every contact at d_max: uniform
                           weights, the mean of the contact points), a fully
                           immersed body (every f = 1: equal to the gated
@@ -23,7 +25,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                           tau_blend -> 0 argmin over every contact.
   * ``sdf``            -- brute-force polytope distance, LSE bounds, tau -> 0 limit.
   * ``edge_point``     -- Cyrus-Beck chord midpoint (many iterations, small tau),
-                          inside-edge midpoint, one-step convergence on a face.
+                          inside-edge midpoint, one-step convergence on a face;
+                          at the default softness, every trace step against the
+                          recurrence with scipy's logsumexp SDF (and no step
+                          crossing the surface), and many steps converging to
+                          the soft SDF's root along the edge.
   * ``transition``     -- knot values and C^2 continuity.
   * ``forward``        -- cube-on-cube closed form and hard limits, rigid-motion
                           invariance, body-swap symmetry, separation; on random
@@ -38,9 +44,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                           inside their edge, the mollified depth against the
                           quintic smoothstep, each group against the softmax
                           average of its contacts.
-  * where the soft sphere trace places an edge's contact along the edge at the
-    default softness (between the limits above): parity unpinned (the paper
-    prints no worked example).
+  The paper prints no worked example or numeric table, so every pin is a
+  definition evaluated independently, a limit, an invariant, brute force or
+  finite differences; no function is left without one.
 """
 from __future__ import annotations
 

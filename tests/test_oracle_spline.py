@@ -145,3 +145,43 @@ def test_stacked_cubes_with_spline_sdfs_hard_limit(oracle_lib):
         y = oracle_lib.forward(sc, prm)
         assert np.allclose(y[0], case["group_A"], atol=1e-9), y[0]
         assert np.allclose(y[1], case["group_B"], atol=1e-6), y[1]
+
+
+def test_window_sum_equals_the_full_tensor_product_sum(oracle_lib):
+    """The oracle evaluates each spline from the 64 coefficients whose basis
+    functions reach the point; summing c_k u(t_x - (k_x - 1)) u(t_y - (k_y - 1))
+    u(t_z - (k_z - 1)) over every coefficient of the grid (brute force, with
+    the row layout of the coefficient table: z fastest) gives the same SDF
+    value and normal at any point of the grid box, its faces and corners
+    included -- so the window's cell index, its clamping at the last cell and
+    the table's layout are those of the tensor-product definition of Sec. 3.2."""
+    lo, h, dims = np.array([-0.2, -0.1, -0.15]), 0.05, np.array([5, 4, 6])
+
+    def field(p):
+        r = np.linalg.norm(p - [0.02, 0.01, -0.03], axis=1, keepdims=True)
+        return np.concatenate([r - 0.08, np.cos(4 * p)], 1)
+    geom = _one_piece_geom(field, lo, h, dims)
+    coef = geom.splines.coef.astype(np.float64)
+    u = np.vectorize(oracle_lib.spline_u)
+    nx, ny, nz = dims + 3
+    rng = np.random.default_rng(3)
+    # the grid as the geometry stores it (float32)
+    lo32, h32 = geom.splines.grid[0, :3].astype(np.float64), float(geom.splines.grid[0, 3])
+    pts = list(lo32 + h32 * dims * rng.uniform(size=(40, 3)))
+    pts += [lo32 + h32 * np.array(t, float)
+            for t in ((0, 0, 0), dims, (dims[0], 0, dims[2]), dims // 2, (0, dims[1], 2.5))]
+    for x in pts:
+        t = (x - lo32) / h32
+        # a point on a face may round to just outside the box: the extension
+        # beyond it (the value at the nearest box point plus the distance)
+        tc = np.clip(t, 0.0, dims)
+        out = h32 * np.linalg.norm(t - tc)
+        t = tc
+        wx = u(t[0] - (np.arange(nx) - 1))
+        wy = u(t[1] - (np.arange(ny) - 1))
+        wz = u(t[2] - (np.arange(nz) - 1))
+        w = (wx[:, None, None] * wy[None, :, None] * wz[None, None, :]).reshape(-1)
+        ref = w @ coef[:nx * ny * nz]
+        phi, n = oracle_lib.spline_sdf(geom, 0, x)
+        assert out < 1e-12
+        assert abs(phi - (ref[0] + out)) < 1e-12 and np.abs(n - ref[1:]).max() < 1e-12, (x, phi, ref)

@@ -133,3 +133,77 @@ def test_traced_points_never_leave_the_edge(oracle_lib):
         assert 0.0 < t < 1.0
         assert np.linalg.norm(np.cross(pe - a, b - a)) / L < 1e-12   # on the line
         assert 0.0 < al[2] < L + 1e-12 and 0.0 < al[3] < L + 1e-12
+
+
+# ------------------------------------------- Sec. 4.2 at the default softness
+def _soft_sdf(P, tau):
+    from scipy.special import logsumexp
+    return lambda x: tau * logsumexp((P[:, :3] @ x + P[:, 3]) / tau)
+
+
+def test_trace_steps_follow_their_recurrence_at_default_softness(oracle_lib):
+    """The oracle's traced corners after k = 0..3 steps (trace_iters = k) obey
+    the sphere-trace recurrence of Sec. 4.2 with the soft gate of Sec. 2,
+    alpha_{k+1} = alpha_k +/- sigmoid(phi_k / tau_trace) phi_k along the edge,
+    with phi evaluated here by scipy's logsumexp of the plane values; and
+    since phi is 1-Lipschitz and the gate below 1, no step crosses the surface:
+    phi keeps the sign it has at the corner."""
+    from scipy.special import expit
+    rng = np.random.default_rng(11)
+    V, P, _ = scenes.hull_piece(rng.normal(0, 0.05, size=(64, 3)))
+    P = P.astype(np.float64)
+    d = oracle_lib.DEFAULTS
+    phi = _soft_sdf(P, d["tau_sdf"])
+    checked = 0
+    for _ in range(60):
+        a, b = rng.normal(0, 0.12, size=(2, 3))
+        L = np.linalg.norm(b - a)
+        e = (b - a) / L
+        al = [oracle_lib.edge_point(P, a, b, oracle_lib.params(trace_iters=k))[1] for k in range(4)]
+        assert al[0][0] == 0.0 and abs(al[0][1] - L) < 1e-15
+        for k in range(3):
+            for c, sgn in ((0, 1.0), (1, -1.0)):        # corner I along +e, corner II along -e
+                f = phi(a + al[k][c] * e)
+                step = expit(f / d["tau_trace"]) * f
+                assert abs(al[k + 1][c] - (al[k][c] + sgn * step)) < 1e-12
+                f0 = phi(a + al[0][c] * e)
+                f1 = phi(a + al[k + 1][c] * e)
+                assert f1 == 0.0 or np.sign(f1) == np.sign(f0)
+                checked += 1
+    assert checked == 360
+
+
+def test_trace_converges_to_the_soft_surface_at_default_softness(oracle_lib):
+    """Many steps at the default softness: a corner outside the piece moves to
+    the first zero of the soft SDF along its edge (a root found here by
+    bracketing scipy's logsumexp SDF), for edges that cross the surface
+    transversally."""
+    from scipy.optimize import brentq
+    rng = np.random.default_rng(12)
+    V, P, _ = scenes.hull_piece(rng.normal(0, 0.05, size=(64, 3)))
+    P = P.astype(np.float64)
+    d = oracle_lib.DEFAULTS
+    phi = _soft_sdf(P, d["tau_sdf"])
+    prm = oracle_lib.params(trace_iters=400)
+    done = 0
+    while done < 10:
+        c = rng.normal(0, 0.01, 3)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        a, b = c - 0.3 * u, c + 0.3 * u                  # both corners outside
+        L = 0.6
+        g = lambda t: phi(a + t * u)
+        ts = np.linspace(0, L, 601)
+        vals = np.array([g(t) for t in ts])
+        if vals[0] <= 0 or vals[-1] <= 0 or vals.min() >= 0:
+            continue
+        i0 = np.argmax(vals < 0)                         # first sample inside
+        i1 = len(ts) - 1 - np.argmax(vals[::-1] < 0)     # last sample inside
+        t1 = brentq(g, ts[i0 - 1], ts[i0], xtol=1e-15)
+        t2 = brentq(g, ts[i1], ts[i1 + 1], xtol=1e-15)
+        h = 1e-7                                          # crossing slopes
+        if min(abs(g(t1 + h) - g(t1 - h)), abs(g(t2 + h) - g(t2 - h))) / (2 * h) < 0.2:
+            continue
+        _, al = oracle_lib.edge_point(P, a, b, prm)
+        assert abs(al[0] - t1) < 1e-9 and abs(al[1] - t2) < 1e-9, (al[:2], t1, t2)
+        done += 1
