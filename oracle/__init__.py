@@ -9,9 +9,11 @@ marshals numpy arrays through ctypes.
 Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   * ``body_sdf`` / FLAG_BODY_UNION -- LSE bounds against the pieces' SDFs,
                           finite differences, far-apart and single-piece limits,
-                          rigid-motion invariance and body-swap symmetry.
+                          rigid-motion invariance and body-swap symmetry, and
+                          its definition evaluated with scipy's logsumexp.
   * FLAG_PROJECT       -- a single half-space and the stacked-cube face: the
-                          projected points lie on the plane.
+                          projected points lie on the plane; on random hulls,
+                          every projected point is p - phi n of its contact.
   * ``spline_u`` / ``spline_sdf`` / FLAG_SPLINE -- basis partition of unity
                           and support, interpolation at the nodes, exact
                           reproduction of linear fields, convergence to a

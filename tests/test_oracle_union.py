@@ -139,3 +139,37 @@ def test_projection_of_a_single_half_space_lands_on_it(oracle_lib):
     assert len(side_b) > 0
     plane = np.asarray(geom.planes[0], np.float64)
     assert np.allclose(side_b[:, 4:7] @ plane[:3] + plane[3], 0.0, atol=1e-9)
+
+
+def test_union_is_the_softmin_of_its_pieces_definition(oracle_lib, hull_body):
+    """Eq. soft_union evaluated here from its definition: every piece SDF as
+    tau * logsumexp(plane values / tau) and the union as
+    -tau * logsumexp(-phi_s / tau) over the pieces (scipy), its gradient the
+    softmin-weighted mix of the pieces' softmax-weighted plane normals."""
+    from scipy.special import logsumexp, softmax
+    g = hull_body.geom
+    rng = np.random.default_rng(4)
+    body = 0
+    planes = [np.asarray(g.piece(p)[1], np.float64) for p in g.pieces_of(body)]
+    for x in rng.normal(0.0, 0.15, size=(100, 3)):
+        vals = [(P[:, :3] @ x + P[:, 3]) / TAU for P in planes]
+        phis = np.array([TAU * logsumexp(v) for v in vals])
+        grads = np.array([softmax(v) @ P[:, :3] for v, P in zip(vals, planes)])
+        ref = -TAU * logsumexp(-phis / TAU)
+        ref_g = softmax(-phis / TAU) @ grads
+        phi, grad = oracle_lib.body_sdf(g, body, x, TAU)
+        assert abs(phi - ref) < 1e-12 and np.abs(grad - ref_g).max() < 1e-10
+
+
+def test_projection_moves_every_contact_by_its_depth_along_its_normal(oracle_lib):
+    """On random hulls at the default softness every projected contact point
+    is the unprojected one moved by -phi along the contact normal (Sec. 4.1,
+    p - phi(p) n(p), here in world frame, where the normal is the SDF body's
+    rotated normal), and nothing else about the contact changes."""
+    sc = scenes.hull_env_scene(seed=6, n_envs=3, workers=1)
+    for i in range(sc.n_pairs):
+        rows = oracle_lib.pair_contacts(sc, i, oracle_lib.params(flags=oracle_lib.FLAG_PROJECT))
+        base = oracle_lib.pair_contacts(sc, i)
+        assert np.array_equal(rows[:, :4], base[:, :4]) and np.array_equal(rows[:, 7:], base[:, 7:])
+        moved = base[:, 4:7] - base[:, 1:2] * base[:, 7:10]
+        assert np.abs(rows[:, 4:7] - moved).max() < 1e-12
