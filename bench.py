@@ -410,7 +410,8 @@ def run_ours(args, rank, world):
 def oracle_sample_rate(sc, target_s=12.0, kind="hvp", what="environments"):
     """Times the oracle on a bounded seeded sample of the scene's pairs:
     kind "hvp" = forward, gradient and H u in one nested-dual pass, "grad" =
-    the forward and the gradient; returns (qps, cores, sample, seconds)."""
+    the forward and the gradient, "fwd" = the forward alone; returns (qps,
+    cores, sample, seconds)."""
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0))
@@ -427,7 +428,8 @@ def oracle_sample_rate(sc, target_s=12.0, kind="hvp", what="environments"):
             oracle.hvp(sub, yb, u, threads=cores)
         else:
             oracle.forward(sub, threads=cores)
-            oracle.gradient(sub, yb, threads=cores)
+            if kind == "grad":
+                oracle.gradient(sub, yb, threads=cores)
         return time.perf_counter() - t0, sub.piece_pairs()
 
     k = min(16, sc.n_pairs)
@@ -831,7 +833,17 @@ def run_serve(args, rank, world, n_req=10000, rates=None):
             P = run_rate(len(results), f * sat["req_s"], round(f, 3))
     top = max(results, key=lambda r: r["served"]["req_s"])
     plain = plain_batched(P)
-    return {"geometry": f"uneven pool: {sc.n_pairs} placed pairs over "
+    extra = {}
+    if not args.no_cpu_baseline:
+        # the oracle on the same pool's pairs, forward alone and forward +
+        # gradient, combined for the 50/50 request mix
+        qf, cores, sf, tf = oracle_sample_rate(sc, target_s=4.0, kind="fwd", what="body pairs")
+        qg, _, sg, tg = oracle_sample_rate(sc, target_s=4.0, kind="grad", what="body pairs")
+        extra["cpu_baseline"] = {
+            "value": 1.0 / (0.5 / qf + 0.5 / qg), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"forward: {sf}, {tf:.1f} s; forward + gradient: {sg}, {tg:.1f} s; "
+                      "rate of the 50/50 mix of the two"}
+    return {**extra, "geometry": f"uneven pool: {sc.n_pairs} placed pairs over "
                         f"{len(npb)} bodies, pieces/body log-U[1,64], hull points log-U[8,512]",
             "requests": "Poisson arrivals; 1-256 envs log-uniform; 50/50 fwd vs fwd+grad",
             "hbm_budget_bytes": SERVE_BUDGET, "generation_s": t_gen,
