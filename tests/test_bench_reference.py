@@ -46,3 +46,20 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert len(lines) == 1, r.stdout
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_oracle_sample_rates_of_each_kind():
+    """The oracle timing behind the CPU baselines (the 4096-environment step,
+    the uneven batch and the serving mix): a bounded seeded sample for every
+    kind of pass, a positive rate, and a sample description that names it."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    from paper_2604_17538_b300 import scenes
+    sc = scenes.uneven_scene(seed=3, n_pairs=40, max_pieces=3, max_points=24, pool_bodies=12,
+                             workers=1)
+    for kind in ("fwd", "grad", "hvp"):
+        qps, cores, sample, dt = bench.oracle_sample_rate(sc, target_s=0.2, kind=kind,
+                                                          what="body pairs")
+        assert qps > 0 and cores >= 1 and dt > 0
+        assert "of 40 body pairs" in sample and "piece pairs" in sample
